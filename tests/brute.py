@@ -1,0 +1,69 @@
+"""Brute-force definitions used to pin the oracle on tiny inputs (pure Python, no oracle code).
+
+Everything here is the plain definition, enumerated exhaustively:
+  * a colourful embedding (Section 1, SubIso; Section 2.1, colourful copy) is an injective map
+    Phi: V(F) -> V(G) that keeps every edge of F and gives its image distinct colours;
+  * the table value D(x, phi, C) (Section 2.1, semantics of the table) counted: the number of
+    colourful embeddings of F[V*_x] that agree with phi on the bag V_x and use exactly colours C.
+"""
+from __future__ import annotations
+
+from collections import Counter
+from itertools import permutations
+
+import numpy as np
+
+
+def adj_sets(row_ptr, col):
+    n = len(row_ptr) - 1
+    return [set(int(c) for c in col[row_ptr[v]:row_ptr[v + 1]]) for v in range(n)]
+
+
+def embeddings(G, nF, edges, zeta=None, verts=None):
+    """All colourful embeddings of F[verts] (default: all of F) as dicts u -> v.  zeta=None
+    drops the colour condition (plain injective homomorphisms)."""
+    adj = G
+    n = len(adj)
+    verts = list(range(nF)) if verts is None else sorted(verts)
+    vs = set(verts)
+    E = [(int(a), int(b)) for a, b in np.asarray(edges).reshape(-1, 2) if a in vs and b in vs]
+    out = []
+    for img in permutations(range(n), len(verts)):
+        m = dict(zip(verts, img))
+        if any(m[b] not in adj[m[a]] for a, b in E):
+            continue
+        if zeta is not None and len({int(zeta[v]) for v in img}) != len(img):
+            continue
+        out.append(m)
+    return out
+
+
+def count_embeddings(G, nF, edges, zeta):
+    return len(embeddings(G, nF, edges, zeta))
+
+
+def vstar(nodes):
+    """V*_x for every node of a nice decomposition given as (type, c0, c1, vertex, bag)."""
+    vs = []
+    for (ty, c0, c1, u, bag) in nodes:
+        s = set(bag)
+        for c in (c0, c1):
+            if c >= 0:
+                s |= vs[c]
+        vs.append(s)
+    return vs
+
+
+def node_table(G, nF, edges, zeta, bag, verts, degG=None, degF=None):
+    """D(x, ., .) by definition: Counter over (phi tuple in bag order, colour set) of colourful
+    embeddings of F[verts].  With degG/degF given, only maps with deg_G(Phi(y)) >= deg_F(y)
+    for every y are counted (the degree filter of Section 3.2)."""
+    tab = Counter()
+    for m in embeddings(G, nF, edges, zeta, verts):
+        if degG is not None and any(degG[m[y]] < degF[y] for y in m):
+            continue
+        C = 0
+        for v in m.values():
+            C |= 1 << int(zeta[v])
+        tab[(tuple(m[u] for u in bag), C)] += 1
+    return tab
