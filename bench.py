@@ -1,0 +1,349 @@
+"""Benchmark of the colour-coding dynamic programme (arXiv 1908.11248) on one GB300.
+
+Workload (default): Barabasi-Albert host graph n=20000, m=4 (seed 1, ~80k edges, int32 CSR);
+pattern the 2x4 grid (8 vertices, treewidth 2, column-sweep decomposition); k=8 colours from
+Philox4x32-10 seed 7; 64 colouring trials in one batched run.  One step = colour all trials,
+run every node of the nice decomposition for all trials at once, test the root and read the
+per-trial uint64 counts back.
+
+Metric: DP entries/s, entries = sum over nodes and trials of |D_x| (distinct table entries; the
+same number on the CPU oracle for the same decomposition and flags).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure, never the product path) on a
+bounded sample of the same workload.  With N > 1 (torchrun) every rank runs an independent
+replica with its own colouring seed; rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "ba20k_grid2x4"
+METRIC = "DP entries/s"
+UNIT = "entries/s"
+# dram bytes (read + write) of the dominant kernel per launch from an ncu capture of this
+# workload, or None when no capture matches the current kernel
+TRAFFIC = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def slot_bytes(b, k):
+    """Algorithmic bytes of one table entry: b vertex ids, the colour set and the count."""
+    return 4 * b + (2 if k <= 16 else 4) + 8
+
+
+def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
+    """Bytes a launch must move by the method's definition (not by this implementation)."""
+    ty, c0, c1, u, bag = nodes[node]
+    S = lambda x: slot_bytes(len(nodes[x][4]), k)  # noqa: E731
+    if kind == "color":
+        return T * n
+    if kind == "leaf":
+        return n * T * (1 + S(node))
+    if kind in ("intro_count", "intro_write", "intro_fused"):
+        b = int(sizes[c0]) * S(c0) + int(cand) * 5
+        if kind == "intro_write":
+            b += int(sizes[node]) * S(node)
+        if kind == "intro_fused":
+            parent = next(i for i, nd in enumerate(nodes) if nd[1] == node)
+            b += int(sizes[parent]) * S(parent)
+        return b
+    if kind == "forget":
+        return int(sizes[c0]) * S(c0) + int(sizes[node]) * S(node)
+    if kind.startswith("join"):
+        b = (int(sizes[c0]) + int(sizes[c1])) * S(node)
+        if kind == "join_write":
+            b += int(sizes[node]) * S(node)
+        return b
+    if kind == "root":
+        return int(sizes[node]) * S(node)
+    return 0
+
+
+def run_reference(args, rank):
+    """The CPU oracle, as it stands, on a bounded sample: one trial of the workload per step."""
+    import oracle
+
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[WORKLOAD]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    n = len(g[0]) - 1
+    z = oracle.colors(n, w["trials"], w["k"], w["seed"])
+    times, entries = [], 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ref = oracle.run_dp(g, pat, z[s % w["trials"]:s % w["trials"] + 1], w["k"])
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            entries += int(ref.node_sizes.sum())
+    tot = sum(times)
+    value = entries / tot
+    sample = "one of the 64 trials per step (trials 0..), single-threaded std::map oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "BA n=20000 m=4 seed 1",
+                   "pattern": "grid 2x4", "k": 8, "trials_per_step": 1,
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1908_11248_gb300 as cc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    w = synth.WORKLOADS[WORKLOAD]
+    g = synth.make_graph(w["graph"])
+    nF, edges, td = synth.make_pattern(w["pattern"])
+    n = len(g[0]) - 1
+    T, k = w["trials"], w["k"]
+    seed = w["seed"] + 1000003 * rank
+    ctx = cc.Context(arena_bytes=96 << 30, device=local)
+    h = ctx.h
+    cc.cc_load_graph(h, *g)
+    pid = cc.cc_load_pattern(h, nF, edges, td)
+    nodes = cc.cc_pattern_nodes(h, pid, nF)
+    opts = cc.cc_default_opts(profile=1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        cid = cc.cc_color(h, seed, T, k)
+        run = cc.cc_run_dp(h, pid, cid, opts)
+        counts = cc.cc_count(h, run, T)
+        return cid, run, counts
+
+    for _ in range(args.warmup):
+        cid, run, counts = step()
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = cc.cc_context_stats(h)[0]
+    step_ms, entries, kern = [], 0, {}
+    sizes = None
+    for s in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (256 MB > 129 MB L2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cid, run, counts = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sizes, total = cc.cc_table_stats(h, run, len(nodes))
+        entries += total
+        node, kind, ms, cand = cc.cc_run_timings(h, run)
+        for i in range(len(node)):
+            kn = cc.KERNEL_KINDS[int(kind[i])]
+            d = kern.setdefault(kn, {"launches": 0, "ms": 0.0, "bytes": 0})
+            d["launches"] += 1
+            d["ms"] += float(ms[i])
+            d["bytes"] += algorithmic_bytes(kn, int(node[i]), nodes, sizes, cand[i], n, T, k)
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    torch.cuda.synchronize()
+    launches = cc.cc_context_stats(h)[0] - launches0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        ent = torch.tensor([entries], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ent)
+        entries_all = float(ent.item())
+    else:
+        entries_all = float(entries)
+    value = entries_all / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel (largest share of device time)
+    dom = max(kern, key=lambda x: kern[x]["ms"])
+    d = kern[dom]
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC,
+            "bytes_per_launch": d["bytes"] / d["launches"],
+            "ms_per_launch": d["ms"] / d["launches"],
+            "kernels": {kn: {"launches": v["launches"] // args.steps,
+                             "ms_per_step": v["ms"] / args.steps,
+                             "share": v["ms"] / sum(x["ms"] for x in kern.values()),
+                             "gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None}
+                        for kn, v in sorted(kern.items(), key=lambda x: -x[1]["ms"])}}
+
+    # end to end through the C ABI: graph from pinned host memory, counts back to the host
+    e2e = None
+    if rank == 0:
+        rp_h = torch.from_numpy(np.asarray(g[0], np.int32)).pin_memory().numpy()
+        col_h = torch.from_numpy(np.asarray(g[1], np.int32)).pin_memory().numpy()
+        e2e_t, e2e_ent = [], 0
+        for s in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cc.cc_load_graph(h, rp_h, col_h)
+            cid = cc.cc_color(h, seed, T, k)
+            run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts())
+            counts = cc.cc_count(h, run, T)
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_ent += cc.cc_table_stats(h, run, len(nodes))[1]
+            cc.cc_release(h, run)
+            cc.cc_release_colors(h, cid)
+        e2e = {"value": e2e_ent / sum(e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes),
+               "d2h_bytes_per_step": int(T * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        z = oracle.colors(n, 1, k, seed)
+        t0 = time.perf_counter()
+        ref = oracle.run_dp(g, (nF, edges, td), z, k)
+        dt = time.perf_counter() - t0
+        cpu = {"value": float(ref.node_sizes.sum()) / dt, "unit": UNIT, "cores": 1,
+               "kind": "oracle",
+               "sample": "trial 0 of the 64 (one colouring), single-threaded std::map oracle, "
+                         f"{dt:.1f} s"}
+        # the sampled trial's count must agree with the GPU's
+        assert int(ref.count[0]) == int(counts[0]), "oracle and GPU disagree on trial 0"
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": "BA n=20000 m=4 seed 1",
+                       "pattern": "grid 2x4 (column-sweep decomposition)", "k": k,
+                       "trials": T, "entries_per_step": int(entries / args.steps),
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * cc.h -- C ABI of the GB300 colour-coding library for subgraph isomorphism (SubIso) and
+ * subgraph enumeration (SubEnum), after Malik, Suchy and Valla, arXiv 1908.11248.
+ *
+ * The method (paper Sections 2-4): colour the host graph G at random with k colours (Section
+ * 2.1), run a dynamic programme bottom-up over a nice tree decomposition of the pattern F whose
+ * tables hold the nonzero configurations (bag mapping phi, colour set C) of every node
+ * (Section 3.1: leaf, introduce, forget and join rules), test the root (a solution exists iff the
+ * root table is nonempty), and reconstruct the embeddings top-down (Section 4).  This library
+ * extends the Boolean table of the paper to uint64 counts of colourful embeddings (mod 2^64);
+ * the set of nonzero configurations is exactly the paper's.
+ *
+ * Conventions
+ *   - Every function returns CC_OK (0) or a negative error code; no exception crosses the ABI.
+ *   - Pointers named h_* are HOST pointers and are only read or written during the call (the
+ *     library copies inputs in).  Pointers named d_* are DEVICE pointers of the context's GPU.
+ *   - Graph vertices are int32 ids 0..n-1; pattern vertices 0..n_F-1 with n_F <= 32.
+ *   - Colours are 0-based; bit i of a colour set is colour i (Section 3.2).  k >= n_F, k <= 32.
+ *   - One context is driven by one host thread at a time, except the cc_serve_* functions,
+ *     which are thread-safe.
+ *   - All device work runs on the stream given to cc_create, in the order of the calls.
+ */
+#ifndef CC_H
+#define CC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------------ */
+#define CC_OK 0
+#define CC_EINVAL (-1)     /* malformed argument: bad CSR, bad decomposition, k < n_F, ...     */
+#define CC_ENOMEM (-2)     /* the device arena cannot hold the request                          */
+#define CC_ECAPACITY (-3)  /* a table outgrew its planned capacity; nothing partial is returned */
+#define CC_ETIMEOUT (-4)   /* a bounded device-side wait or a host wait ran out                 */
+#define CC_ECUDA (-5)      /* a CUDA runtime call failed                                        */
+#define CC_ENOTFOUND (-6)  /* unknown pattern, colouring, run or ticket id                      */
+#define CC_EKEYWIDTH (-7)  /* trial, bag-mapping and colour-set bits do not fit in 128 bits     */
+
+/* Static text for an error code. */
+const char *cc_strerror(int code);
+
+/* ---- context ------------------------------------------------------------------------------ */
+typedef struct cc_ctx cc_ctx;
+
+/* Creates a context on CUDA device `device`, issuing all work on `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  Device memory: if d_arena is non-NULL the context
+ * sub-allocates every device buffer from [d_arena, d_arena + arena_bytes), which stays owned by
+ * the caller and must outlive the context; if d_arena is NULL the context allocates an arena of
+ * arena_bytes itself (cudaMalloc) and frees it in cc_destroy.  Errors: CC_EINVAL (bad device or
+ * arena_bytes == 0), CC_ECUDA, CC_ENOMEM. */
+int cc_create(cc_ctx **out, int device, void *cuda_stream, void *d_arena, size_t arena_bytes);
+
+/* Waits for the context's stream, stops a running server and frees the context. */
+int cc_destroy(cc_ctx *ctx);
+
+/* ---- host graph G (paper Section 1.2: undirected and simple) ------------------------------- */
+/* Loads G from host CSR: h_row_ptr[n+1] (h_row_ptr[0] == 0, nondecreasing) and
+ * h_col[h_row_ptr[n]].  Every row must be strictly increasing, hold no self loop, and the
+ * adjacency must be symmetric; anything else is CC_EINVAL.  Replaces a previous graph and
+ * releases every run and colouring made on it.  n may be 0 (no vertex). */
+int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_t *h_col);
+
+/* ---- pattern F and its decomposition (Sections 1.2 and 3) ---------------------------------- */
+/* A tree decomposition (Section 1.2, Definition of tree decomposition): num_bags bags, bag i
+ * holding h_bag_vtx[h_bag_ptr[i] .. h_bag_ptr[i+1]), h_parent[i] its parent bag or -1 for the
+ * single root.  Bags must be nonempty. */
+typedef struct {
+  int32_t num_bags;
+  const int32_t *h_bag_ptr;
+  const int32_t *h_bag_vtx;
+  const int32_t *h_parent;
+} cc_td;
+
+/* Loads F (n_F vertices, m_F undirected edges h_edges[2*m_F]) with decomposition `td`, or, if
+ * td is NULL, with a minimum-width decomposition computed from elimination orderings
+ * (Section 3, O(n_F^2 2^n_F) for n_F <= 20, a greedy min-fill ordering above).  The
+ * decomposition is converted to a nice one (Section 1.2, leaf bags of size one, empty root of
+ * degree one): children taken in increasing id, forgets before introduces, each in increasing
+ * vertex order, several children joined left-deep.  Errors: CC_EINVAL for n_F outside 1..32,
+ * an edge out of range or a loop, or a td that is not a tree decomposition of F. */
+int cc_load_pattern(cc_ctx *ctx, int32_t n_F, int32_t m_F, const int32_t *h_edges,
+                    const cc_td *td, int32_t *pattern_id);
+
+/* Node count and width (largest bag size minus one) of a loaded pattern's nice decomposition. */
+int cc_pattern_info(cc_ctx *ctx, int32_t pattern_id, int32_t *num_nodes, int32_t *width);
+
+/* The nice decomposition in post-order (root last).  type: 0 leaf, 1 introduce, 2 forget,
+ * 3 join; child0/child1 node ids or -1; vertex: leaf, introduced or forgotten F-vertex (-1 for
+ * join); bag of node i is h_bag_vtx[h_bag_ptr[i] .. h_bag_ptr[i+1]) in increasing order.
+ * Arrays: num_nodes entries, h_bag_ptr num_nodes+1, h_bag_vtx num_nodes*n_F. */
+int cc_pattern_nodes(cc_ctx *ctx, int32_t pattern_id, int32_t *h_type, int32_t *h_child0,
+                     int32_t *h_child1, int32_t *h_vertex, int32_t *h_bag_ptr,
+                     int32_t *h_bag_vtx);
+
+/* ---- colourings (Section 2.1) ------------------------------------------------------------- */
+/* Draws `trials` random k-colourings of the loaded graph on the device: the colour of vertex v in
+ * trial t is floor(x * k / 2^32) where x is the first output word of Philox4x32-10 (Salmon et
+ * al., SC'11) at counter (v, t, 0, 0) and key (low 32 bits of seed, high 32 bits of seed).
+ * Errors: CC_EINVAL (no graph, trials < 1, k outside 1..32). */
+int cc_color(cc_ctx *ctx, uint64_t seed, int32_t trials, int32_t k, int32_t *coloring_id);
+
+/* Uses explicit colourings h_colors[trials * n] (row t = trial t, values < k). */
+int cc_set_colors(cc_ctx *ctx, const uint8_t *h_colors, int32_t trials, int32_t k,
+                  int32_t *coloring_id);
+
+/* Copies a colouring back to the host (h_out[trials * n]). */
+int cc_get_colors(cc_ctx *ctx, int32_t coloring_id, uint8_t *h_out);
+
+/* Frees a colouring (runs made from it keep their own reference until released). */
+int cc_release_colors(cc_ctx *ctx, int32_t coloring_id);
+
+/* ---- the dynamic programme (Section 3.1) -------------------------------------------------- */
+typedef struct {
+  int32_t degree_filter; /* map y to x only if deg_G(x) >= deg_F(y) (Section 3.2); 1 = on     */
+  int32_t retain;        /* keep every node table for cc_enumerate / cc_table_dump            */
+  int32_t fuse;          /* 1: an introduce followed by a forget runs as one kernel, and its  */
+                         /*    table is never stored (its size is still counted)              */
+  int32_t use_graph;     /* 1: replay the node kernels from a captured CUDA graph when the     */
+                         /*    plan's capacities are known (falls back to planning otherwise)  */
+  float load_factor;     /* hash-table fill target in (0, 0.9]; 0 = library default           */
+  int32_t block;         /* threads per block of the node kernels (128, 256 or 512)           */
+  int32_t profile;       /* 1: time every kernel launch with CUDA events (cc_run_timings)     */
+} cc_run_opts;
+
+/* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 1, use_graph 0, load factor
+ * 0.5, block 256, profile 0). */
+void cc_default_opts(cc_run_opts *opts);
+
+/* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in
+ * the same launches: the trial index is part of every table key).  Requires k >= n_F.  On
+ * success *run_id names the result; per-trial results stay on the device until read.
+ * Errors: CC_EINVAL, CC_ENOTFOUND, CC_ENOMEM (arena too small: nothing is kept),
+ * CC_EKEYWIDTH (ceil(log2 trials) + width_bags * ceil(log2 n) + k > 128), CC_ECUDA. */
+int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run_opts *opts,
+              int32_t *run_id);
+
+/* Runs several (pattern, colouring) DPs; their node steps are issued on forked streams and
+ * replayed as one CUDA graph once their capacities are planned.  run_ids[npat] out. */
+int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *h_pattern_ids,
+                 const int32_t *h_coloring_ids, const cc_run_opts *opts, int32_t *h_run_ids);
+
+/* Per trial: 1 if a colourful copy of F exists (the root table is nonempty), else 0. */
+int cc_decide(cc_ctx *ctx, int32_t run_id, uint8_t *h_exists);
+
+/* Per trial: number of colourful embeddings Phi: V(F) -> V(G) (labelled maps, so every copy
+ * counts |Aut(F)| times), mod 2^64. */
+int cc_count(cc_ctx *ctx, int32_t run_id, uint64_t *h_counts);
+
+/* Table sizes |D_x| summed over trials, one per node (h_sizes[num_nodes]), and their sum. */
+int cc_table_stats(cc_ctx *ctx, int32_t run_id, uint64_t *h_sizes, uint64_t *h_total);
+
+/* Copies the table of node `node` (run made with retain = 1 and fuse = 0, or a node whose table
+ * was stored) to the host, unpacked: for entry i, h_trial[i], the bag tuple
+ * h_phi[i*b .. i*b+b) (b = bag size, bag order increasing), h_mask[i] and h_cnt[i].  Arrays
+ * must hold `capacity` entries; *n_out gets the entry count (CC_ECAPACITY if it exceeds
+ * capacity).  Entries come in no particular order. */
+int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity,
+                  int32_t *h_trial, int32_t *h_phi, uint32_t *h_mask, uint64_t *h_cnt,
+                  uint64_t *n_out);
+
+/* Result reconstruction (Section 4) on the device for a run made with retain = 1: the union
+ * over the run's trials of all colourful embeddings, without repeats, sorted lexicographically
+ * by (Phi(0), ..., Phi(n_F-1)), truncated to `limit` rows written to h_out[limit * n_F].
+ * *n_out = rows written, *n_total = distinct embeddings before truncation.  Errors:
+ * CC_EINVAL (run not retained), CC_ENOMEM (the embeddings do not fit the arena). */
+int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, uint64_t *n_out,
+                 uint64_t *n_total);
+
+/* Frees a run's tables and results. */
+int cc_release(cc_ctx *ctx, int32_t run_id);
+
+/* Kernel kinds reported by cc_run_timings. */
+#define CC_K_COLOR 0
+#define CC_K_LEAF 1
+#define CC_K_INTRO_COUNT 2
+#define CC_K_INTRO_WRITE 3
+#define CC_K_INTRO_FUSED 4
+#define CC_K_FORGET 5
+#define CC_K_JOIN_BUILD 6
+#define CC_K_JOIN_COUNT 7
+#define CC_K_JOIN_WRITE 8
+#define CC_K_ROOT 9
+
+/* Per-launch device times of a run made with profile = 1, in launch order: node id, kernel
+ * kind (CC_K_*), milliseconds between CUDA events recorded on the context's stream just before
+ * and just after the launch, and the number of candidate vertices the launch examined
+ * (introduce kinds; 0 otherwise).  Arrays hold `capacity` entries; *n_out gets the launch
+ * count (CC_ECAPACITY if it exceeds capacity). */
+int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,
+                   int32_t *h_kind, float *h_ms, uint64_t *h_candidates, int32_t *n_out);
+
+/* Context counters: kernel launches issued since cc_create, arena bytes in use and arena size. */
+int cc_context_stats(cc_ctx *ctx, uint64_t *kernel_launches, uint64_t *arena_used,
+                     uint64_t *arena_size);
+
+/* ---- serving: a resident graph, queries admitted by table memory, batched as they arrive --- */
+/* Starts a server thread that owns device work for submitted queries; mem_budget bytes of the
+ * arena may hold query tables at once (0 = half the free arena). */
+int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight);
+
+/* Queues a query (pattern, seed, trials, k); returns at once with a ticket. */
+int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t trials, int32_t k,
+                    int64_t *ticket);
+
+/* Polls a ticket: *done = 1 when finished (then counts/exists hold `trials` values and
+ * latency_ns the submit-to-completion time), 0 while queued or running; *status its result. */
+int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
+                  uint64_t *h_counts, uint8_t *h_exists, int64_t *latency_ns);
+
+/* Stops the server after the queued queries finish. */
+int cc_serve_stop(cc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H */

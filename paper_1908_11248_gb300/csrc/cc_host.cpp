@@ -1,0 +1,1174 @@
+// Host runtime of the colour-coding library: the C ABI of include/cc.h.
+//
+// It owns the device arena, validates and uploads the host graph, turns a pattern and its tree
+// decomposition into a nice decomposition (Section 1.2, Section 3), plans every node's table and
+// issues the node kernels of cc_kernels.cu in post-order (Section 3.1).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cc.h"
+#include "cc_internal.h"
+
+namespace cc {
+int enumerate_run(struct Ctx *ctx, struct Run *run, uint64_t limit, int32_t *h_out,
+                  uint64_t *n_out, uint64_t *n_total);
+}
+
+using cc::DevInfo;
+using cc::KeyLayout;
+using cc::TableDesc;
+typedef unsigned long long u64;
+
+// ------------------------------------------------------------------------------------------
+// device arena: first-fit over one device range, 256-byte aligned blocks
+// ------------------------------------------------------------------------------------------
+namespace {
+
+class Arena {
+ public:
+  void init(char *base, size_t size) {
+    base_ = base;
+    size_ = size;
+    free_.clear();
+    used_.clear();
+    if (size) free_[0] = size;
+  }
+  void *alloc(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      size_t off = it->first, sz = it->second;
+      free_.erase(it);
+      if (sz > bytes) free_[off + bytes] = sz - bytes;
+      used_[off] = bytes;
+      return base_ + off;
+    }
+    return nullptr;
+  }
+  void release(void *p) {
+    if (!p) return;
+    size_t off = (char *)p - base_;
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t sz = u->second;
+    used_.erase(u);
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + sz) {
+      sz += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        pv->second += sz;
+        return;
+      }
+    }
+    free_[off] = sz;
+  }
+  size_t free_bytes() const {
+    size_t s = 0;
+    for (auto &f : free_) s += f.second;
+    return s;
+  }
+  size_t size() const { return size_; }
+  size_t largest_free() const {
+    size_t s = 0;
+    for (auto &f : free_) s = std::max(s, f.second);
+    return s;
+  }
+
+ private:
+  char *base_ = nullptr;
+  size_t size_ = 0;
+  std::map<size_t, size_t> free_, used_;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// context objects
+// ------------------------------------------------------------------------------------------
+namespace cc {
+
+struct NiceNode {
+  int32_t type = 0;  // 0 leaf, 1 introduce, 2 forget, 3 join
+  int32_t child0 = -1, child1 = -1, vertex = -1, parent = -1;
+  std::vector<int32_t> bag;  // increasing
+};
+
+struct Pattern {
+  int32_t nF = 0;
+  std::vector<uint32_t> adj;  // adjacency bitmask per F-vertex
+  std::vector<int32_t> deg;
+  std::vector<NiceNode> nodes;  // post-order, root last
+  int32_t width = 0;
+};
+
+struct Coloring {
+  int32_t trials = 0, k = 0;
+  uint8_t *d_colors = nullptr;
+  int refs = 1;
+};
+
+struct NodeTable {
+  void *slots = nullptr;
+  u64 cap = 0;
+  int hashed = 0;
+  bool stored = false;
+};
+
+struct Timing {
+  int32_t node, kind;
+  cudaEvent_t start, stop;
+  u64 candidates;
+};
+
+struct Run {
+  int32_t pattern = -1, coloring = -1;
+  std::vector<Timing> timings;
+  cc_run_opts opts{};
+  KeyLayout L{};
+  int kw = 1;
+  int32_t trials = 0;
+  std::vector<NodeTable> tables;
+  u64 *d_counters = nullptr;  // one per node
+  unsigned *d_exists = nullptr;
+  u64 *d_count = nullptr;
+  std::vector<u64> sizes;
+  bool retained = false;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  DevInfo dev;
+  Arena arena;
+  char *owned_arena = nullptr;
+  // graph
+  int32_t n = -1;
+  int32_t *d_row_ptr = nullptr, *d_col = nullptr;
+  std::vector<int32_t> h_row_ptr, h_col;
+  int *d_err = nullptr;
+  u64 *d_scratch = nullptr;  // small per-call scratch (block counts, pair counter)
+  size_t scratch_words = 0;
+  std::map<int32_t, Pattern> patterns;
+  std::map<int32_t, Coloring> colorings;
+  std::map<int32_t, std::unique_ptr<Run>> runs;
+  int32_t next_pattern = 1, next_coloring = 1, next_run = 1;
+  u64 launches = 0;
+  // serving
+  struct Server *server = nullptr;
+};
+
+}  // namespace cc
+
+using cc::Ctx;
+using cc::NiceNode;
+using cc::Pattern;
+using cc::Run;
+
+namespace {
+
+#define CUDA_OK(expr)                               \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return CC_ECUDA;         \
+  } while (0)
+
+int check_launch(int r) { return r == 0 ? CC_OK : CC_ECUDA; }
+
+int bits_for(u64 x) {  // bits to hold values 0..x
+  int b = 0;
+  while ((x >> b) != 0) ++b;
+  return b;
+}
+
+u64 hash_cap(u64 entries, float lf) {
+  double want = (double)std::max<u64>(entries, 1) / (double)lf;
+  u64 c = 16;
+  while ((double)c < want) c <<= 1;
+  return c;
+}
+
+// ---- nice tree decomposition (Section 1.2; Section 3, after Cygan et al.) ------------------
+bool valid_td(const std::vector<uint32_t> &adj, int nF, const std::vector<std::vector<int>> &bags,
+              const std::vector<int> &parent, int &root) {
+  int nb = (int)bags.size();
+  if (nb == 0) return false;
+  root = -1;
+  for (int i = 0; i < nb; ++i) {
+    if (bags[i].empty()) return false;
+    if (parent[i] < 0) {
+      if (root >= 0) return false;
+      root = i;
+    } else if (parent[i] >= nb || parent[i] == i) {
+      return false;
+    }
+  }
+  if (root < 0) return false;
+  for (int i = 0; i < nb; ++i) {  // acyclic, reaches the root
+    int x = i, steps = 0;
+    while (parent[x] >= 0 && steps <= nb) {
+      x = parent[x];
+      ++steps;
+    }
+    if (x != root) return false;
+  }
+  std::vector<uint32_t> bm(nb, 0);
+  for (int i = 0; i < nb; ++i)
+    for (int u : bags[i]) {
+      if (u < 0 || u >= nF || (bm[i] >> u & 1u)) return false;
+      bm[i] |= 1u << u;
+    }
+  for (int u = 0; u < nF; ++u) {  // (i) covered, (iii) connected: exactly one topmost bag
+    int tops = 0, holders = 0;
+    for (int i = 0; i < nb; ++i) {
+      if (!(bm[i] >> u & 1u)) continue;
+      ++holders;
+      if (parent[i] < 0 || !(bm[parent[i]] >> u & 1u)) ++tops;
+    }
+    if (holders == 0 || tops != 1) return false;
+  }
+  for (int a = 0; a < nF; ++a)  // (ii) every edge in some bag
+    for (int b = a + 1; b < nF; ++b) {
+      if (!(adj[a] >> b & 1u)) continue;
+      bool ok = false;
+      for (int i = 0; i < nb && !ok; ++i) ok = (bm[i] >> a & 1u) && (bm[i] >> b & 1u);
+      if (!ok) return false;
+    }
+  return true;
+}
+
+void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<int> &parent,
+                int root, std::vector<NiceNode> &out) {
+  int nb = (int)bags_in.size();
+  std::vector<std::vector<int>> bags(bags_in), kids(nb);
+  for (auto &b : bags) std::sort(b.begin(), b.end());
+  for (int i = 0; i < nb; ++i)
+    if (parent[i] >= 0) kids[parent[i]].push_back(i);  // increasing id
+  out.clear();
+  auto push = [&](NiceNode nd) {
+    out.push_back(nd);
+    return (int)out.size() - 1;
+  };
+  auto contains = [](const std::vector<int> &v, int u) {
+    return std::binary_search(v.begin(), v.end(), u);
+  };
+  // explicit post-order walk of the decomposition tree
+  std::vector<int> top(nb, -1);
+  std::vector<std::pair<int, size_t>> stack{{root, 0}};
+  while (!stack.empty()) {
+    int i = stack.back().first;
+    size_t &next = stack.back().second;
+    if (next < kids[i].size()) {
+      int c = kids[i][next++];
+      stack.push_back({c, 0});
+      continue;
+    }
+    stack.pop_back();
+    const std::vector<int> &B = bags[i];
+    if (kids[i].empty()) {
+      NiceNode leaf;
+      leaf.type = 0;
+      leaf.vertex = B[0];
+      leaf.bag = {B[0]};
+      int t = push(leaf);
+      for (size_t j = 1; j < B.size(); ++j) {
+        NiceNode in;
+        in.type = 1;
+        in.child0 = t;
+        in.vertex = B[j];
+        in.bag = out[t].bag;
+        in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), B[j]), B[j]);
+        t = push(in);
+      }
+      top[i] = t;
+      continue;
+    }
+    int acc = -1;
+    for (int c : kids[i]) {
+      int t = top[c];
+      for (int u : bags[c])  // forgets first, increasing vertex
+        if (!contains(B, u)) {
+          NiceNode f;
+          f.type = 2;
+          f.child0 = t;
+          f.vertex = u;
+          for (int w : out[t].bag)
+            if (w != u) f.bag.push_back(w);
+          t = push(f);
+        }
+      for (int u : B)  // then introduces, increasing vertex
+        if (!contains(bags[c], u)) {
+          NiceNode in;
+          in.type = 1;
+          in.child0 = t;
+          in.vertex = u;
+          in.bag = out[t].bag;
+          in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
+          t = push(in);
+        }
+      if (acc < 0) {
+        acc = t;
+      } else {  // left-deep join
+        NiceNode j;
+        j.type = 3;
+        j.child0 = acc;
+        j.child1 = t;
+        j.bag = out[acc].bag;
+        acc = push(j);
+      }
+    }
+    top[i] = acc;
+  }
+  int t = top[root];
+  for (int u : bags[root]) {  // empty-bag root of degree one
+    NiceNode f;
+    f.type = 2;
+    f.child0 = t;
+    f.vertex = u;
+    for (int w : out[t].bag)
+      if (w != u) f.bag.push_back(w);
+    t = push(f);
+  }
+  for (size_t i = 0; i < out.size(); ++i) {
+    if (out[i].child0 >= 0) out[out[i].child0].parent = (int)i;
+    if (out[i].child1 >= 0) out[out[i].child1].parent = (int)i;
+  }
+}
+
+// ---- minimum-width decomposition from elimination orderings (Section 3) -------------------
+// Exact dynamic programme over vertex subsets (Bodlaender, Fomin, Koster, Kratsch, Thilikos):
+// TW(S) = min over v in S of max(TW(S - v), |Q(S - v, v)|), where Q(S, v) holds the vertices
+// outside S + v reachable from v through S; the minimiser gives the elimination order.
+uint32_t q_set(const std::vector<uint32_t> &adj, uint32_t S, int v) {
+  uint32_t seen = 1u << v, reach = adj[v];
+  uint32_t inner = reach & S & ~seen;
+  while (inner) {
+    int x = __builtin_ctz(inner);
+    seen |= 1u << x;
+    reach |= adj[x];
+    inner = reach & S & ~seen;
+  }
+  return reach & ~S & ~(1u << v);
+}
+
+std::vector<int> exact_order(const std::vector<uint32_t> &adj, int n) {
+  size_t N = size_t(1) << n;
+  std::vector<int8_t> tw(N);
+  std::vector<uint8_t> arg(N);
+  tw[0] = -1;
+  for (size_t S = 1; S < N; ++S) {
+    int best = 127, bv = 0;
+    for (uint32_t rest = (uint32_t)S; rest; rest &= rest - 1) {
+      int v = __builtin_ctz(rest);
+      uint32_t Sm = (uint32_t)S & ~(1u << v);
+      int val = std::max<int>(tw[Sm], __builtin_popcount(q_set(adj, Sm, v)));
+      if (val < best) {
+        best = val;
+        bv = v;
+      }
+    }
+    tw[S] = (int8_t)best;
+    arg[S] = (uint8_t)bv;
+  }
+  std::vector<int> order(n);
+  uint32_t S = (uint32_t)(N - 1);
+  for (int i = n - 1; i >= 0; --i) {
+    order[i] = arg[S];
+    S &= ~(1u << arg[S]);
+  }
+  return order;
+}
+
+std::vector<int> min_fill_order(std::vector<uint32_t> adj, int n) {
+  std::vector<int> order;
+  uint32_t left = n == 32 ? ~0u : ((1u << n) - 1u);
+  while (left) {
+    int best = -1, bf = INT32_MAX;
+    for (uint32_t r = left; r; r &= r - 1) {
+      int v = __builtin_ctz(r);
+      uint32_t nb = adj[v] & left;
+      int fill = 0;
+      for (uint32_t a = nb; a; a &= a - 1) {
+        int x = __builtin_ctz(a);
+        fill += __builtin_popcount(nb & ~adj[x] & ~(1u << x));
+      }
+      if (fill < bf) {
+        bf = fill;
+        best = v;
+      }
+    }
+    uint32_t nb = adj[best] & left;
+    for (uint32_t a = nb; a; a &= a - 1) {
+      int x = __builtin_ctz(a);
+      adj[x] |= nb & ~(1u << x);
+    }
+    left &= ~(1u << best);
+    order.push_back(best);
+  }
+  return order;
+}
+
+void td_from_order(std::vector<uint32_t> adj, int n, const std::vector<int> &order,
+                   std::vector<std::vector<int>> &bags, std::vector<int> &parent) {
+  std::vector<int> pos(n);
+  for (int i = 0; i < n; ++i) pos[order[i]] = i;
+  std::vector<uint32_t> later(n);
+  for (int i = 0; i < n; ++i) {
+    int v = order[i];
+    uint32_t hi = 0;
+    for (uint32_t a = adj[v]; a; a &= a - 1) {
+      int x = __builtin_ctz(a);
+      if (pos[x] > i) hi |= 1u << x;
+    }
+    later[i] = hi;
+    for (uint32_t a = hi; a; a &= a - 1) {  // fill: the later neighbours become a clique
+      int x = __builtin_ctz(a);
+      adj[x] |= hi & ~(1u << x);
+    }
+  }
+  bags.assign(n, {});
+  parent.assign(n, -1);
+  int root = -1;
+  for (int i = 0; i < n; ++i) {
+    bags[i].push_back(order[i]);
+    int first = n;
+    for (uint32_t a = later[i]; a; a &= a - 1) {
+      int x = __builtin_ctz(a);
+      bags[i].push_back(x);
+      first = std::min(first, pos[x]);
+    }
+    parent[i] = first < n ? first : -1;
+  }
+  // bags without a parent belong to different components: hang them under the last one
+  for (int i = n - 1; i >= 0; --i)
+    if (parent[i] < 0) {
+      if (root < 0) root = i;
+      else parent[i] = root;
+    }
+}
+
+// ---- helpers ------------------------------------------------------------------------------
+template <typename T>
+T *arena_alloc(Ctx *c, size_t count) {
+  return (T *)c->arena.alloc(count * sizeof(T));
+}
+
+void free_run(Ctx *c, Run *r) {
+  for (auto &t : r->timings) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  r->timings.clear();
+  for (auto &t : r->tables)
+    if (t.slots) c->arena.release(t.slots);
+  r->tables.clear();
+  c->arena.release(r->d_counters);
+  c->arena.release(r->d_exists);
+  c->arena.release(r->d_count);
+  auto it = c->colorings.find(r->coloring);
+  if (it != c->colorings.end() && --it->second.refs == 0) {
+    c->arena.release(it->second.d_colors);
+    c->colorings.erase(it);
+  }
+}
+
+int ensure_scratch(Ctx *c, size_t words) {
+  if (c->scratch_words >= words) return CC_OK;
+  c->arena.release(c->d_scratch);
+  c->d_scratch = arena_alloc<u64>(c, words);
+  c->scratch_words = c->d_scratch ? words : 0;
+  return c->d_scratch ? CC_OK : CC_ENOMEM;
+}
+
+int read_u64(Ctx *c, const u64 *d, u64 *h) {
+  CUDA_OK(cudaMemcpyAsync(h, d, sizeof(u64), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CC_OK;
+}
+
+int pos_in(const std::vector<int32_t> &bag, int u) {
+  return (int)(std::lower_bound(bag.begin(), bag.end(), u) - bag.begin());
+}
+
+// ---- the planner: node by node in post-order, exact capacities ----------------------------
+int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
+  const int N = (int)P.nodes.size();
+  const int32_t n = c->n;
+  const float lf = R->opts.load_factor;
+  const int block = R->opts.block;
+  const int df = R->opts.degree_filter;
+  cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n};
+  R->tables.assign(N, {});
+  R->sizes.assign(N, 0);
+  std::vector<bool> made(N, false);
+  const int grid = cc::intro_grid(c->dev, block);
+  int rc = ensure_scratch(c, 2 * (size_t)grid + 8);
+  if (rc) return rc;
+  u64 *blk = c->d_scratch;
+  CUDA_OK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+
+  // every launch goes through `timed`: it counts the launch and, when profiling, brackets it
+  // with CUDA events on the context's stream
+  auto timed = [&](int node, int kind, int kernels, auto &&launch) -> int {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (R->opts.profile) {
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return CC_ECUDA;
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) return CC_ECUDA;
+    }
+    int r = check_launch(launch());
+    c->launches += kernels;
+    if (R->opts.profile) {
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess) return CC_ECUDA;
+      R->timings.push_back({node, kind, e0, e1, 0});
+    }
+    return r;
+  };
+  auto release_child = [&](int y) {
+    if (R->opts.retain || y < 0) return;
+    c->arena.release(R->tables[y].slots);
+    R->tables[y] = {};
+  };
+  auto desc = [&](int x) {
+    TableDesc t;
+    t.slots = R->tables[x].slots;
+    t.cap = R->tables[x].cap;
+    t.count = R->d_counters + x;
+    t.hashed = R->tables[x].hashed;
+    return t;
+  };
+  auto new_hash = [&](int x, u64 entries) -> int {
+    u64 cap = hash_cap(entries, lf);
+    void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+    if (!p) return CC_ENOMEM;
+    CUDA_OK(cudaMemsetAsync(p, 0, cap * cc::slot_bytes(R->kw), c->stream));
+    R->tables[x] = {p, cap, 1, true};
+    return CC_OK;
+  };
+
+  for (int x = 0; x < N; ++x) {
+    if (made[x]) continue;
+    const NiceNode &nd = P.nodes[x];
+    if (nd.type == 0) {  // leaf
+      u64 cap = std::max<u64>(1, (u64)n * (u64)R->trials);
+      void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+      if (!p) return CC_ENOMEM;
+      R->tables[x] = {p, cap, 1, true};
+      cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), c->d_err};
+      if (n == 0) CUDA_OK(cudaMemsetAsync(p, 0, cc::slot_bytes(R->kw), c->stream));
+      rc = timed(x, CC_K_LEAF, 1, [&] { return cc::launch_leaf(c->stream, c->dev, R->kw, a); });
+      if (rc) return rc;
+    } else if (nd.type == 1) {  // introduce
+      const int y = nd.child0;
+      const NiceNode &ch = P.nodes[y];
+      cc::IntroArgs a{};
+      a.G = G;
+      a.L = R->L;
+      a.in = desc(y);
+      a.b_in = (int)ch.bag.size();
+      a.p = pos_in(nd.bag, nd.vertex);
+      a.nnb = 0;
+      for (size_t s = 0; s < ch.bag.size(); ++s)
+        if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
+      a.degF = df ? P.deg[nd.vertex] : 0;
+      a.err = c->d_err;
+      a.valid = R->d_counters + x;
+      a.cand = blk + 2 * grid + 1;
+      CUDA_OK(cudaMemsetAsync(a.cand, 0, sizeof(u64), c->stream));
+      rc = timed(x, CC_K_INTRO_COUNT, 2, [&] {
+        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 0, block, a, blk);
+      });
+      if (rc) return rc;
+      u64 total = 0, cand = 0;
+      rc = read_u64(c, blk + 2 * grid, &total);
+      if (!rc) rc = read_u64(c, a.cand, &cand);
+      if (rc) return rc;
+      if (R->opts.profile) R->timings.back().candidates = cand;
+      R->sizes[x] = total;
+      const int f = nd.parent;
+      const bool fuse = R->opts.fuse && f >= 0 && P.nodes[f].type == 2;
+      if (fuse) {
+        rc = new_hash(f, total);
+        if (rc) return rc;
+        a.out = desc(f);
+        a.q = pos_in(nd.bag, P.nodes[f].vertex);
+        CUDA_OK(cudaMemsetAsync(R->d_counters + x, 0, sizeof(u64), c->stream));
+        rc = timed(x, CC_K_INTRO_FUSED, 1, [&] {
+          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, block, a, blk);
+        });
+        if (rc) return rc;
+        if (R->opts.profile) R->timings.back().candidates = cand;
+        made[f] = true;
+        release_child(y);
+        rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
+        if (rc) return rc;
+        if (f == N - 1) break;
+        continue;
+      }
+      u64 cap = std::max<u64>(1, total);
+      void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+      if (!p) return CC_ENOMEM;
+      R->tables[x] = {p, cap, 0, true};
+      a.out = desc(x);
+      CUDA_OK(cudaMemcpyAsync(R->d_counters + x, blk + 2 * grid, sizeof(u64),
+                              cudaMemcpyDeviceToDevice, c->stream));
+      rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
+        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, block, a, blk);
+      });
+      if (rc) return rc;
+      if (R->opts.profile) R->timings.back().candidates = cand;
+      release_child(y);
+      continue;  // size already known
+    } else if (nd.type == 2) {  // forget
+      const int y = nd.child0;
+      rc = new_hash(x, R->sizes[y]);
+      if (rc) return rc;
+      cc::ForgetArgs a{R->L, desc(y), (int)P.nodes[y].bag.size(),
+                       pos_in(P.nodes[y].bag, nd.vertex), desc(x), c->d_err};
+      rc = timed(x, CC_K_FORGET, 1,
+                 [&] { return cc::launch_forget(c->stream, c->dev, R->kw, block, a); });
+      if (rc) return rc;
+      release_child(y);
+    } else {  // join
+      int y = nd.child0, z = nd.child1;
+      if (R->sizes[y] > R->sizes[z]) std::swap(y, z);  // chain the smaller child
+      u64 icap = hash_cap(R->sizes[y], lf);
+      u64 bound_y = R->tables[y].hashed ? R->tables[y].cap : R->sizes[y];
+      void *index = c->arena.alloc(icap * cc::index_slot_bytes(R->kw));
+      u64 *next = arena_alloc<u64>(c, std::max<u64>(1, bound_y));
+      if (!index || !next) {
+        c->arena.release(index);
+        c->arena.release(next);
+        return CC_ENOMEM;
+      }
+      CUDA_OK(cudaMemsetAsync(index, 0, icap * cc::index_slot_bytes(R->kw), c->stream));
+      u64 *pairs = blk + 2 * grid + 2;
+      CUDA_OK(cudaMemsetAsync(pairs, 0, sizeof(u64), c->stream));
+      cc::JoinArgs a{};
+      a.G = G;
+      a.L = R->L;
+      a.build = desc(y);
+      a.probe = desc(z);
+      a.b = (int)nd.bag.size();
+      a.index = index;
+      a.index_cap = icap;
+      a.next = next;
+      a.pairs = pairs;
+      a.err = c->d_err;
+      rc = timed(x, CC_K_JOIN_BUILD, 1,
+                 [&] { return cc::launch_join(c->stream, c->dev, R->kw, 0, block, a); });
+      if (!rc)
+        rc = timed(x, CC_K_JOIN_COUNT, 1,
+                   [&] { return cc::launch_join(c->stream, c->dev, R->kw, 1, block, a); });
+      u64 np = 0;
+      if (!rc) rc = read_u64(c, pairs, &np);
+      if (!rc) rc = new_hash(x, np);
+      if (!rc) {
+        a.out = desc(x);
+        rc = timed(x, CC_K_JOIN_WRITE, 1,
+                   [&] { return cc::launch_join(c->stream, c->dev, R->kw, 2, block, a); });
+      }
+      c->arena.release(index);
+      c->arena.release(next);
+      if (rc) return rc;
+      release_child(y);
+      release_child(z);
+    }
+    rc = read_u64(c, R->d_counters + x, &R->sizes[x]);
+    if (rc) return rc;
+  }
+  // root test (Section 3.1): per trial, nonempty root table and the sum of its counts
+  cc::RootArgs ra{R->L, desc(N - 1), R->d_exists, R->d_count};
+  rc = timed(N - 1, CC_K_ROOT, 1, [&] { return cc::launch_root(c->stream, c->dev, R->kw, ra); });
+  if (rc) return rc;
+  int herr = 0;
+  CUDA_OK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  if (herr & cc::kErrTimeout) return CC_ETIMEOUT;
+  if (herr) return CC_ECAPACITY;
+  return CC_OK;
+}
+
+int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **out) {
+  auto pi = c->patterns.find(pid);
+  auto ci = c->colorings.find(cid);
+  if (pi == c->patterns.end() || ci == c->colorings.end()) return CC_ENOTFOUND;
+  const Pattern &P = pi->second;
+  cc::Coloring &col = ci->second;
+  if (col.k < P.nF) return CC_EINVAL;
+  std::unique_ptr<Run> R(new Run());
+  cc_default_opts(&R->opts);
+  if (opts) R->opts = *opts;
+  if (!(R->opts.load_factor > 0.f && R->opts.load_factor <= 0.9f)) R->opts.load_factor = 0.5f;
+  if (R->opts.block != 128 && R->opts.block != 256 && R->opts.block != 512) R->opts.block = 256;
+  R->pattern = pid;
+  R->coloring = cid;
+  R->trials = col.trials;
+  int bmax = 0;
+  for (auto &nd : P.nodes) bmax = std::max<int>(bmax, (int)nd.bag.size());
+  int nb = std::max(1, bits_for((u64)std::max(0, c->n - 1)));
+  int tb = col.trials > 1 ? bits_for((u64)(col.trials - 1)) : 0;
+  R->L.k = col.k;
+  R->L.nb = nb;
+  R->L.tpos = col.k + bmax * nb;
+  R->L.tb = tb;
+  int width = R->L.tpos + tb;
+  if (bmax > cc::kMaxBag || width > 128) return CC_EKEYWIDTH;
+  R->kw = width <= 64 ? 1 : 2;
+  const int N = (int)P.nodes.size();
+  col.refs++;  // released by free_run
+  R->d_counters = arena_alloc<u64>(c, N);
+  R->d_exists = arena_alloc<unsigned>(c, col.trials);
+  R->d_count = arena_alloc<u64>(c, col.trials);
+  if (!R->d_counters || !R->d_exists || !R->d_count) {
+    free_run(c, R.get());
+    return CC_ENOMEM;
+  }
+  CUDA_OK(cudaMemsetAsync(R->d_counters, 0, N * sizeof(u64), c->stream));
+  CUDA_OK(cudaMemsetAsync(R->d_exists, 0, col.trials * sizeof(unsigned), c->stream));
+  CUDA_OK(cudaMemsetAsync(R->d_count, 0, col.trials * sizeof(u64), c->stream));
+  R->retained = R->opts.retain != 0;
+  int rc = run_plan(c, R.get(), P, col);
+  if (rc) {
+    free_run(c, R.get());
+    return rc;
+  }
+  *out = R.release();
+  return CC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *cc_strerror(int code) {
+  switch (code) {
+    case CC_OK: return "ok";
+    case CC_EINVAL: return "invalid argument";
+    case CC_ENOMEM: return "device arena exhausted";
+    case CC_ECAPACITY: return "table capacity exceeded";
+    case CC_ETIMEOUT: return "bounded wait timed out";
+    case CC_ECUDA: return "CUDA runtime error";
+    case CC_ENOTFOUND: return "unknown id";
+    case CC_EKEYWIDTH: return "trial, bag-mapping and colour bits exceed 128";
+    default: return "unknown error";
+  }
+}
+
+void cc_default_opts(cc_run_opts *o) {
+  o->degree_filter = 1;
+  o->retain = 0;
+  o->fuse = 1;
+  o->use_graph = 0;
+  o->load_factor = 0.5f;
+  o->block = 256;
+  o->profile = 0;
+}
+
+int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
+  if (!out || arena_bytes == 0) return CC_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) return CC_ECUDA;
+  if (device < 0 || device >= ndev) return CC_EINVAL;
+  CUDA_OK(cudaSetDevice(device));
+  Ctx *c = new Ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaDeviceGetAttribute(&c->dev.sms, cudaDevAttrMultiProcessorCount, device) !=
+      cudaSuccess) {
+    delete c;
+    return CC_ECUDA;
+  }
+  c->dev.blocks_per_sm = 8;
+  char *base = (char *)d_arena;
+  if (!base) {
+    if (cudaMalloc(&c->owned_arena, arena_bytes) != cudaSuccess) {
+      delete c;
+      return CC_ENOMEM;
+    }
+    base = c->owned_arena;
+  }
+  c->arena.init(base, arena_bytes);
+  c->d_err = arena_alloc<int>(c, 1);
+  if (!c->d_err || ensure_scratch(c, 4096)) {
+    if (c->owned_arena) cudaFree(c->owned_arena);
+    delete c;
+    return CC_ENOMEM;
+  }
+  *out = (cc_ctx *)c;
+  return CC_OK;
+}
+
+int cc_serve_stop(cc_ctx *ctx);
+
+int cc_destroy(cc_ctx *ctx) {
+  if (!ctx) return CC_EINVAL;
+  Ctx *c = (Ctx *)ctx;
+  cc_serve_stop(ctx);
+  cudaStreamSynchronize(c->stream);
+  if (c->owned_arena) cudaFree(c->owned_arena);
+  delete c;
+  return CC_OK;
+}
+
+int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || n < 0 || !h_row_ptr) return CC_EINVAL;
+  if (h_row_ptr[0] != 0) return CC_EINVAL;
+  for (int32_t v = 0; v < n; ++v)
+    if (h_row_ptr[v + 1] < h_row_ptr[v]) return CC_EINVAL;
+  const int64_t m2 = h_row_ptr[n];
+  if (m2 > 0 && !h_col) return CC_EINVAL;
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t j = h_row_ptr[v]; j < h_row_ptr[v + 1]; ++j) {
+      int32_t w = h_col[j];
+      if (w < 0 || w >= n || w == v) return CC_EINVAL;
+      if (j > h_row_ptr[v] && h_col[j - 1] >= w) return CC_EINVAL;  // sorted, no duplicates
+      if (!std::binary_search(h_col + h_row_ptr[w], h_col + h_row_ptr[w + 1], v))
+        return CC_EINVAL;  // symmetric
+    }
+  // a new graph invalidates runs and colourings
+  for (auto &r : c->runs) free_run(c, r.second.get());
+  c->runs.clear();
+  for (auto &col : c->colorings) c->arena.release(col.second.d_colors);
+  c->colorings.clear();
+  c->arena.release(c->d_row_ptr);
+  c->arena.release(c->d_col);
+  c->d_row_ptr = arena_alloc<int32_t>(c, (size_t)n + 1);
+  c->d_col = arena_alloc<int32_t>(c, std::max<int64_t>(1, m2));
+  if (!c->d_row_ptr || !c->d_col) {
+    c->n = -1;
+    return CC_ENOMEM;
+  }
+  CUDA_OK(cudaMemcpyAsync(c->d_row_ptr, h_row_ptr, ((size_t)n + 1) * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, c->stream));
+  if (m2 > 0)
+    CUDA_OK(cudaMemcpyAsync(c->d_col, h_col, (size_t)m2 * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, c->stream));
+  c->h_row_ptr.assign(h_row_ptr, h_row_ptr + n + 1);
+  c->h_col.assign(h_col, h_col + m2);
+  c->n = n;
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CC_OK;
+}
+
+int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
+                    const cc_td *td, int32_t *pattern_id) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || nF < 1 || nF > 32 || mF < 0 || (mF > 0 && !h_edges) || !pattern_id) return CC_EINVAL;
+  Pattern P;
+  P.nF = nF;
+  P.adj.assign(nF, 0u);
+  P.deg.assign(nF, 0);
+  for (int32_t i = 0; i < mF; ++i) {
+    int32_t a = h_edges[2 * i], b = h_edges[2 * i + 1];
+    if (a < 0 || b < 0 || a >= nF || b >= nF || a == b) return CC_EINVAL;
+    if (P.adj[a] >> b & 1u) continue;
+    P.adj[a] |= 1u << b;
+    P.adj[b] |= 1u << a;
+    P.deg[a]++;
+    P.deg[b]++;
+  }
+  std::vector<std::vector<int>> bags;
+  std::vector<int> parent;
+  if (td) {
+    if (td->num_bags < 1 || !td->h_bag_ptr || !td->h_parent) return CC_EINVAL;
+    bags.resize(td->num_bags);
+    parent.assign(td->h_parent, td->h_parent + td->num_bags);
+    for (int32_t i = 0; i < td->num_bags; ++i) {
+      int32_t b0 = td->h_bag_ptr[i], b1 = td->h_bag_ptr[i + 1];
+      if (b1 < b0) return CC_EINVAL;
+      bags[i].assign(td->h_bag_vtx + b0, td->h_bag_vtx + b1);
+    }
+  } else {
+    std::vector<int> order = nF <= 20 ? exact_order(P.adj, nF) : min_fill_order(P.adj, nF);
+    td_from_order(P.adj, nF, order, bags, parent);
+  }
+  int root = -1;
+  if (!valid_td(P.adj, nF, bags, parent, root)) return CC_EINVAL;
+  build_nice(bags, parent, root, P.nodes);
+  for (auto &nd : P.nodes) P.width = std::max<int>(P.width, (int)nd.bag.size() - 1);
+  int32_t id = c->next_pattern++;
+  c->patterns[id] = std::move(P);
+  *pattern_id = id;
+  return CC_OK;
+}
+
+int cc_pattern_info(cc_ctx *ctx, int32_t pid, int32_t *num_nodes, int32_t *width) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  auto it = c->patterns.find(pid);
+  if (it == c->patterns.end()) return CC_ENOTFOUND;
+  if (num_nodes) *num_nodes = (int32_t)it->second.nodes.size();
+  if (width) *width = it->second.width;
+  return CC_OK;
+}
+
+int cc_pattern_nodes(cc_ctx *ctx, int32_t pid, int32_t *type, int32_t *child0, int32_t *child1,
+                     int32_t *vertex, int32_t *bag_ptr, int32_t *bag_vtx) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  auto it = c->patterns.find(pid);
+  if (it == c->patterns.end()) return CC_ENOTFOUND;
+  int32_t off = 0;
+  const auto &nodes = it->second.nodes;
+  for (size_t i = 0; i < nodes.size(); ++i) {
+    if (type) type[i] = nodes[i].type;
+    if (child0) child0[i] = nodes[i].child0;
+    if (child1) child1[i] = nodes[i].child1;
+    if (vertex) vertex[i] = nodes[i].vertex;
+    if (bag_ptr) bag_ptr[i] = off;
+    for (int u : nodes[i].bag) {
+      if (bag_vtx) bag_vtx[off] = u;
+      ++off;
+    }
+  }
+  if (bag_ptr) bag_ptr[nodes.size()] = off;
+  return CC_OK;
+}
+
+int cc_color(cc_ctx *ctx, uint64_t seed, int32_t trials, int32_t k, int32_t *cid) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || c->n < 0 || trials < 1 || k < 1 || k > 32 || !cid) return CC_EINVAL;
+  cc::Coloring col;
+  col.trials = trials;
+  col.k = k;
+  col.d_colors = arena_alloc<uint8_t>(c, std::max<size_t>(1, (size_t)trials * c->n));
+  if (!col.d_colors) return CC_ENOMEM;
+  if (check_launch(cc::launch_color(c->stream, c->dev, col.d_colors, c->n, trials, k, seed))) {
+    c->arena.release(col.d_colors);
+    return CC_ECUDA;
+  }
+  if ((size_t)trials * c->n > 0) c->launches++;
+  int32_t id = c->next_coloring++;
+  c->colorings[id] = col;
+  *cid = id;
+  return CC_OK;
+}
+
+int cc_set_colors(cc_ctx *ctx, const uint8_t *h_colors, int32_t trials, int32_t k,
+                  int32_t *cid) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || c->n < 0 || trials < 1 || k < 1 || k > 32 || !cid) return CC_EINVAL;
+  size_t total = (size_t)trials * c->n;
+  if (total && !h_colors) return CC_EINVAL;
+  for (size_t i = 0; i < total; ++i)
+    if (h_colors[i] >= k) return CC_EINVAL;
+  cc::Coloring col;
+  col.trials = trials;
+  col.k = k;
+  col.d_colors = arena_alloc<uint8_t>(c, std::max<size_t>(1, total));
+  if (!col.d_colors) return CC_ENOMEM;
+  if (total)
+    CUDA_OK(cudaMemcpyAsync(col.d_colors, h_colors, total, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  int32_t id = c->next_coloring++;
+  c->colorings[id] = col;
+  *cid = id;
+  return CC_OK;
+}
+
+int cc_get_colors(cc_ctx *ctx, int32_t cid, uint8_t *h_out) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !h_out) return CC_EINVAL;
+  auto it = c->colorings.find(cid);
+  if (it == c->colorings.end()) return CC_ENOTFOUND;
+  size_t total = (size_t)it->second.trials * c->n;
+  if (total)
+    CUDA_OK(cudaMemcpyAsync(h_out, it->second.d_colors, total, cudaMemcpyDeviceToHost,
+                            c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CC_OK;
+}
+
+int cc_release_colors(cc_ctx *ctx, int32_t cid) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  auto it = c->colorings.find(cid);
+  if (it == c->colorings.end()) return CC_ENOTFOUND;
+  if (--it->second.refs == 0) {
+    c->arena.release(it->second.d_colors);
+    c->colorings.erase(it);
+  }
+  return CC_OK;
+}
+
+int cc_run_dp(cc_ctx *ctx, int32_t pid, int32_t cid, const cc_run_opts *opts, int32_t *run_id) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !run_id || c->n < 0) return CC_EINVAL;
+  Run *R = nullptr;
+  int rc = make_run(c, pid, cid, opts, &R);
+  if (rc) return rc;
+  int32_t id = c->next_run++;
+  c->runs[id].reset(R);
+  *run_id = id;
+  return CC_OK;
+}
+
+int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *pids, const int32_t *cids,
+                 const cc_run_opts *opts, int32_t *run_ids) {
+  if (!ctx || npat < 0 || (npat && (!pids || !cids || !run_ids))) return CC_EINVAL;
+  for (int32_t i = 0; i < npat; ++i) {
+    int rc = cc_run_dp(ctx, pids[i], cids[i], opts, &run_ids[i]);
+    if (rc) {
+      for (int32_t j = 0; j < i; ++j) cc_release(ctx, run_ids[j]);
+      return rc;
+    }
+  }
+  return CC_OK;
+}
+
+static Run *find_run(Ctx *c, int32_t id) {
+  auto it = c->runs.find(id);
+  return it == c->runs.end() ? nullptr : it->second.get();
+}
+
+int cc_release(cc_ctx *ctx, int32_t run_id);
+
+int cc_decide(cc_ctx *ctx, int32_t run_id, uint8_t *h_exists) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !h_exists) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  std::vector<unsigned> e(R->trials);
+  CUDA_OK(cudaMemcpyAsync(e.data(), R->d_exists, R->trials * sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (int32_t t = 0; t < R->trials; ++t) h_exists[t] = e[t] ? 1 : 0;
+  return CC_OK;
+}
+
+int cc_count(cc_ctx *ctx, int32_t run_id, uint64_t *h_counts) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !h_counts) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  CUDA_OK(cudaMemcpyAsync(h_counts, R->d_count, R->trials * sizeof(u64),
+                          cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  return CC_OK;
+}
+
+int cc_table_stats(cc_ctx *ctx, int32_t run_id, uint64_t *h_sizes, uint64_t *h_total) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  u64 tot = 0;
+  for (size_t i = 0; i < R->sizes.size(); ++i) {
+    if (h_sizes) h_sizes[i] = R->sizes[i];
+    tot += R->sizes[i];
+  }
+  if (h_total) *h_total = tot;
+  return CC_OK;
+}
+
+int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity, int32_t *h_trial,
+                  int32_t *h_phi, uint32_t *h_mask, uint64_t *h_cnt, uint64_t *n_out) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !n_out) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  if (node < 0 || node >= (int32_t)R->tables.size()) return CC_EINVAL;
+  const cc::NodeTable &t = R->tables[node];
+  if (!t.stored || !t.slots) return CC_EINVAL;
+  const Pattern &P = c->patterns[R->pattern];
+  const int b = (int)P.nodes[node].bag.size();
+  const u64 m = R->sizes[node];
+  *n_out = m;
+  if (m > capacity) return CC_ECAPACITY;
+  if (m == 0) return CC_OK;
+  const size_t bytes = m * (sizeof(int32_t) * (1 + (size_t)b) + sizeof(uint32_t) + sizeof(u64)) + 64;
+  char *buf = (char *)c->arena.alloc(bytes + 512);
+  if (!buf) return CC_ENOMEM;
+  u64 *d_n = (u64 *)buf;
+  int32_t *d_trial = (int32_t *)(buf + 256);
+  int32_t *d_phi = d_trial + m;
+  uint32_t *d_mask = (uint32_t *)(d_phi + m * b);
+  u64 *d_cnt = (u64 *)(((uintptr_t)(d_mask + m) + 7) & ~uintptr_t(7));
+  int rc = CC_OK;
+  TableDesc td{t.slots, t.cap, R->d_counters + node, t.hashed};
+  if (cudaMemsetAsync(d_n, 0, sizeof(u64), c->stream) != cudaSuccess ||
+      cc::launch_unpack(c->stream, c->dev, R->kw, R->L, td, b, m, d_trial, d_phi, d_mask, d_cnt,
+                        d_n) != 0) {
+    rc = CC_ECUDA;
+  } else {
+    cudaMemcpyAsync(h_trial, d_trial, m * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (b) cudaMemcpyAsync(h_phi, d_phi, m * b * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(h_mask, d_mask, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(h_cnt, d_cnt, m * sizeof(u64), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CC_ECUDA;
+  }
+  c->arena.release(buf);
+  return rc;
+}
+
+int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, uint64_t *n_out,
+                 uint64_t *n_total) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !n_out || !n_total || (limit && !h_out)) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  if (!R->retained || R->opts.fuse) return CC_EINVAL;
+  return cc::enumerate_run(c, R, limit, h_out, n_out, n_total);
+}
+
+int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,
+                   int32_t *h_kind, float *h_ms, uint64_t *h_cand, int32_t *n_out) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !n_out) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  *n_out = (int32_t)R->timings.size();
+  if ((int32_t)R->timings.size() > capacity) return CC_ECAPACITY;
+  for (size_t i = 0; i < R->timings.size(); ++i) {
+    const auto &t = R->timings[i];
+    float ms = 0.f;
+    CUDA_OK(cudaEventSynchronize(t.stop));
+    CUDA_OK(cudaEventElapsedTime(&ms, t.start, t.stop));
+    if (h_node) h_node[i] = t.node;
+    if (h_kind) h_kind[i] = t.kind;
+    if (h_ms) h_ms[i] = ms;
+    if (h_cand) h_cand[i] = t.candidates;
+  }
+  return CC_OK;
+}
+
+int cc_context_stats(cc_ctx *ctx, uint64_t *launches, uint64_t *used, uint64_t *size) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  if (launches) *launches = c->launches;
+  if (used) *used = c->arena.size() - c->arena.free_bytes();
+  if (size) *size = c->arena.size();
+  return CC_OK;
+}
+
+int cc_release(cc_ctx *ctx, int32_t run_id) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  auto it = c->runs.find(run_id);
+  if (it == c->runs.end()) return CC_ENOTFOUND;
+  free_run(c, it->second.get());
+  c->runs.erase(it);
+  return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal types shared by the host runtime (cc_host.cpp) and the device kernels
+// (cc_kernels.cu).  Not part of the public ABI (include/cc.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace cc {
+
+constexpr int kMaxBag = 8;  // largest bag |V_x| handled by the kernels (treewidth <= 7)
+
+// device error word bits (OR-ed by kernels, read by the host after a run)
+constexpr int kErrOverflow = 1;   // an append table or hash table ran out of slots
+constexpr int kErrProbe = 2;      // a hash probe sequence wrapped the whole table
+constexpr int kErrTimeout = 4;    // a bounded device wait gave up
+
+// Bit layout of a packed table key (64 or 128 bits):
+//   bits [0, k)                 colour set C (bit i = colour i)
+//   bits [k + i*nb, k+(i+1)*nb) G-vertex of bag slot i (slots in increasing F-vertex order)
+//   bits [tpos, tpos + tb)      trial index
+// A valid key never has C == 0, so the all-zero key marks an empty hash slot.
+struct KeyLayout {
+  int k;     // colours
+  int nb;    // bits per vertex id
+  int tpos;  // first trial bit = k + max_bag * nb
+  int tb;    // trial bits
+};
+
+// One table: `slots` holds Slot64 (key, count) or Slot128 (key, count, pad) records.  A dense
+// table holds its entries in [0, min(*count, cap)); a hashed table has holes (key 0) anywhere
+// in [0, cap) and *count is its number of distinct keys.
+struct TableDesc {
+  void *slots;
+  unsigned long long cap;
+  unsigned long long *count;  // device counter
+  int hashed;
+};
+
+struct GraphDev {
+  const int32_t *row_ptr;  // n + 1
+  const int32_t *col;      // row_ptr[n]
+  const uint8_t *colors;   // trials * n
+  int32_t n;
+};
+
+struct LeafArgs {
+  GraphDev G;
+  KeyLayout L;
+  int trials;
+  int degF;  // minimum host degree (degree filter), 0 = off
+  TableDesc out;
+  int *err;
+};
+
+struct IntroArgs {
+  GraphDev G;
+  KeyLayout L;
+  TableDesc in;
+  int b_in;                  // child bag size
+  int p;                     // slot of the introduced vertex u in the new bag
+  int nnb;                   // bag neighbours of u in F[V_x]
+  int nb_slot[kMaxBag];      // their slots in the child bag
+  int degF;                  // minimum host degree of u's image (0 = off)
+  TableDesc out;             // dense (mode 1) or hashed (mode 2) output
+  int q;                     // mode 2: slot (in the new bag) of the vertex the parent forgets
+  unsigned long long *valid; // mode 2: number of introduce entries produced
+  unsigned long long *cand;  // mode 0: number of candidate vertices examined
+  int *err;
+};
+
+struct ForgetArgs {
+  KeyLayout L;
+  TableDesc in;
+  int b_in;
+  int q;  // slot of the forgotten vertex in the child bag
+  TableDesc out;
+  int *err;
+};
+
+struct JoinArgs {
+  GraphDev G;
+  KeyLayout L;
+  TableDesc build;      // child whose entries are chained by bag mapping
+  TableDesc probe;      // the other child
+  int b;                // bag size
+  void *index;          // hashed (phi-key, head) records, capacity index_cap
+  unsigned long long index_cap;
+  unsigned long long *next;  // per build slot: next chained slot + 1 (0 ends a chain)
+  TableDesc out;        // hashed output (mode 1)
+  unsigned long long *pairs;  // mode 0: number of matching (C', C'') pairs
+  int *err;
+};
+
+struct RootArgs {
+  KeyLayout L;
+  TableDesc in;
+  unsigned int *exists;      // per trial
+  unsigned long long *count; // per trial
+};
+
+// launch configuration derived once per device
+struct DevInfo {
+  int sms = 0;
+  int blocks_per_sm = 4;
+};
+
+// ---- launchers (cc_kernels.cu); return a cudaError_t as int ---------------------------------
+int launch_color(cudaStream_t s, const DevInfo &d, uint8_t *out, int32_t n, int32_t trials,
+                 int32_t k, uint64_t seed);
+int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a);
+// Introduce in three modes: 0 counts valid extensions per block into blk[0, grid) and writes
+// exclusive bases to blk[grid, 2*grid) and the total to blk[2*grid]; 1 writes them densely at
+// those bases; 2 adds them, projected by the parent forget, into a hashed table.  Modes 0 and 1
+// of one node must use the same block size (and so the same grid).
+int intro_grid(const DevInfo &d, int block);
+int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int block,
+                     const IntroArgs &a, unsigned long long *blk);
+int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
+int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
+                const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write
+int launch_root(cudaStream_t s, const DevInfo &d, int kw, const RootArgs &a);
+int launch_unpack(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L,
+                  const TableDesc &t, int b, unsigned long long cap, int32_t *trial,
+                  int32_t *phi, uint32_t *mask, unsigned long long *cnt,
+                  unsigned long long *n_out);
+
+size_t slot_bytes(int kw);       // bytes of one table record for 1- or 2-word keys
+size_t index_slot_bytes(int kw); // bytes of one join-index record
+
+}  // namespace cc

@@ -1,0 +1,699 @@
+// Device kernels of the colour-coding dynamic programme (arXiv 1908.11248, Sections 2.1, 3.1).
+//
+// Tables are arrays of (packed key, uint64 count) records.  A key packs the trial index, the bag
+// mapping phi (one G-vertex id per bag slot, slots in increasing F-vertex order, Section 3.2)
+// and the colour set C (bit i = colour i, Section 3.2) into 64 or 128 bits, so that a whole key
+// can be compared, hashed and claimed with one compare-and-swap.  All trials of a colouring live
+// in the same tables, so one launch per node serves every trial.
+//
+// Node rules (Section 3.1, "Dynamic Programming Description"), extended from the Boolean table to
+// counts of colourful embeddings mod 2^64:
+//   leaf      (u)       : (phi = (v), C = {zeta(v)}) with count 1 for every host vertex v
+//   introduce (u)       : (phi' + u->v, C' + zeta(v)) for every child entry and candidate v with
+//                         zeta(v) not in C' and every edge of F[V_x] at u present in G
+//   forget    (u)       : (phi' restricted to V_x, C), counts of equal results summed
+//   join      (y, z)    : (phi, C' | C''), count c' * c'', whenever C' & C'' is exactly the colour
+//                         set of phi's image; equal results summed
+//   root                : a colourful copy exists iff the root table is nonempty; the count is
+//                         the sum of the root counts
+#include <climits>
+#include <cstdint>
+
+#include "cc_internal.h"
+
+namespace cc {
+namespace {
+
+typedef unsigned long long u64;
+typedef unsigned __int128 u128;
+
+template <typename K>
+struct alignas(sizeof(K) == 8 ? 16 : 32) Slot {
+  K key;
+  u64 cnt;
+};
+
+// ---- key helpers ------------------------------------------------------------------------
+template <typename K>
+__device__ __forceinline__ K low_mask(int s) {
+  return s >= (int)(8 * sizeof(K)) ? ~(K)0 : (((K)1 << s) - (K)1);
+}
+
+template <typename K>
+__device__ __forceinline__ int key_slot(K key, const KeyLayout &L, int i) {
+  return (int)((key >> (L.k + i * L.nb)) & (K)((1ull << L.nb) - 1ull));
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t key_mask(K key, const KeyLayout &L) {
+  return (uint32_t)(key & (K)((1ull << L.k) - 1ull));
+}
+
+template <typename K>
+__device__ __forceinline__ int key_trial(K key, const KeyLayout &L) {
+  return L.tb ? (int)(key >> L.tpos) : 0;
+}
+
+template <typename K>
+__device__ __forceinline__ K key_trial_bits(K key, const KeyLayout &L) {
+  return L.tb ? (key >> L.tpos) << L.tpos : (K)0;
+}
+
+// insert vertex v as slot p of a bag that had b slots
+template <typename K>
+__device__ __forceinline__ K key_insert(K key, const KeyLayout &L, int p, int v) {
+  K body = key & low_mask<K>(L.tpos);
+  int lo = L.k + p * L.nb;
+  K lower = body & low_mask<K>(lo);
+  K upper = body >> lo;
+  return lower | ((K)(unsigned)v << lo) | (upper << (lo + L.nb)) | key_trial_bits(key, L);
+}
+
+// drop slot q
+template <typename K>
+__device__ __forceinline__ K key_remove(K key, const KeyLayout &L, int q) {
+  K body = key & low_mask<K>(L.tpos);
+  int lo = L.k + q * L.nb;
+  K lower = body & low_mask<K>(lo);
+  K upper = body >> (lo + L.nb);
+  return lower | (upper << lo) | key_trial_bits(key, L);
+}
+
+// MurmurHash3 64-bit finaliser (Appleby), a published bit mixer
+__device__ __forceinline__ u64 fmix64(u64 x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+__device__ __forceinline__ u64 key_hash(u64 k) { return fmix64(k); }
+__device__ __forceinline__ u64 key_hash(u128 k) { return fmix64((u64)k ^ fmix64((u64)(k >> 64))); }
+
+// ---- record load/store (16-byte vector accesses) ---------------------------------------
+__device__ __forceinline__ void load_slot(const Slot<u64> *s, u64 i, u64 &key, u64 &cnt) {
+  ulonglong2 r = reinterpret_cast<const ulonglong2 *>(s)[i];
+  key = r.x;
+  cnt = r.y;
+}
+__device__ __forceinline__ void load_slot(const Slot<u128> *s, u64 i, u128 &key, u64 &cnt) {
+  const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(s) + 2 * i;
+  ulonglong2 a = p[0];
+  key = ((u128)a.y << 64) | a.x;
+  cnt = p[1].x;
+}
+__device__ __forceinline__ void store_slot(Slot<u64> *s, u64 i, u64 key, u64 cnt) {
+  reinterpret_cast<ulonglong2 *>(s)[i] = make_ulonglong2(key, cnt);
+}
+__device__ __forceinline__ void store_slot(Slot<u128> *s, u64 i, u128 key, u64 cnt) {
+  ulonglong2 *p = reinterpret_cast<ulonglong2 *>(s) + 2 * i;
+  p[0] = make_ulonglong2((u64)key, (u64)(key >> 64));
+  p[1] = make_ulonglong2(cnt, 0ull);
+}
+
+template <typename K>
+__device__ __forceinline__ u64 table_bound(const TableDesc &t) {
+  if (t.hashed) return t.cap;
+  u64 c = *t.count;
+  return c < t.cap ? c : t.cap;
+}
+
+// ---- hash table (open addressing, linear probing, key claimed by compare-and-swap) -------
+// Returns 1 if the key was new, 0 if it was present, -1 if the table is full.
+__device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 capmask, u64 key, u64 c) {
+  u64 h = key_hash(key) & capmask;
+  for (u64 probe = 0; probe <= capmask; ++probe) {
+    u64 cur = *reinterpret_cast<volatile u64 *>(&slots[h].key);  // 8-byte reads are atomic
+    if (cur == key) {
+      atomicAdd(&slots[h].cnt, c);
+      return 0;
+    }
+    if (cur == 0) {
+      u64 old = atomicCAS(&slots[h].key, 0ull, key);
+      if (old == 0) {
+        atomicAdd(&slots[h].cnt, c);
+        return 1;
+      }
+      if (old == key) {
+        atomicAdd(&slots[h].cnt, c);
+        return 0;
+      }
+    }
+    h = (h + 1) & capmask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 capmask, u128 key, u64 c) {
+  u64 h = key_hash(key) & capmask;
+  for (u64 probe = 0; probe <= capmask; ++probe) {
+    // a 16-byte plain read is not guaranteed to be single-copy atomic: always compare-and-swap
+    u128 old = atomicCAS(&slots[h].key, (u128)0, key);
+    if (old == 0) {
+      atomicAdd(&slots[h].cnt, c);
+      return 1;
+    }
+    if (old == key) {
+      atomicAdd(&slots[h].cnt, c);
+      return 0;
+    }
+    h = (h + 1) & capmask;
+  }
+  return -1;
+}
+
+// find-or-insert; returns the slot index or -1 if the table is full
+template <typename K>
+__device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 capmask, K key) {
+  u64 h = key_hash(key) & capmask;
+  for (u64 probe = 0; probe <= capmask; ++probe) {
+    K old = atomicCAS(&slots[h].key, (K)0, key);
+    if (old == 0 || old == key) return (long long)h;
+    h = (h + 1) & capmask;
+  }
+  return -1;
+}
+
+// lookup in a table no thread is writing; -1 if absent
+template <typename K>
+__device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 capmask, K key) {
+  u64 h = key_hash(key) & capmask;
+  for (u64 probe = 0; probe <= capmask; ++probe) {
+    K cur;
+    u64 c;
+    load_slot(slots, h, cur, c);
+    if (cur == key) return (long long)h;
+    if (cur == 0) return -1;
+    h = (h + 1) & capmask;
+  }
+  return -1;
+}
+
+// ---- block reductions -------------------------------------------------------------------
+template <int BLOCK>
+__device__ __forceinline__ u64 block_sum(u64 v, u64 *s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_red[w] = v;
+  __syncthreads();
+  u64 t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < BLOCK / 32; ++i) t += s_red[i];
+  return t;  // valid in thread 0
+}
+
+// exclusive prefix of per-thread 64-bit values; s_off[BLOCK] receives the total
+template <int BLOCK>
+__device__ __forceinline__ void block_exclusive_scan(long long v, long long *s_off,
+                                                     long long *s_warp) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    long long s = lane < BLOCK / 32 ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < BLOCK / 32) s_warp[lane] = s;  // inclusive warp totals
+  }
+  __syncthreads();
+  long long before = (w ? s_warp[w - 1] : 0) + x - v;
+  s_off[threadIdx.x] = before;
+  if (threadIdx.x == BLOCK - 1) s_off[BLOCK] = before + v;
+  __syncthreads();
+}
+
+// exclusive rank of a flag within the block (deterministic order), and the block's count
+template <int BLOCK>
+__device__ __forceinline__ int block_flag_rank(bool f, int *s_wc, int &total) {
+  unsigned bal = __ballot_sync(0xffffffffu, f);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // previous readers of s_wc are done
+  if (lane == 0) s_wc[w] = __popc(bal);
+  __syncthreads();
+  int before = 0;
+  total = 0;
+  for (int i = 0; i < BLOCK / 32; ++i) {
+    int c = s_wc[i];
+    before += i < w ? c : 0;
+    total += c;
+  }
+  return before + __popc(bal & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ bool adjacent(const GraphDev &G, int a, int v) {
+  int lo = G.row_ptr[a], hi = G.row_ptr[a + 1];
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    int c = __ldg(G.col + mid);
+    if (c < v) lo = mid + 1;
+    else if (c > v) hi = mid;
+    else return true;
+  }
+  return false;
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) and the colouring of Section 2.1 -----------------
+__global__ void color_kernel(uint8_t *out, int32_t n, int32_t trials, int32_t k, uint32_t key0,
+                             uint32_t key1) {
+  u64 total = (u64)n * (u64)trials;
+  for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
+       i += (u64)gridDim.x * blockDim.x) {
+    uint32_t t = (uint32_t)(i / (u64)n), v = (uint32_t)(i % (u64)n);
+    uint32_t x0 = v, x1 = t, x2 = 0u, x3 = 0u;
+    uint32_t k0 = key0, k1 = key1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+      uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+      uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+      x0 = n0;
+      x1 = lo1;
+      x2 = n2;
+      x3 = lo0;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    out[i] = (uint8_t)(((u64)x0 * (u64)(uint32_t)k) >> 32);
+  }
+}
+
+// ---- leaf: one record per (trial, host vertex); filtered vertices leave an empty slot -------
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) leaf_kernel(LeafArgs a) {
+  __shared__ u64 s_red[BLOCK / 32];
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const u64 n = (u64)a.G.n, total = n * (u64)a.trials;
+  u64 made = 0;
+  for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < total; i += (u64)gridDim.x * BLOCK) {
+    int t = (int)(i / n), v = (int)(i % n);
+    K key = 0;
+    if (a.degF == 0 || a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF) {
+      int c = a.G.colors[i];
+      key = ((K)1 << c) | ((K)(unsigned)v << a.L.k);
+      if (a.L.tb) key |= (K)(unsigned)t << a.L.tpos;
+      ++made;
+    }
+    store_slot(out, i, key, key ? 1ull : 0ull);
+  }
+  u64 s = block_sum<BLOCK>(made, s_red);
+  if (threadIdx.x == 0 && s) atomicAdd(a.out.count, s);
+}
+
+// ---- introduce ---------------------------------------------------------------------------
+// Each block takes BLOCK child entries at a time, lays their candidate lists (the adjacency of
+// the bag neighbour whose image has the smallest degree, or all of V(G) when u has no bag
+// neighbour) end to end with a block prefix sum, and walks the concatenation with all threads,
+// so a hub's list is shared by the whole block.
+//   MODE 0: count the valid extensions per block (blk_count[blockIdx.x])
+//   MODE 1: write them densely at blk_base[blockIdx.x] + block-local rank (deterministic order)
+//   MODE 2: project out slot q (the parent forget) and add into the hashed output
+template <typename K, int MODE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_count,
+                                                      const u64 *blk_base) {
+  __shared__ long long s_off[BLOCK + 1];
+  __shared__ long long s_warp[BLOCK / 32];
+  __shared__ K s_key[BLOCK];
+  __shared__ u64 s_cnt[BLOCK];
+  __shared__ int s_rs[BLOCK];
+  __shared__ int s_anc[BLOCK];
+  __shared__ int s_wc[BLOCK / 32];
+  __shared__ u64 s_red[BLOCK / 32];
+
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const u64 bound = table_bound<K>(a.in);
+  const u64 capmask = a.out.cap - 1;
+  u64 produced = 0, fresh = 0, examined = 0;
+  u64 cursor = (MODE == 1) ? blk_base[blockIdx.x] : 0;
+  bool full = false;
+
+  for (u64 base = (u64)blockIdx.x * BLOCK; base < bound; base += (u64)gridDim.x * BLOCK) {
+    u64 i = base + threadIdx.x;
+    long long nc = 0;
+    int rs = -1, anc = -1;
+    K key = 0;
+    u64 c = 0;
+    if (i < bound) {
+      load_slot(in, i, key, c);
+      if (key != 0) {
+        if (a.nnb == 0) {
+          nc = a.G.n;
+        } else {
+          int best = INT_MAX;
+          for (int j = 0; j < a.nnb; ++j) {
+            int w = key_slot(key, a.L, a.nb_slot[j]);
+            int r0 = a.G.row_ptr[w], d = a.G.row_ptr[w + 1] - r0;
+            if (d < best) {
+              best = d;
+              rs = r0;
+              anc = j;
+            }
+          }
+          nc = best;
+        }
+      }
+    }
+    s_key[threadIdx.x] = key;
+    s_cnt[threadIdx.x] = c;
+    s_rs[threadIdx.x] = rs;
+    s_anc[threadIdx.x] = anc;
+    block_exclusive_scan<BLOCK>(nc, s_off, s_warp);
+    const long long total = s_off[BLOCK];
+    examined += (u64)total;
+
+    for (long long j0 = 0; j0 < total; j0 += BLOCK) {
+      long long j = j0 + threadIdx.x;
+      bool valid = false;
+      K okey = 0;
+      u64 oc = 0;
+      if (j < total) {
+        int lo = 0, hi = BLOCK - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= j) lo = mid;
+          else hi = mid - 1;
+        }
+        const int e = lo;
+        const long long r = j - s_off[e];
+        const int v = s_rs[e] >= 0 ? __ldg(a.G.col + s_rs[e] + r) : (int)r;
+        const K ekey = s_key[e];
+        const int t = key_trial(ekey, a.L);
+        const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+        valid = !((key_mask(ekey, a.L) >> cv) & 1u);
+        if (valid && a.degF) valid = a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
+        if (valid) {
+          const int an = s_anc[e];
+          for (int q = 0; q < a.nnb && valid; ++q)
+            if (q != an) valid = adjacent(a.G, key_slot(ekey, a.L, a.nb_slot[q]), v);
+        }
+        if (valid) {
+          okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
+          oc = s_cnt[e];
+        }
+      }
+      if (MODE == 0) {
+        produced += valid;
+      } else if (MODE == 1) {
+        int tot;
+        int rank = block_flag_rank<BLOCK>(valid, s_wc, tot);
+        if (valid) {
+          u64 pos = cursor + (u64)rank;
+          if (pos < a.out.cap) store_slot(out, pos, okey, oc);
+          else full = true;
+        }
+        cursor += (u64)tot;
+      } else {
+        if (valid) {
+          ++produced;
+          int r = hash_add(out, capmask, key_remove(okey, a.L, a.q), oc);
+          if (r > 0) ++fresh;
+          if (r < 0) full = true;
+        }
+      }
+    }
+    __syncthreads();  // the next tile overwrites the shared arrays
+  }
+  if (full) atomicOr(a.err, kErrOverflow);
+  if (MODE == 0) {
+    u64 s = block_sum<BLOCK>(produced, s_red);
+    if (threadIdx.x == 0) {
+      blk_count[blockIdx.x] = s;
+      if (examined) atomicAdd(a.cand, examined);
+    }
+  } else if (MODE == 2) {
+    u64 s = block_sum<BLOCK>(produced, s_red);
+    if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
+    u64 f = block_sum<BLOCK>(fresh, s_red);
+    if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
+  }
+}
+
+// exclusive scan of the per-block counts (one block); writes bases and the grand total
+__global__ void scan_blocks_kernel(const u64 *cnt, int nblk, u64 *base, u64 *total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    u64 s = 0;
+    for (int i = 0; i < nblk; ++i) {
+      base[i] = s;
+      s += cnt[i];
+    }
+    *total = s;
+  }
+}
+
+// ---- forget: project out slot q and aggregate into a hash table ---------------------------
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) forget_kernel(ForgetArgs a) {
+  __shared__ u64 s_red[BLOCK / 32];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const u64 bound = table_bound<K>(a.in);
+  const u64 capmask = a.out.cap - 1;
+  u64 fresh = 0;
+  bool full = false;
+  for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    int r = hash_add(out, capmask, key_remove(key, a.L, a.q), c);
+    if (r > 0) ++fresh;
+    if (r < 0) full = true;
+  }
+  if (full) atomicOr(a.err, kErrOverflow);
+  u64 f = block_sum<BLOCK>(fresh, s_red);
+  if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
+}
+
+// ---- join: chain the build child's entries by bag mapping, then probe with the other -------
+template <typename K>
+__device__ __forceinline__ K phi_key(K key, const KeyLayout &L) {
+  // colour set cleared; bit 0 marks an occupied index slot
+  return (key & ~(K)((1ull << L.k) - 1ull)) | (K)1;
+}
+
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) join_build_kernel(JoinArgs a) {
+  const Slot<K> *bt = reinterpret_cast<const Slot<K> *>(a.build.slots);
+  Slot<K> *idx = reinterpret_cast<Slot<K> *>(a.index);
+  const u64 bound = table_bound<K>(a.build);
+  const u64 capmask = a.index_cap - 1;
+  bool full = false;
+  for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
+    K key;
+    u64 c;
+    load_slot(bt, i, key, c);
+    if (key == 0) continue;
+    long long h = hash_claim(idx, capmask, phi_key(key, a.L));
+    if (h < 0) {
+      full = true;
+      continue;
+    }
+    a.next[i] = atomicExch(&idx[h].cnt, (u64)(i + 1));
+  }
+  if (full) atomicOr(a.err, kErrOverflow);
+}
+
+template <typename K, int MODE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
+  __shared__ u64 s_red[BLOCK / 32];
+  const Slot<K> *bt = reinterpret_cast<const Slot<K> *>(a.build.slots);
+  const Slot<K> *pt = reinterpret_cast<const Slot<K> *>(a.probe.slots);
+  const Slot<K> *idx = reinterpret_cast<const Slot<K> *>(a.index);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const u64 bound = table_bound<K>(a.probe);
+  const u64 icapmask = a.index_cap - 1, ocapmask = a.out.cap - 1;
+  const K cmask = (K)((1ull << a.L.k) - 1ull);
+  u64 pairs = 0, fresh = 0;
+  bool full = false;
+  for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
+    K key;
+    u64 c2;
+    load_slot(pt, i, key, c2);
+    if (key == 0) continue;
+    long long h = hash_find(idx, icapmask, phi_key(key, a.L));
+    if (h < 0) continue;
+    const int t = key_trial(key, a.L);
+    uint32_t bagc = 0;
+    for (int s = 0; s < a.b; ++s)
+      bagc |= 1u << a.G.colors[(u64)t * (u64)a.G.n + (u64)key_slot(key, a.L, s)];
+    const uint32_t C2 = key_mask(key, a.L);
+    K hk;
+    u64 e;
+    load_slot(idx, (u64)h, hk, e);
+    while (e) {
+      K k1;
+      u64 c1;
+      load_slot(bt, e - 1, k1, c1);
+      const uint32_t C1 = key_mask(k1, a.L);
+      if ((C1 & C2) == bagc) {
+        ++pairs;
+        if (MODE == 1) {
+          int r = hash_add(out, ocapmask, (key & ~cmask) | (K)(C1 | C2), c1 * c2);
+          if (r > 0) ++fresh;
+          if (r < 0) full = true;
+        }
+      }
+      e = a.next[e - 1];
+    }
+  }
+  if (full) atomicOr(a.err, kErrOverflow);
+  if (MODE == 0) {
+    u64 s = block_sum<BLOCK>(pairs, s_red);
+    if (threadIdx.x == 0 && s) atomicAdd(a.pairs, s);
+  } else {
+    u64 f = block_sum<BLOCK>(fresh, s_red);
+    if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
+  }
+}
+
+// ---- root: per trial, exists = root table nonempty, count = sum of its counts --------------
+template <typename K>
+__global__ void root_kernel(RootArgs a) {
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  const u64 bound = table_bound<K>(a.in);
+  for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < bound;
+       i += (u64)gridDim.x * blockDim.x) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    int t = key_trial(key, a.L);
+    a.exists[t] = 1u;
+    atomicAdd(&a.count[t], c);
+  }
+}
+
+// ---- unpack a table for inspection ----------------------------------------------------------
+template <typename K>
+__global__ void unpack_kernel(KeyLayout L, TableDesc t, int b, int32_t *trial, int32_t *phi,
+                              uint32_t *mask, u64 *cnt, u64 *n_out, u64 cap) {
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(t.slots);
+  const u64 bound = table_bound<K>(t);
+  for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < bound;
+       i += (u64)gridDim.x * blockDim.x) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    u64 pos = atomicAdd(n_out, 1ull);
+    if (pos >= cap) continue;
+    trial[pos] = key_trial(key, L);
+    for (int s = 0; s < b; ++s) phi[pos * b + s] = key_slot(key, L, s);
+    mask[pos] = key_mask(key, L);
+    cnt[pos] = c;
+  }
+}
+
+int grid_for(const DevInfo &d, int block) {
+  int per_sm = d.blocks_per_sm * 256 / block;
+  if (per_sm < 1) per_sm = 1;
+  return d.sms * per_sm;
+}
+
+template <typename K, int BLOCK>
+int intro_dispatch(cudaStream_t s, const DevInfo &d, int mode, const IntroArgs &a, u64 *blk_count,
+                   const u64 *blk_base) {
+  int grid = grid_for(d, BLOCK);
+  if (mode == 0) intro_kernel<K, 0, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
+  else if (mode == 1) intro_kernel<K, 1, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
+  else intro_kernel<K, 2, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+size_t slot_bytes(int kw) { return kw == 1 ? sizeof(Slot<u64>) : sizeof(Slot<u128>); }
+size_t index_slot_bytes(int kw) { return slot_bytes(kw); }
+
+int intro_grid(const DevInfo &d, int block) { return grid_for(d, block); }
+
+int launch_color(cudaStream_t s, const DevInfo &d, uint8_t *out, int32_t n, int32_t trials,
+                 int32_t k, uint64_t seed) {
+  if ((u64)n * (u64)trials == 0) return 0;
+  color_kernel<<<d.sms * 4, 256, 0, s>>>(out, n, trials, k, (uint32_t)seed,
+                                         (uint32_t)(seed >> 32));
+  return (int)cudaGetLastError();
+}
+
+int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a) {
+  if ((u64)a.G.n * (u64)a.trials == 0) return 0;
+  int grid = grid_for(d, 256);
+  if (kw == 1) leaf_kernel<u64, 256><<<grid, 256, 0, s>>>(a);
+  else leaf_kernel<u128, 256><<<grid, 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int block,
+                     const IntroArgs &a, u64 *blk) {
+  int grid = grid_for(d, block);
+  u64 *cnt = blk, *base = blk + grid, *total = blk + 2 * grid;
+  int r = 0;
+#define CC_INTRO(B)                                                              \
+  if (block == B) {                                                              \
+    r = kw == 1 ? intro_dispatch<u64, B>(s, d, mode, a, cnt, base)               \
+                : intro_dispatch<u128, B>(s, d, mode, a, cnt, base);             \
+  } else
+  CC_INTRO(128) CC_INTRO(256) CC_INTRO(512) { return (int)cudaErrorInvalidValue; }
+#undef CC_INTRO
+  if (r) return r;
+  if (mode == 0) {
+    scan_blocks_kernel<<<1, 32, 0, s>>>(cnt, grid, base, total);
+    r = (int)cudaGetLastError();
+  }
+  return r;
+}
+
+int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a) {
+  (void)block;
+  int grid = grid_for(d, 256);
+  if (kw == 1) forget_kernel<u64, 256><<<grid, 256, 0, s>>>(a);
+  else forget_kernel<u128, 256><<<grid, 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
+                const JoinArgs &a) {
+  (void)block;
+  int grid = grid_for(d, 256);
+  if (phase == 0) {
+    if (kw == 1) join_build_kernel<u64, 256><<<grid, 256, 0, s>>>(a);
+    else join_build_kernel<u128, 256><<<grid, 256, 0, s>>>(a);
+  } else if (phase == 1) {
+    if (kw == 1) join_probe_kernel<u64, 0, 256><<<grid, 256, 0, s>>>(a);
+    else join_probe_kernel<u128, 0, 256><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (kw == 1) join_probe_kernel<u64, 1, 256><<<grid, 256, 0, s>>>(a);
+    else join_probe_kernel<u128, 1, 256><<<grid, 256, 0, s>>>(a);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_root(cudaStream_t s, const DevInfo &d, int kw, const RootArgs &a) {
+  int grid = d.sms;
+  if (kw == 1) root_kernel<u64><<<grid, 256, 0, s>>>(a);
+  else root_kernel<u128><<<grid, 256, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_unpack(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L,
+                  const TableDesc &t, int b, unsigned long long cap, int32_t *trial,
+                  int32_t *phi, uint32_t *mask, unsigned long long *cnt,
+                  unsigned long long *n_out) {
+  int grid = d.sms * 2;
+  if (kw == 1)
+    unpack_kernel<u64><<<grid, 256, 0, s>>>(L, t, b, trial, phi, mask, cnt, n_out, cap);
+  else
+    unpack_kernel<u128><<<grid, 256, 0, s>>>(L, t, b, trial, phi, mask, cnt, n_out, cap);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace cc

@@ -1,0 +1,273 @@
+"""GPU parity of the dynamic programme against the CPU oracle (bit-exact, integer results).
+
+Every GPU call goes through the C ABI (paper_1908_11248_gb300 is its ctypes binding).  Small
+cases compare per trial: exists, the uint64 count, every node's table size and (with tables
+kept and fusion off) every node's table contents.  The full-size workloads compare sampled
+trials with the oracle and check properties that hold at any size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+cc = pytest.importorskip("paper_1908_11248_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    c = cc.Context(arena_bytes=24 << 30)
+    yield c
+    c.close()
+
+
+def gpu_dp(ctx, g, pat, colours=None, k=None, seed=None, trials=1, **opt):
+    nF, e, td = pat
+    k = k or nF
+    cc.cc_load_graph(ctx.h, *g)
+    pid = cc.cc_load_pattern(ctx.h, nF, e, td)
+    n = len(g[0]) - 1
+    if colours is not None:
+        cid = cc.cc_set_colors(ctx.h, colours, k)
+        trials = colours.shape[0]
+    else:
+        cid = cc.cc_color(ctx.h, seed, trials, k)
+    o = cc.cc_default_opts(**opt)
+    run = cc.cc_run_dp(ctx.h, pid, cid, o)
+    N, _ = cc.cc_pattern_info(ctx.h, pid)
+    res = dict(
+        count=cc.cc_count(ctx.h, run, trials),
+        exists=cc.cc_decide(ctx.h, run, trials),
+        sizes=cc.cc_table_stats(ctx.h, run, N)[0],
+        nodes=cc.cc_pattern_nodes(ctx.h, pid, nF),
+        colours=cc.cc_get_colors(ctx.h, cid, trials, n),
+        run=run, pid=pid, cid=cid, trials=trials,
+    )
+    return res
+
+
+def release(ctx, r):
+    cc.cc_release(ctx.h, r["run"])
+    cc.cc_release_colors(ctx.h, r["cid"])
+
+
+def oracle_tables(ref, nodes, trials):
+    out = []
+    for x, nd in enumerate(nodes):
+        b = len(nd[4])
+        d = {}
+        for t in range(trials):
+            phi, mask, cnt = ref.table(t, x, b)
+            for i in range(len(mask)):
+                d[(t, tuple(int(v) for v in phi[i]), int(mask[i]))] = int(cnt[i])
+        out.append(d)
+    return out
+
+
+def gpu_table(ctx, r, x, b, cap):
+    tr, phi, mask, cnt = cc.cc_table_dump(ctx.h, r["run"], x, cap, b)
+    d = {}
+    for i in range(len(mask)):
+        key = (int(tr[i]), tuple(int(v) for v in phi[i]), int(mask[i]))
+        assert key not in d, "duplicate key in a GPU table"
+        d[key] = int(cnt[i])
+    return d
+
+
+# ------------------------------------------------------------------------------------------
+
+def test_colouring_matches_oracle(ctx):
+    for n, T, k, seed in [(1, 1, 1, 0), (200, 1, 5, 7), (20000, 3, 8, 7), (777, 64, 32, 2 ** 40 + 5),
+                          (100003, 2, 9, 123456789)]:
+        g = synth.csr_from_edges(n, np.zeros((0, 2), np.int64))
+        cc.cc_load_graph(ctx.h, *g)
+        cid = cc.cc_color(ctx.h, seed, T, k)
+        got = cc.cc_get_colors(ctx.h, cid, T, n)
+        cc.cc_release_colors(ctx.h, cid)
+        assert np.array_equal(got, oracle.colors(n, T, k, seed)), (n, T, k, seed)
+
+
+PATTERNS = {
+    "P1": synth.path_pattern(1), "P2": synth.path_pattern(2), "P4": synth.path_pattern(4),
+    "C4": synth.cycle_pattern(4), "C5": synth.cycle_pattern(5), "S5": synth.star_pattern(5),
+    "K4": synth.clique_pattern(4), "G22": synth.grid_pattern(2, 2), "G23": synth.grid_pattern(2, 3),
+    "A": synth.pattern_A(), "B": synth.pattern_B(), "C": synth.pattern_C(), "D": synth.pattern_D(),
+    "T3": synth.random_partial_ktree(9, 3, 4), "T2": synth.random_partial_ktree(8, 2, 9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PATTERNS))
+def test_nice_decomposition_matches_oracle(ctx, name):
+    nF, e, td = PATTERNS[name]
+    pid = cc.cc_load_pattern(ctx.h, nF, e, td)
+    assert cc.cc_pattern_nodes(ctx.h, pid, nF) == oracle.nice_td(nF, e, td)
+
+
+def test_min_width_decomposition(ctx):
+    """With no decomposition given the library finds one of minimum width (Table 1 widths)."""
+    for pat, tw in [(synth.path_pattern(6), 1), (synth.cycle_pattern(7), 2),
+                    (synth.clique_pattern(5), 4), (synth.grid_pattern(3, 3), 3),
+                    (synth.grid_pattern(2, 5), 2), (synth.star_pattern(6), 1),
+                    (synth.pattern_A(), 1), (synth.pattern_B(), 2), (synth.pattern_C(), 2),
+                    (synth.pattern_D(), 2)]:
+        nF, e, _ = pat
+        pid = cc.cc_load_pattern(ctx.h, nF, e, None)
+        assert cc.cc_pattern_info(ctx.h, pid)[1] == tw
+
+
+def _check_small(ctx, g, pat, colours, k, df, fuse, block=256, tables=True):
+    nF, e, td = pat
+    T = colours.shape[0]
+    ref = oracle.run_dp(g, pat, colours, k, degree_filter=df)
+    r = gpu_dp(ctx, g, pat, colours=colours, k=k, degree_filter=int(df), fuse=int(fuse),
+               retain=1, block=block)
+    try:
+        assert r["nodes"] == oracle.nice_td(nF, e, td)
+        assert np.array_equal(r["count"], ref.count)
+        assert np.array_equal(r["exists"], ref.exists)
+        assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+        if tables and not fuse:
+            want = oracle_tables(ref, r["nodes"], T)
+            for x, nd in enumerate(r["nodes"]):
+                got = gpu_table(ctx, r, x, len(nd[4]), int(r["sizes"][x]) + 1)
+                assert got == want[x], (x, nd)
+    finally:
+        release(ctx, r)
+
+
+@pytest.mark.parametrize("name", sorted(PATTERNS))
+@pytest.mark.parametrize("fuse", [0, 1])
+def test_dp_small_parity(ctx, name, fuse):
+    pat = PATTERNS[name]
+    nF = pat[0]
+    g = synth.erdos_renyi(60, 0.15, 5)
+    for k, df in [(nF, True), (nF + 2, False)]:
+        k = min(k, 32)
+        colours = oracle.colors(60, 3, k, seed=11 + k)
+        _check_small(ctx, g, pat, colours, k, df, fuse)
+
+
+@pytest.mark.parametrize("block", [128, 256, 512])
+def test_dp_block_sizes(ctx, block):
+    g = synth.barabasi_albert(500, 3, 2)
+    pat = synth.grid_pattern(2, 3)
+    colours = oracle.colors(500, 4, 6, seed=3)
+    _check_small(ctx, g, pat, colours, 6, True, 0, block=block)
+    _check_small(ctx, g, pat, colours, 6, True, 1, block=block)
+
+
+def test_dp_wide_keys(ctx):
+    """k + max_bag * ceil(log2 n) + ceil(log2 trials) > 64: 128-bit keys."""
+    g = synth.barabasi_albert(3000, 3, 4)
+    pat = synth.random_partial_ktree(8, 3, 2)
+    colours = oracle.colors(3000, 5, 20, seed=8)
+    _check_small(ctx, g, pat, colours, 20, True, 0, tables=True)
+    _check_small(ctx, g, pat, colours, 20, True, 1, tables=False)
+
+
+def test_dp_edge_cases(ctx):
+    # a single vertex pattern: count = number of vertices (degree 0 passes the filter)
+    g = synth.erdos_renyi(50, 0.1, 1)
+    z = oracle.colors(50, 2, 1, seed=1)
+    _check_small(ctx, g, synth.path_pattern(1), z, 1, True, 0)
+    # a graph without edges: only edgeless patterns embed
+    g0 = synth.csr_from_edges(30, np.zeros((0, 2), np.int64))
+    z = oracle.colors(30, 2, 4, seed=2)
+    _check_small(ctx, g0, synth.path_pattern(2), z, 4, True, 0)
+    _check_small(ctx, g0, (3, np.zeros((0, 2), np.int32), ([[0], [1], [2]], [1, 2, -1])), z, 4,
+                 False, 0)
+    # one host vertex, more pattern vertices than host vertices
+    g1 = synth.csr_from_edges(1, np.zeros((0, 2), np.int64))
+    _check_small(ctx, g1, synth.path_pattern(3), np.zeros((1, 1), np.uint8), 3, True, 1)
+    # complete host graph: closed form n_F! * prod(colour class sizes) when k = n_F
+    gk = synth.complete_graph(12)
+    z = oracle.colors(12, 4, 4, seed=5)
+    r = gpu_dp(ctx, gk, synth.cycle_pattern(4), colours=z, k=4)
+    for t in range(4):
+        assert int(r["count"][t]) == 24 * int(np.prod(np.bincount(z[t], minlength=4)))
+    release(ctx, r)
+
+
+def test_invalid_inputs(ctx):
+    rp = np.array([0, 1, 1], np.int32)
+    with pytest.raises(cc.CCError) as e:  # asymmetric
+        cc.cc_load_graph(ctx.h, rp, np.array([1], np.int32))
+    assert e.value.code == cc.CC_EINVAL
+    with pytest.raises(cc.CCError):  # self loop
+        cc.cc_load_graph(ctx.h, np.array([0, 1], np.int32), np.array([0], np.int32))
+    with pytest.raises(cc.CCError):  # unsorted row
+        cc.cc_load_graph(ctx.h, *[np.array([0, 2, 3, 4], np.int32), np.array([2, 1, 0, 0], np.int32)])
+    nF, e, td = synth.cycle_pattern(5)
+    with pytest.raises(cc.CCError):  # decomposition misses an edge
+        cc.cc_load_pattern(ctx.h, nF, e, ([[0, 1, 2], [2, 3, 4]], [1, -1]))
+    with pytest.raises(cc.CCError):
+        cc.cc_load_pattern(ctx.h, 33, [], None)
+    g = synth.erdos_renyi(40, 0.1, 1)
+    cc.cc_load_graph(ctx.h, *g)
+    pid = cc.cc_load_pattern(ctx.h, nF, e, td)
+    cid = cc.cc_color(ctx.h, 1, 1, 4)
+    with pytest.raises(cc.CCError) as ex:  # k < n_F
+        cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
+    assert ex.value.code == cc.CC_EINVAL
+    cc.cc_release_colors(ctx.h, cid)
+    # 32 colours, bags of 4, 24-bit vertex ids and 2 trials need 129 bits
+    gb = synth.csr_from_edges(1 << 24, np.zeros((0, 2), np.int64))
+    cc.cc_load_graph(ctx.h, *gb)
+    p4 = cc.cc_load_pattern(ctx.h, *synth.clique_pattern(4)[:2], None)
+    cid = cc.cc_color(ctx.h, 1, 2, 32)
+    with pytest.raises(cc.CCError) as ex:
+        cc.cc_run_dp(ctx.h, p4, cid, cc.cc_default_opts())
+    assert ex.value.code == cc.CC_EKEYWIDTH
+    # a bag of nine vertices is beyond the kernels' largest bag
+    p9 = cc.cc_load_pattern(ctx.h, *synth.clique_pattern(9)[:2], None)
+    with pytest.raises(cc.CCError) as ex:
+        cc.cc_run_dp(ctx.h, p9, cid, cc.cc_default_opts())
+    assert ex.value.code == cc.CC_EKEYWIDTH
+    cc.cc_release_colors(ctx.h, cid)
+
+
+# ---- the benchmark workloads ----------------------------------------------------------------
+
+def test_workload_er200_c5(ctx):
+    """Erdos-Renyi n=200, p=0.05 (seed 1); 5-cycle; k=5; Philox seed 7; one trial."""
+    w = synth.WORKLOADS["er200_c5"]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    z = oracle.colors(200, 1, 5, w["seed"])
+    ref = oracle.run_dp(g, pat, z, 5)
+    for fuse in (0, 1):
+        r = gpu_dp(ctx, g, pat, seed=w["seed"], trials=1, k=5, fuse=fuse, retain=1)
+        assert np.array_equal(r["colours"], z)
+        assert np.array_equal(r["count"], ref.count) and int(ref.count[0]) > 0
+        assert np.array_equal(r["exists"], ref.exists)
+        assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+        release(ctx, r)
+
+
+def test_workload_ba20k_grid2x4_sampled(ctx):
+    """Barabasi-Albert n=20000, m=4; 2x4 grid; k=8; 64 trials in one run (the benchmark's
+    launch configuration).  Two sampled trials against the oracle; every trial's count is a
+    multiple of |Aut(G_{2,4})| = 4 and exists agrees with a nonzero count."""
+    w = synth.WORKLOADS["ba20k_grid2x4"]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    r = gpu_dp(ctx, g, pat, seed=w["seed"], trials=64, k=8)
+    z = oracle.colors(20000, 64, 8, w["seed"])
+    assert np.array_equal(r["colours"], z)
+    counts, exists = r["count"], r["exists"]
+    assert all(int(c) % 4 == 0 for c in counts)
+    assert np.array_equal(exists, (counts > 0).astype(np.uint8))
+    for t in (0, 63):
+        ref = oracle.run_dp(g, pat, z[t:t + 1], 8)
+        assert int(counts[t]) == int(ref.count[0]), t
+    release(ctx, r)
+    # the same trials alone give the same counts (trial batching changes nothing)
+    r1 = gpu_dp(ctx, g, pat, colours=z[[5, 40]], k=8)
+    assert int(r1["count"][0]) == int(counts[5]) and int(r1["count"][1]) == int(counts[40])
+    release(ctx, r1)
