@@ -85,6 +85,19 @@ typedef struct {
 int cc_load_pattern(cc_ctx *ctx, int32_t n_F, int32_t m_F, const int32_t *h_edges,
                     const cc_td *td, int32_t *pattern_id);
 
+/* Host-only (no context, no GPU): the nice decomposition cc_load_pattern would build for F and
+ * td (td NULL: minimum width), in the layout of cc_pattern_nodes.  Arrays hold max_nodes nodes
+ * (h_bag_ptr max_nodes+1, h_bag_vtx max_nodes*n_F).  *num_nodes and *width receive its size and
+ * width.  Errors: as cc_load_pattern; CC_ECAPACITY if it has more than max_nodes nodes. */
+int cc_nice_decomposition(int32_t n_F, int32_t m_F, const int32_t *h_edges, const cc_td *td,
+                          int32_t max_nodes, int32_t *h_type, int32_t *h_child0,
+                          int32_t *h_child1, int32_t *h_vertex, int32_t *h_bag_ptr,
+                          int32_t *h_bag_vtx, int32_t *num_nodes, int32_t *width);
+
+/* Host-only: CC_OK if (n, h_row_ptr, h_col) is a valid simple undirected CSR graph (the checks of
+ * cc_load_graph), CC_EINVAL otherwise. */
+int cc_check_graph(int32_t n, const int32_t *h_row_ptr, const int32_t *h_col);
+
 /* Node count and width (largest bag size minus one) of a loaded pattern's nice decomposition. */
 int cc_pattern_info(cc_ctx *ctx, int32_t pattern_id, int32_t *num_nodes, int32_t *width);
 

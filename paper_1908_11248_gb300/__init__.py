@@ -30,6 +30,7 @@ EXPORTS = [
     "cc_release_colors", "cc_default_opts", "cc_run_dp", "cc_run_batch", "cc_decide", "cc_count",
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
+    "cc_nice_decomposition", "cc_check_graph",
 ]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
                 "join_build", "join_count", "join_write", "root"]
@@ -93,6 +94,8 @@ def lib():
         "cc_serve_stop": ([P], ctypes.c_int),
         "cc_run_timings": ([P, i32, i32, P, P, P, P, P], ctypes.c_int),
         "cc_context_stats": ([P, P, P, P], ctypes.c_int),
+        "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "cc_check_graph": ([i32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -136,23 +139,52 @@ def cc_load_graph(ctx, row_ptr, col):
            "cc_load_graph")
 
 
+def _td_struct(td):
+    """(cc_td by reference or None, arrays to keep alive)."""
+    if td is None:
+        return None, []
+    bags, parent = td
+    bp = np.zeros(len(bags) + 1, np.int32)
+    bp[1:] = np.cumsum([len(b) for b in bags])
+    bv = _i32([u for b in bags for u in b]) if bp[-1] else np.zeros(1, np.int32)
+    par = _i32(parent)
+    st = cc_td(len(bags), _p(bp), _p(bv), _p(par))
+    return ctypes.byref(st), [bp, bv, par, st]
+
+
 def cc_load_pattern(ctx, nF: int, edges, td=None) -> int:
     e = _i32(edges).reshape(-1)
     pid = ctypes.c_int32(0)
-    tdp = None
-    keep = []
-    if td is not None:
-        bags, parent = td
-        bp = np.zeros(len(bags) + 1, np.int32)
-        bp[1:] = np.cumsum([len(b) for b in bags])
-        bv = _i32([u for b in bags for u in b]) if bp[-1] else np.zeros(1, np.int32)
-        par = _i32(parent)
-        keep = [bp, bv, par]
-        tdp = ctypes.byref(cc_td(len(bags), _p(bp), _p(bv), _p(par)))
+    tdp, keep = _td_struct(td)
     _check(lib().cc_load_pattern(ctx, nF, len(e) // 2, _p(e) if len(e) else None, tdp,
                                  ctypes.byref(pid)), "cc_load_pattern")
     del keep
     return pid.value
+
+
+def cc_nice_decomposition(nF: int, edges, td=None):
+    """Host-only: (nodes in the layout of cc_pattern_nodes, width)."""
+    e = _i32(edges).reshape(-1)
+    tdp, keep = _td_struct(td)
+    cap = 8 * nF * (len(td[0]) if td is not None else nF) + 16
+    ty, c0, c1, vx = (np.zeros(cap, np.int32) for _ in range(4))
+    bp = np.zeros(cap + 1, np.int32)
+    bv = np.zeros(cap * nF + 1, np.int32)
+    nn, w = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().cc_nice_decomposition(nF, len(e) // 2, _p(e) if len(e) else None, tdp, cap,
+                                       _p(ty), _p(c0), _p(c1), _p(vx), _p(bp), _p(bv),
+                                       ctypes.byref(nn), ctypes.byref(w)),
+           "cc_nice_decomposition")
+    del keep
+    N = nn.value
+    return [(int(ty[i]), int(c0[i]), int(c1[i]), int(vx[i]),
+             [int(u) for u in bv[bp[i]:bp[i + 1]]]) for i in range(N)], w.value
+
+
+def cc_check_graph(row_ptr, col) -> int:
+    """Host-only CSR validation; returns the C return code."""
+    rp, cl = _i32(row_ptr), _i32(col)
+    return lib().cc_check_graph(len(rp) - 1, _p(rp), _p(cl) if len(cl) else None)
 
 
 def cc_pattern_info(ctx, pid: int):

@@ -267,7 +267,34 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
   auto contains = [](const std::vector<int> &v, int u) {
     return std::binary_search(v.begin(), v.end(), u);
   };
-  // explicit post-order walk of the decomposition tree
+  // chain from bag `from` to bag `to` on top of node t: forgets first, then introduces, each in
+  // increasing vertex order
+  auto transition = [&](int t, const std::vector<int> &from, const std::vector<int> &to) {
+    for (int u : from)
+      if (!contains(to, u)) {
+        NiceNode f;
+        f.type = 2;
+        f.child0 = t;
+        f.vertex = u;
+        for (int w : out[t].bag)
+          if (w != u) f.bag.push_back(w);
+        t = push(f);
+      }
+    for (int u : to)
+      if (!contains(from, u)) {
+        NiceNode in;
+        in.type = 1;
+        in.child0 = t;
+        in.vertex = u;
+        in.bag = out[t].bag;
+        in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
+        t = push(in);
+      }
+    return t;
+  };
+  // explicit post-order walk of the decomposition tree; a finished child's subtree is followed
+  // at once by its transition to the parent's bag, and a node with several children joins their
+  // transitioned tops left-deep
   std::vector<int> top(nb, -1);
   std::vector<std::pair<int, size_t>> stack{{root, 0}};
   while (!stack.empty()) {
@@ -280,12 +307,13 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
     }
     stack.pop_back();
     const std::vector<int> &B = bags[i];
+    int t = -1;
     if (kids[i].empty()) {
       NiceNode leaf;
       leaf.type = 0;
       leaf.vertex = B[0];
       leaf.bag = {B[0]};
-      int t = push(leaf);
+      t = push(leaf);
       for (size_t j = 1; j < B.size(); ++j) {
         NiceNode in;
         in.type = 1;
@@ -295,44 +323,21 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
         in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), B[j]), B[j]);
         t = push(in);
       }
-      top[i] = t;
-      continue;
-    }
-    int acc = -1;
-    for (int c : kids[i]) {
-      int t = top[c];
-      for (int u : bags[c])  // forgets first, increasing vertex
-        if (!contains(B, u)) {
-          NiceNode f;
-          f.type = 2;
-          f.child0 = t;
-          f.vertex = u;
-          for (int w : out[t].bag)
-            if (w != u) f.bag.push_back(w);
-          t = push(f);
+    } else {
+      for (int c : kids[i]) {
+        if (t < 0) {
+          t = top[c];
+        } else {
+          NiceNode j;
+          j.type = 3;
+          j.child0 = t;
+          j.child1 = top[c];
+          j.bag = out[t].bag;
+          t = push(j);
         }
-      for (int u : B)  // then introduces, increasing vertex
-        if (!contains(bags[c], u)) {
-          NiceNode in;
-          in.type = 1;
-          in.child0 = t;
-          in.vertex = u;
-          in.bag = out[t].bag;
-          in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
-          t = push(in);
-        }
-      if (acc < 0) {
-        acc = t;
-      } else {  // left-deep join
-        NiceNode j;
-        j.type = 3;
-        j.child0 = acc;
-        j.child1 = t;
-        j.bag = out[acc].bag;
-        acc = push(j);
       }
     }
-    top[i] = acc;
+    top[i] = (parent[i] >= 0) ? transition(t, B, bags[parent[i]]) : t;
   }
   int t = top[root];
   for (int u : bags[root]) {  // empty-bag root of degree one
@@ -829,9 +834,8 @@ int cc_destroy(cc_ctx *ctx) {
   return CC_OK;
 }
 
-int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
-  Ctx *c = (Ctx *)ctx;
-  if (!c || n < 0 || !h_row_ptr) return CC_EINVAL;
+int cc_check_graph(int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
+  if (n < 0 || !h_row_ptr) return CC_EINVAL;
   if (h_row_ptr[0] != 0) return CC_EINVAL;
   for (int32_t v = 0; v < n; ++v)
     if (h_row_ptr[v + 1] < h_row_ptr[v]) return CC_EINVAL;
@@ -845,6 +849,15 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
       if (!std::binary_search(h_col + h_row_ptr[w], h_col + h_row_ptr[w + 1], v))
         return CC_EINVAL;  // symmetric
     }
+  return CC_OK;
+}
+
+int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  int vr = cc_check_graph(n, h_row_ptr, h_col);
+  if (vr) return vr;
+  const int64_t m2 = h_row_ptr[n];
   // a new graph invalidates runs and colourings
   for (auto &r : c->runs) free_run(c, r.second.get());
   c->runs.clear();
@@ -870,11 +883,9 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   return CC_OK;
 }
 
-int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
-                    const cc_td *td, int32_t *pattern_id) {
-  Ctx *c = (Ctx *)ctx;
-  if (!c || nF < 1 || nF > 32 || mF < 0 || (mF > 0 && !h_edges) || !pattern_id) return CC_EINVAL;
-  Pattern P;
+static int make_pattern(int32_t nF, int32_t mF, const int32_t *h_edges, const cc_td *td,
+                        Pattern &P) {
+  if (nF < 1 || nF > 32 || mF < 0 || (mF > 0 && !h_edges)) return CC_EINVAL;
   P.nF = nF;
   P.adj.assign(nF, 0u);
   P.deg.assign(nF, 0);
@@ -906,6 +917,42 @@ int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
   if (!valid_td(P.adj, nF, bags, parent, root)) return CC_EINVAL;
   build_nice(bags, parent, root, P.nodes);
   for (auto &nd : P.nodes) P.width = std::max<int>(P.width, (int)nd.bag.size() - 1);
+  return CC_OK;
+}
+
+int cc_nice_decomposition(int32_t nF, int32_t mF, const int32_t *h_edges, const cc_td *td,
+                          int32_t max_nodes, int32_t *type, int32_t *child0, int32_t *child1,
+                          int32_t *vertex, int32_t *bag_ptr, int32_t *bag_vtx,
+                          int32_t *num_nodes, int32_t *width) {
+  Pattern P;
+  int rc = make_pattern(nF, mF, h_edges, td, P);
+  if (rc) return rc;
+  if (num_nodes) *num_nodes = (int32_t)P.nodes.size();
+  if (width) *width = P.width;
+  if ((int32_t)P.nodes.size() > max_nodes) return CC_ECAPACITY;
+  int32_t off = 0;
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    if (type) type[i] = P.nodes[i].type;
+    if (child0) child0[i] = P.nodes[i].child0;
+    if (child1) child1[i] = P.nodes[i].child1;
+    if (vertex) vertex[i] = P.nodes[i].vertex;
+    if (bag_ptr) bag_ptr[i] = off;
+    for (int u : P.nodes[i].bag) {
+      if (bag_vtx) bag_vtx[off] = u;
+      ++off;
+    }
+  }
+  if (bag_ptr) bag_ptr[P.nodes.size()] = off;
+  return CC_OK;
+}
+
+int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
+                    const cc_td *td, int32_t *pattern_id) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !pattern_id) return CC_EINVAL;
+  Pattern P;
+  int rc = make_pattern(nF, mF, h_edges, td, P);
+  if (rc) return rc;
   int32_t id = c->next_pattern++;
   c->patterns[id] = std::move(P);
   *pattern_id = id;
