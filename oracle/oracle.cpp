@@ -122,12 +122,43 @@ struct NiceTD {
   std::vector<NiceNode> nodes;  // post-order; the root (empty bag) is last
 };
 
+// Introduces the vertices `add` on top of node `top`, one introduce node each.  The paper does
+// not fix their order; we take, each time, the smallest remaining vertex that has an F-neighbour
+// in the current bag, or the smallest remaining vertex if none has, so that an introduce finds
+// its candidates in adjacency lists whenever F allows (Section 3.2, mapping expansion).
+int32_t introduce_all(NiceTD &T, const Pattern &F, int32_t top, std::vector<int32_t> add) {
+  std::sort(add.begin(), add.end());
+  while (!add.empty()) {
+    size_t pick = 0;
+    for (size_t j = 0; j < add.size(); ++j) {
+      bool anchored = false;
+      for (int32_t w : T.nodes[top].bag) anchored = anchored || F.adj[add[j]][w];
+      if (anchored) {
+        pick = j;
+        break;
+      }
+    }
+    int32_t u = add[pick];
+    add.erase(add.begin() + pick);
+    NiceNode in;
+    in.type = INTRODUCE;
+    in.child0 = top;
+    in.vertex = u;
+    in.bag = T.nodes[top].bag;
+    in.bag.push_back(u);
+    std::sort(in.bag.begin(), in.bag.end());
+    T.nodes.push_back(in);
+    top = (int32_t)T.nodes.size() - 1;
+  }
+  return top;
+}
+
 // Builds the nice decomposition rooted at decomposition node i: its top node has bag B_i.
 // Children of a decomposition node are taken in increasing id; going from a child's bag to
-// B_i first forgets B_c \ B_i, then introduces B_i \ B_c, each in increasing vertex order;
-// several children are combined by left-deep joins.  A leaf bag becomes a size-one leaf node
-// holding its smallest vertex followed by introductions of the rest.
-int32_t nice_build(NiceTD &T, const std::vector<std::vector<int32_t>> &bags,
+// B_i first forgets B_c \ B_i in increasing vertex order, then introduces B_i \ B_c (order of
+// introduce_all); several children are combined by left-deep joins.  A leaf bag becomes a
+// size-one leaf node holding its smallest vertex followed by introductions of the rest.
+int32_t nice_build(NiceTD &T, const Pattern &F, const std::vector<std::vector<int32_t>> &bags,
                    const std::vector<std::vector<int32_t>> &kids, int32_t i) {
   const std::vector<int32_t> &B = bags[i];
   if (kids[i].empty()) {
@@ -137,22 +168,11 @@ int32_t nice_build(NiceTD &T, const std::vector<std::vector<int32_t>> &bags,
     leaf.bag = {B[0]};
     T.nodes.push_back(leaf);
     int32_t top = (int32_t)T.nodes.size() - 1;
-    for (size_t j = 1; j < B.size(); ++j) {
-      NiceNode in;
-      in.type = INTRODUCE;
-      in.child0 = top;
-      in.vertex = B[j];
-      in.bag = T.nodes[top].bag;
-      in.bag.push_back(B[j]);
-      std::sort(in.bag.begin(), in.bag.end());
-      T.nodes.push_back(in);
-      top = (int32_t)T.nodes.size() - 1;
-    }
-    return top;
+    return introduce_all(T, F, top, std::vector<int32_t>(B.begin() + 1, B.end()));
   }
   std::vector<int32_t> tops;
   for (int32_t c : kids[i]) {
-    int32_t top = nice_build(T, bags, kids, c);
+    int32_t top = nice_build(T, F, bags, kids, c);
     const std::vector<int32_t> &Bc = bags[c];
     for (int32_t u : Bc) {
       if (std::find(B.begin(), B.end(), u) != B.end()) continue;
@@ -165,18 +185,10 @@ int32_t nice_build(NiceTD &T, const std::vector<std::vector<int32_t>> &bags,
       T.nodes.push_back(f);
       top = (int32_t)T.nodes.size() - 1;
     }
-    for (int32_t u : B) {
-      if (std::find(Bc.begin(), Bc.end(), u) != Bc.end()) continue;
-      NiceNode in;
-      in.type = INTRODUCE;
-      in.child0 = top;
-      in.vertex = u;
-      in.bag = T.nodes[top].bag;
-      in.bag.push_back(u);
-      std::sort(in.bag.begin(), in.bag.end());
-      T.nodes.push_back(in);
-      top = (int32_t)T.nodes.size() - 1;
-    }
+    std::vector<int32_t> add;
+    for (int32_t u : B)
+      if (std::find(Bc.begin(), Bc.end(), u) == Bc.end()) add.push_back(u);
+    top = introduce_all(T, F, top, add);
     tops.push_back(top);
   }
   int32_t top = tops[0];
@@ -245,7 +257,7 @@ bool make_nice(const Pattern &F, int32_t nbags, const int32_t *bag_ptr, const in
       if (!ok) return false;
     }
   T.nodes.clear();
-  int32_t top = nice_build(T, bags, kids, root);
+  int32_t top = nice_build(T, F, bags, kids, root);
   for (int32_t u : bags[root]) {
     NiceNode f;
     f.type = FORGET;
