@@ -137,10 +137,12 @@ typedef struct {
   float load_factor;     /* hash-table fill target in (0, 0.9]; 0 = library default           */
   int32_t block;         /* threads per block of the node kernels (128, 256 or 512)           */
   int32_t profile;       /* 1: time every kernel launch with CUDA events (cc_run_timings)     */
+  int32_t group;         /* 1: an introduce whose vertex has >= 2 bag neighbours first sorts   */
+                         /*    its child by their images and shares candidate lists per run    */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 1, use_graph 0, load factor
- * 0.5, block 256, profile 0). */
+ * 0.5, block 256, profile 0, group 1). */
 void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in
@@ -197,6 +199,7 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 #define CC_K_JOIN_COUNT 7
 #define CC_K_JOIN_WRITE 8
 #define CC_K_ROOT 9
+#define CC_K_SORT 10 /* all passes of one child sort by bag-neighbour images */
 
 /* Per-launch device times of a run made with profile = 1, in launch order: node id, kernel
  * kind (CC_K_*), milliseconds between CUDA events recorded on the context's stream just before

@@ -33,7 +33,7 @@ EXPORTS = [
     "cc_nice_decomposition", "cc_check_graph",
 ]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
-                "join_build", "join_count", "join_write", "root"]
+                "join_build", "join_count", "join_write", "root", "sort"]
 
 
 class CCError(RuntimeError):
@@ -51,7 +51,7 @@ class cc_run_opts(ctypes.Structure):
     _fields_ = [("degree_filter", ctypes.c_int32), ("retain", ctypes.c_int32),
                 ("fuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("load_factor", ctypes.c_float), ("block", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("group", ctypes.c_int32)]
 
 
 _lib = None

@@ -196,11 +196,11 @@ int bits_for(u64 x) {  // bits to hold values 0..x
   return b;
 }
 
+// capacity for `entries` keys at fill `lf`, rounded up to a whole 256-byte line of records
 u64 hash_cap(u64 entries, float lf) {
   double want = (double)std::max<u64>(entries, 1) / (double)lf;
-  u64 c = 16;
-  while ((double)c < want) c <<= 1;
-  return c;
+  u64 c = (u64)want + 16;
+  return (c + 15) & ~u64(15);
 }
 
 // ---- nice tree decomposition (Section 1.2; Section 3, after Cygan et al.) ------------------
@@ -252,8 +252,8 @@ bool valid_td(const std::vector<uint32_t> &adj, int nF, const std::vector<std::v
   return true;
 }
 
-void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<int> &parent,
-                int root, std::vector<NiceNode> &out) {
+void build_nice(const std::vector<uint32_t> &adj, const std::vector<std::vector<int>> &bags_in,
+                const std::vector<int> &parent, int root, std::vector<NiceNode> &out) {
   int nb = (int)bags_in.size();
   std::vector<std::vector<int>> bags(bags_in), kids(nb);
   for (auto &b : bags) std::sort(b.begin(), b.end());
@@ -267,8 +267,33 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
   auto contains = [](const std::vector<int> &v, int u) {
     return std::binary_search(v.begin(), v.end(), u);
   };
-  // chain from bag `from` to bag `to` on top of node t: forgets first, then introduces, each in
-  // increasing vertex order
+  // introduces `todo` (increasing) on top of node t: each step takes the smallest vertex with an
+  // F-neighbour already in the bag, else the smallest, so introduces are anchored in adjacency
+  // lists whenever the pattern allows
+  auto introduce_all = [&](int t, std::vector<int> todo) {
+    while (!todo.empty()) {
+      uint32_t bagmask = 0;
+      for (int w : out[t].bag) bagmask |= 1u << w;
+      size_t pick = 0;
+      for (size_t j = 0; j < todo.size(); ++j)
+        if (adj[todo[j]] & bagmask) {
+          pick = j;
+          break;
+        }
+      int u = todo[pick];
+      todo.erase(todo.begin() + pick);
+      NiceNode in;
+      in.type = 1;
+      in.child0 = t;
+      in.vertex = u;
+      in.bag = out[t].bag;
+      in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
+      t = push(in);
+    }
+    return t;
+  };
+  // chain from bag `from` to bag `to` on top of node t: forgets in increasing vertex order,
+  // then introduces
   auto transition = [&](int t, const std::vector<int> &from, const std::vector<int> &to) {
     for (int u : from)
       if (!contains(to, u)) {
@@ -280,17 +305,10 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
           if (w != u) f.bag.push_back(w);
         t = push(f);
       }
+    std::vector<int> todo;
     for (int u : to)
-      if (!contains(from, u)) {
-        NiceNode in;
-        in.type = 1;
-        in.child0 = t;
-        in.vertex = u;
-        in.bag = out[t].bag;
-        in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
-        t = push(in);
-      }
-    return t;
+      if (!contains(from, u)) todo.push_back(u);
+    return introduce_all(t, todo);
   };
   // explicit post-order walk of the decomposition tree; a finished child's subtree is followed
   // at once by its transition to the parent's bag, and a node with several children joins their
@@ -313,16 +331,7 @@ void build_nice(const std::vector<std::vector<int>> &bags_in, const std::vector<
       leaf.type = 0;
       leaf.vertex = B[0];
       leaf.bag = {B[0]};
-      t = push(leaf);
-      for (size_t j = 1; j < B.size(); ++j) {
-        NiceNode in;
-        in.type = 1;
-        in.child0 = t;
-        in.vertex = B[j];
-        in.bag = out[t].bag;
-        in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), B[j]), B[j]);
-        t = push(in);
-      }
+      t = introduce_all(push(leaf), std::vector<int>(B.begin() + 1, B.end()));
     } else {
       for (int c : kids[i]) {
         if (t < 0) {
@@ -594,9 +603,46 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       a.err = c->d_err;
       a.valid = R->d_counters + x;
       a.cand = blk + 2 * grid + 1;
+      // several bag neighbours: sort the child by their images so runs share candidate lists
+      const int grouped = R->opts.group && a.nnb >= 2 && a.nnb * R->L.nb <= 64 && R->sizes[y] > 0;
+      void *sorted = nullptr;
+      if (grouped) {
+        const u64 m = R->sizes[y];
+        const u64 n_src = R->tables[y].hashed ? R->tables[y].cap : m;
+        const size_t rb = cc::slot_bytes(R->kw);
+        void *ba = c->arena.alloc(m * rb), *bb = c->arena.alloc(m * rb);
+        u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev));
+        if (!ba || !bb || !hist) {
+          c->arena.release(ba);
+          c->arena.release(bb);
+          c->arena.release(hist);
+          return CC_ENOMEM;
+        }
+        int which = 0;
+        const int passes = (a.nnb * R->L.nb + 7) / 8;
+        rc = timed(x, CC_K_SORT, 3 * passes, [&] {
+          return cc::launch_tuple_sort(c->stream, c->dev, R->kw, R->L, a.nnb, a.nb_slot,
+                                       R->tables[y].slots, n_src, m, ba, bb, hist, &which);
+        });
+        c->arena.release(hist);
+        sorted = which ? bb : ba;
+        c->arena.release(which ? ba : bb);
+        if (rc) {
+          c->arena.release(sorted);
+          return rc;
+        }
+        a.in.slots = sorted;
+        a.in.cap = m;
+        a.in.hashed = 0;
+      }
+      struct SortedGuard {
+        Ctx *c;
+        void *p;
+        ~SortedGuard() { c->arena.release(p); }
+      } sorted_guard{c, sorted};
       CUDA_OK(cudaMemsetAsync(a.cand, 0, sizeof(u64), c->stream));
       rc = timed(x, CC_K_INTRO_COUNT, 2, [&] {
-        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 0, block, a, blk);
+        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 0, grouped, block, a, blk);
       });
       if (rc) return rc;
       u64 total = 0, cand = 0;
@@ -614,7 +660,7 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         a.q = pos_in(nd.bag, P.nodes[f].vertex);
         CUDA_OK(cudaMemsetAsync(R->d_counters + x, 0, sizeof(u64), c->stream));
         rc = timed(x, CC_K_INTRO_FUSED, 1, [&] {
-          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, block, a, blk);
+          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a, blk);
         });
         if (rc) return rc;
         if (R->opts.profile) R->timings.back().candidates = cand;
@@ -633,7 +679,7 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       CUDA_OK(cudaMemcpyAsync(R->d_counters + x, blk + 2 * grid, sizeof(u64),
                               cudaMemcpyDeviceToDevice, c->stream));
       rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, block, a, blk);
+        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
       });
       if (rc) return rc;
       if (R->opts.profile) R->timings.back().candidates = cand;
@@ -786,6 +832,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->load_factor = 0.5f;
   o->block = 256;
   o->profile = 0;
+  o->group = 1;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
@@ -915,7 +962,7 @@ static int make_pattern(int32_t nF, int32_t mF, const int32_t *h_edges, const cc
   }
   int root = -1;
   if (!valid_td(P.adj, nF, bags, parent, root)) return CC_EINVAL;
-  build_nice(bags, parent, root, P.nodes);
+  build_nice(P.adj, bags, parent, root, P.nodes);
   for (auto &nd : P.nodes) P.width = std::max<int>(P.width, (int)nd.bag.size() - 1);
   return CC_OK;
 }

@@ -114,9 +114,20 @@ int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a);
 // exclusive bases to blk[grid, 2*grid) and the total to blk[2*grid]; 1 writes them densely at
 // those bases; 2 adds them, projected by the parent forget, into a hashed table.  Modes 0 and 1
 // of one node must use the same block size (and so the same grid).
+// `grouped` selects candidate lists shared by runs of equal bag-neighbour images (the child
+// table must then be sorted by those images, see launch_tuple_sort).
 int intro_grid(const DevInfo &d, int block);
-int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int block,
+int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int grouped, int block,
                      const IntroArgs &a, unsigned long long *blk);
+// Stable sort of the nonempty records of `src` (n_src slots, n of them nonempty) by the G-vertices
+// of bag slots slots[0..nsl) (nsl * nb <= 64 bits), alternating between buf_a and buf_b (n
+// records each); *which = 0 or 1 names the buffer holding the result.  hist needs
+// 256 * sort_grid(d) words.
+int sort_grid(const DevInfo &d);
+int launch_tuple_sort(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L, int nsl,
+                      const int *slots, const void *src, unsigned long long n_src,
+                      unsigned long long n, void *buf_a, void *buf_b, unsigned long long *hist,
+                      int *which);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
                 const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write

@@ -120,34 +120,39 @@ __device__ __forceinline__ u64 table_bound(const TableDesc &t) {
 }
 
 // ---- hash table (open addressing, linear probing, key claimed by compare-and-swap) -------
-// Returns 1 if the key was new, 0 if it was present, -1 if the table is full.
-__device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 capmask, u64 key, u64 c) {
-  u64 h = key_hash(key) & capmask;
-  for (u64 probe = 0; probe <= capmask; ++probe) {
+// The home slot of a key is its 64-bit hash scaled to [0, cap) by a multiply-high (Lemire's
+// range reduction), so capacities need not be powers of two.
+__device__ __forceinline__ u64 home_slot(u64 h, u64 cap) { return __umul64hi(h, cap); }
+__device__ __forceinline__ u64 next_slot(u64 h, u64 cap) { return h + 1 == cap ? 0 : h + 1; }
+
+// Adds count c to key's record.  Returns 1 if the key was new, 0 if it was present, -1 if the
+// table is full.  A new key and its count are installed by one 128-bit compare-and-swap of the
+// whole (key, count) record; later additions are 64-bit atomic adds on the count.
+__device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 cap, u64 key, u64 c) {
+  u64 h = home_slot(key_hash(key), cap);
+  for (u64 probe = 0; probe < cap; ++probe) {
     u64 cur = *reinterpret_cast<volatile u64 *>(&slots[h].key);  // 8-byte reads are atomic
     if (cur == key) {
       atomicAdd(&slots[h].cnt, c);
       return 0;
     }
     if (cur == 0) {
-      u64 old = atomicCAS(&slots[h].key, 0ull, key);
-      if (old == 0) {
-        atomicAdd(&slots[h].cnt, c);
-        return 1;
-      }
-      if (old == key) {
+      u128 old = atomicCAS(reinterpret_cast<u128 *>(&slots[h]), (u128)0,
+                           (u128)key | ((u128)c << 64));
+      if (old == 0) return 1;
+      if ((u64)old == key) {
         atomicAdd(&slots[h].cnt, c);
         return 0;
       }
     }
-    h = (h + 1) & capmask;
+    h = next_slot(h, cap);
   }
   return -1;
 }
 
-__device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 capmask, u128 key, u64 c) {
-  u64 h = key_hash(key) & capmask;
-  for (u64 probe = 0; probe <= capmask; ++probe) {
+__device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 cap, u128 key, u64 c) {
+  u64 h = home_slot(key_hash(key), cap);
+  for (u64 probe = 0; probe < cap; ++probe) {
     // a 16-byte plain read is not guaranteed to be single-copy atomic: always compare-and-swap
     u128 old = atomicCAS(&slots[h].key, (u128)0, key);
     if (old == 0) {
@@ -158,34 +163,34 @@ __device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 capmask, u128 key
       atomicAdd(&slots[h].cnt, c);
       return 0;
     }
-    h = (h + 1) & capmask;
+    h = next_slot(h, cap);
   }
   return -1;
 }
 
 // find-or-insert; returns the slot index or -1 if the table is full
 template <typename K>
-__device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 capmask, K key) {
-  u64 h = key_hash(key) & capmask;
-  for (u64 probe = 0; probe <= capmask; ++probe) {
+__device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 cap, K key) {
+  u64 h = home_slot(key_hash(key), cap);
+  for (u64 probe = 0; probe < cap; ++probe) {
     K old = atomicCAS(&slots[h].key, (K)0, key);
     if (old == 0 || old == key) return (long long)h;
-    h = (h + 1) & capmask;
+    h = next_slot(h, cap);
   }
   return -1;
 }
 
 // lookup in a table no thread is writing; -1 if absent
 template <typename K>
-__device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 capmask, K key) {
-  u64 h = key_hash(key) & capmask;
-  for (u64 probe = 0; probe <= capmask; ++probe) {
+__device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 cap, K key) {
+  u64 h = home_slot(key_hash(key), cap);
+  for (u64 probe = 0; probe < cap; ++probe) {
     K cur;
     u64 c;
     load_slot(slots, h, cur, c);
     if (cur == key) return (long long)h;
     if (cur == 0) return -1;
-    h = (h + 1) & capmask;
+    h = next_slot(h, cap);
   }
   return -1;
 }
@@ -316,124 +321,376 @@ __global__ void __launch_bounds__(BLOCK) leaf_kernel(LeafArgs a) {
 //   MODE 0: count the valid extensions per block (blk_count[blockIdx.x])
 //   MODE 1: write them densely at blk_base[blockIdx.x] + block-local rank (deterministic order)
 //   MODE 2: project out slot q (the parent forget) and add into the hashed output
-template <typename K, int MODE, int BLOCK>
+//
+// The grouped variant expects the child table sorted by the images of u's bag neighbours
+// (tuple_sort), so entries that differ only in trial, colour set or other slots come in runs.
+// In every tile the first entry of each run computes the run's candidate list once (adjacency
+// to every bag neighbour's image and the degree filter) into shared memory, and each entry of
+// the run then only tests its own colour set.  A tile whose lists overflow the shared buffer is
+// processed entry by entry instead.
+
+template <typename K, int BLOCK, int VCAP>
+struct IntroSmem {
+  long long off[BLOCK + 1];
+  long long warp[BLOCK / 32];
+  K key[BLOCK];
+  u64 cnt[BLOCK];
+  u64 tup[BLOCK];
+  int rs[BLOCK];
+  int anc[BLOCK];
+  int head[BLOCK];
+  int hvc[BLOCK];
+  int hst[BLOCK];
+  int wc[BLOCK / 32];
+  int hmax[BLOCK / 32];
+  u64 red[BLOCK / 32];
+  int vbuf[VCAP];
+};
+
+struct EmitState {
+  u64 produced = 0, fresh = 0, examined = 0, cursor = 0;
+  bool full = false;
+};
+
+template <typename K, int MODE, int BLOCK, typename S>
+__device__ __forceinline__ void emit(const IntroArgs &a, S &sm, EmitState &st, bool valid, K okey,
+                                     u64 oc) {
+  if (MODE == 0) {
+    st.produced += valid;
+  } else if (MODE == 1) {
+    int tot;
+    int rank = block_flag_rank<BLOCK>(valid, sm.wc, tot);
+    if (valid) {
+      u64 pos = st.cursor + (u64)rank;
+      if (pos < a.out.cap) store_slot(reinterpret_cast<Slot<K> *>(a.out.slots), pos, okey, oc);
+      else st.full = true;
+    }
+    st.cursor += (u64)tot;
+  } else if (valid) {
+    ++st.produced;
+    int r = hash_add(reinterpret_cast<Slot<K> *>(a.out.slots), a.out.cap,
+                     key_remove(okey, a.L, a.q), oc);
+    if (r > 0) ++st.fresh;
+    if (r < 0) st.full = true;
+  }
+}
+
+// index e of the entry whose candidate range [off[e], off[e+1]) holds j
+template <int BLOCK>
+__device__ __forceinline__ int owner(const long long *off, long long j) {
+  int lo = 0, hi = BLOCK - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// entry by entry: every candidate of every entry is checked in full (the tile's entries are in
+// sm.key / sm.cnt)
+template <typename K, int MODE, int BLOCK, typename S>
+__device__ __forceinline__ void plain_tile(const IntroArgs &a, S &sm, EmitState &st) {
+  const K key = sm.key[threadIdx.x];
+  long long nc = 0;
+  int rs = -1, anc = -1;
+  if (key != 0) {
+    if (a.nnb == 0) {
+      nc = a.G.n;
+    } else {
+      int best = INT_MAX;
+      for (int j = 0; j < a.nnb; ++j) {
+        int w = key_slot(key, a.L, a.nb_slot[j]);
+        int r0 = a.G.row_ptr[w], d = a.G.row_ptr[w + 1] - r0;
+        if (d < best) {
+          best = d;
+          rs = r0;
+          anc = j;
+        }
+      }
+      nc = best;
+    }
+  }
+  sm.rs[threadIdx.x] = rs;
+  sm.anc[threadIdx.x] = anc;
+  block_exclusive_scan<BLOCK>(nc, sm.off, sm.warp);
+  const long long total = sm.off[BLOCK];
+  st.examined += (u64)total;
+  for (long long j0 = 0; j0 < total; j0 += BLOCK) {
+    const long long j = j0 + threadIdx.x;
+    bool valid = false;
+    K okey = 0;
+    u64 oc = 0;
+    if (j < total) {
+      const int e = owner<BLOCK>(sm.off, j);
+      const long long r = j - sm.off[e];
+      const int v = sm.rs[e] >= 0 ? __ldg(a.G.col + sm.rs[e] + r) : (int)r;
+      const K ekey = sm.key[e];
+      const int t = key_trial(ekey, a.L);
+      const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+      valid = !((key_mask(ekey, a.L) >> cv) & 1u);
+      if (valid && a.degF) valid = a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
+      if (valid) {
+        const int an = sm.anc[e];
+        for (int q = 0; q < a.nnb && valid; ++q)
+          if (q != an) valid = adjacent(a.G, key_slot(ekey, a.L, a.nb_slot[q]), v);
+      }
+      if (valid) {
+        okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
+        oc = sm.cnt[e];
+      }
+    }
+    emit<K, MODE, BLOCK>(a, sm, st, valid, okey, oc);
+  }
+}
+
+template <typename K>
+__device__ __forceinline__ u64 nb_tuple(K key, const IntroArgs &a) {
+  u64 t = 0;
+  for (int j = 0; j < a.nnb; ++j) t = (t << a.L.nb) | (u64)key_slot(key, a.L, a.nb_slot[j]);
+  return t;
+}
+
+// candidate lists shared by runs of equal bag-neighbour images; false if they overflowed
+template <typename K, int MODE, int BLOCK, int VCAP, typename S>
+__device__ __forceinline__ bool grouped_tile(const IntroArgs &a, S &sm, EmitState &st) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const K key = sm.key[tid];
+  const u64 tup = key != 0 ? nb_tuple(key, a) : ~0ull;
+  sm.tup[tid] = tup;
+  __syncthreads();
+  const bool head = key != 0 && (tid == 0 || sm.tup[tid - 1] != tup);
+  // the run head of every entry: inclusive max-scan of (head ? tid : -1)
+  int h = head ? tid : -1;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, h, o);
+    if (lane >= o) h = max(h, y);
+  }
+  if (lane == 31) sm.hmax[w] = h;
+  long long nc = 0;
+  int rs = -1, anc = -1;
+  if (head) {
+    int best = INT_MAX;
+    for (int j = 0; j < a.nnb; ++j) {
+      int wv = key_slot(key, a.L, a.nb_slot[j]);
+      int r0 = a.G.row_ptr[wv], d = a.G.row_ptr[wv + 1] - r0;
+      if (d < best) {
+        best = d;
+        rs = r0;
+        anc = j;
+      }
+    }
+    nc = best;
+  }
+  sm.rs[tid] = rs;
+  sm.anc[tid] = anc;
+  sm.hvc[tid] = 0;
+  __syncthreads();
+  for (int i = 0; i < w; ++i) h = max(h, sm.hmax[i]);
+  sm.head[tid] = h;
+  block_exclusive_scan<BLOCK>(nc, sm.off, sm.warp);
+  const long long total = sm.off[BLOCK];
+  st.examined += (u64)total;
+  int vtotal = 0;
+  for (long long j0 = 0; j0 < total; j0 += BLOCK) {
+    const long long j = j0 + tid;
+    bool ok = false;
+    int e = 0, v = 0;
+    if (j < total) {
+      e = owner<BLOCK>(sm.off, j);
+      v = __ldg(a.G.col + sm.rs[e] + (j - sm.off[e]));
+      ok = a.degF == 0 || a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
+      if (ok) {
+        const K ekey = sm.key[e];
+        const int an = sm.anc[e];
+        for (int q = 0; q < a.nnb && ok; ++q)
+          if (q != an) ok = adjacent(a.G, key_slot(ekey, a.L, a.nb_slot[q]), v);
+      }
+    }
+    int tot;
+    const int rank = block_flag_rank<BLOCK>(ok, sm.wc, tot);
+    if (ok) {
+      const int pos = vtotal + rank;
+      if (pos < VCAP) sm.vbuf[pos] = v;
+      atomicAdd(&sm.hvc[e], 1);
+    }
+    vtotal += tot;
+  }
+  if (vtotal > VCAP) return false;  // uniform across the block
+  __syncthreads();
+  // each head's list starts after the lists of the heads before it (stream order)
+  block_exclusive_scan<BLOCK>(sm.hvc[tid], sm.off, sm.warp);
+  sm.hst[tid] = (int)sm.off[tid];
+  __syncthreads();
+  const int hd = sm.head[tid];
+  const long long mine = key != 0 ? sm.hvc[hd] : 0;
+  block_exclusive_scan<BLOCK>(mine, sm.off, sm.warp);
+  const long long total2 = sm.off[BLOCK];
+  for (long long j0 = 0; j0 < total2; j0 += BLOCK) {
+    const long long j = j0 + tid;
+    bool valid = false;
+    K okey = 0;
+    u64 oc = 0;
+    if (j < total2) {
+      const int e = owner<BLOCK>(sm.off, j);
+      const int v = sm.vbuf[sm.hst[sm.head[e]] + (int)(j - sm.off[e])];
+      const K ekey = sm.key[e];
+      const int t = key_trial(ekey, a.L);
+      const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+      valid = !((key_mask(ekey, a.L) >> cv) & 1u);
+      if (valid) {
+        okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
+        oc = sm.cnt[e];
+      }
+    }
+    emit<K, MODE, BLOCK>(a, sm, st, valid, okey, oc);
+  }
+  return true;
+}
+
+template <typename K, int MODE, int BLOCK, int GROUPED>
 __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_count,
                                                       const u64 *blk_base) {
-  __shared__ long long s_off[BLOCK + 1];
-  __shared__ long long s_warp[BLOCK / 32];
-  __shared__ K s_key[BLOCK];
-  __shared__ u64 s_cnt[BLOCK];
-  __shared__ int s_rs[BLOCK];
-  __shared__ int s_anc[BLOCK];
-  __shared__ int s_wc[BLOCK / 32];
-  __shared__ u64 s_red[BLOCK / 32];
-
+  constexpr int VCAP = GROUPED ? 2048 : 1;
+  __shared__ IntroSmem<K, BLOCK, VCAP> sm;
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
-  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
   const u64 bound = table_bound<K>(a.in);
-  const u64 capmask = a.out.cap - 1;
-  u64 produced = 0, fresh = 0, examined = 0;
-  u64 cursor = (MODE == 1) ? blk_base[blockIdx.x] : 0;
-  bool full = false;
-
+  EmitState st;
+  if (MODE == 1) st.cursor = blk_base[blockIdx.x];
   for (u64 base = (u64)blockIdx.x * BLOCK; base < bound; base += (u64)gridDim.x * BLOCK) {
-    u64 i = base + threadIdx.x;
-    long long nc = 0;
-    int rs = -1, anc = -1;
+    const u64 i = base + threadIdx.x;
     K key = 0;
     u64 c = 0;
-    if (i < bound) {
-      load_slot(in, i, key, c);
-      if (key != 0) {
-        if (a.nnb == 0) {
-          nc = a.G.n;
-        } else {
-          int best = INT_MAX;
-          for (int j = 0; j < a.nnb; ++j) {
-            int w = key_slot(key, a.L, a.nb_slot[j]);
-            int r0 = a.G.row_ptr[w], d = a.G.row_ptr[w + 1] - r0;
-            if (d < best) {
-              best = d;
-              rs = r0;
-              anc = j;
-            }
-          }
-          nc = best;
-        }
-      }
-    }
-    s_key[threadIdx.x] = key;
-    s_cnt[threadIdx.x] = c;
-    s_rs[threadIdx.x] = rs;
-    s_anc[threadIdx.x] = anc;
-    block_exclusive_scan<BLOCK>(nc, s_off, s_warp);
-    const long long total = s_off[BLOCK];
-    examined += (u64)total;
-
-    for (long long j0 = 0; j0 < total; j0 += BLOCK) {
-      long long j = j0 + threadIdx.x;
-      bool valid = false;
-      K okey = 0;
-      u64 oc = 0;
-      if (j < total) {
-        int lo = 0, hi = BLOCK - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (s_off[mid] <= j) lo = mid;
-          else hi = mid - 1;
-        }
-        const int e = lo;
-        const long long r = j - s_off[e];
-        const int v = s_rs[e] >= 0 ? __ldg(a.G.col + s_rs[e] + r) : (int)r;
-        const K ekey = s_key[e];
-        const int t = key_trial(ekey, a.L);
-        const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
-        valid = !((key_mask(ekey, a.L) >> cv) & 1u);
-        if (valid && a.degF) valid = a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
-        if (valid) {
-          const int an = s_anc[e];
-          for (int q = 0; q < a.nnb && valid; ++q)
-            if (q != an) valid = adjacent(a.G, key_slot(ekey, a.L, a.nb_slot[q]), v);
-        }
-        if (valid) {
-          okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
-          oc = s_cnt[e];
-        }
-      }
-      if (MODE == 0) {
-        produced += valid;
-      } else if (MODE == 1) {
-        int tot;
-        int rank = block_flag_rank<BLOCK>(valid, s_wc, tot);
-        if (valid) {
-          u64 pos = cursor + (u64)rank;
-          if (pos < a.out.cap) store_slot(out, pos, okey, oc);
-          else full = true;
-        }
-        cursor += (u64)tot;
-      } else {
-        if (valid) {
-          ++produced;
-          int r = hash_add(out, capmask, key_remove(okey, a.L, a.q), oc);
-          if (r > 0) ++fresh;
-          if (r < 0) full = true;
-        }
-      }
-    }
+    if (i < bound) load_slot(in, i, key, c);
+    sm.key[threadIdx.x] = key;
+    sm.cnt[threadIdx.x] = c;
+    if (!GROUPED || !grouped_tile<K, MODE, BLOCK, VCAP>(a, sm, st))
+      plain_tile<K, MODE, BLOCK>(a, sm, st);
     __syncthreads();  // the next tile overwrites the shared arrays
   }
-  if (full) atomicOr(a.err, kErrOverflow);
+  if (st.full) atomicOr(a.err, kErrOverflow);
   if (MODE == 0) {
-    u64 s = block_sum<BLOCK>(produced, s_red);
+    u64 s = block_sum<BLOCK>(st.produced, sm.red);
+    u64 x = block_sum<BLOCK>(st.examined, sm.red);
     if (threadIdx.x == 0) {
       blk_count[blockIdx.x] = s;
-      if (examined) atomicAdd(a.cand, examined);
+      if (x) atomicAdd(a.cand, x);
     }
   } else if (MODE == 2) {
-    u64 s = block_sum<BLOCK>(produced, s_red);
+    u64 s = block_sum<BLOCK>(st.produced, sm.red);
     if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
-    u64 f = block_sum<BLOCK>(fresh, s_red);
+    u64 f = block_sum<BLOCK>(st.fresh, sm.red);
     if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
+  }
+}
+
+// ---- stable LSD radix sort of table records by the images of chosen bag slots ---------------
+// Sorts the nonempty records of a table (holes are dropped) by the tuple of the G-vertices in
+// slots `sl[0..nsl)` (first slot most significant), eight bits per pass.  Each of G blocks owns
+// one contiguous range of the input; per pass: a per-block digit histogram, one exclusive scan
+// over (digit, block), and a scatter that ranks equal digits in input order (warp match plus
+// per-warp counts), so every pass is stable.
+struct TupleSpec {
+  KeyLayout L;
+  int nsl;
+  int sl[kMaxBag];
+};
+
+template <typename K>
+__device__ __forceinline__ u64 spec_tuple(K key, const TupleSpec &sp) {
+  u64 t = 0;
+#pragma unroll
+  for (int j = 0; j < kMaxBag; ++j)
+    if (j < sp.nsl) t = (t << sp.L.nb) | (u64)key_slot(key, sp.L, sp.sl[j]);
+  return t;
+}
+
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) sort_hist_kernel(TupleSpec sp, const void *src, u64 n,
+                                                          int shift, u64 *hist) {
+  __shared__ unsigned s_h[256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  for (int d = threadIdx.x; d < 256; d += BLOCK) s_h[d] = 0;
+  __syncthreads();
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (u64 i = lo + threadIdx.x; i < hi; i += BLOCK) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    atomicAdd(&s_h[(spec_tuple(key, sp) >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += BLOCK) hist[(u64)d * G + blockIdx.x] = s_h[d];
+}
+
+// exclusive scan of m values in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) sort_scan_kernel(u64 *v, u64 m) {
+  __shared__ u64 s[1024];
+  const u64 per = (m + 1023) / 1024;
+  const u64 lo = threadIdx.x * per, hi = min(m, lo + per);
+  u64 sum = 0;
+  for (u64 i = lo; i < hi; ++i) sum += v[i];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    u64 y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += y;
+    __syncthreads();
+  }
+  u64 run = s[threadIdx.x] - sum;
+  for (u64 i = lo; i < hi; ++i) {
+    u64 x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(TupleSpec sp, const void *src, u64 n,
+                                                             int shift, const u64 *off,
+                                                             void *dst) {
+  constexpr int W = BLOCK / 32;
+  __shared__ unsigned s_wc[W][256];
+  __shared__ unsigned s_run[256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int d = tid; d < 256; d += BLOCK) {
+    s_run[d] = 0;
+    for (int x = 0; x < W; ++x) s_wc[x][d] = 0;
+  }
+  __syncthreads();
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (u64 base = lo; base < hi; base += BLOCK) {
+    const u64 i = base + tid;
+    K key = 0;
+    u64 c = 0;
+    if (i < hi) load_slot(in, i, key, c);
+    const bool valid = key != 0;
+    const int d = valid ? (int)((spec_tuple(key, sp) >> shift) & 255u) : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && lane == __ffs(peers) - 1) s_wc[w][d] = __popc(peers);
+    __syncthreads();
+    for (int dd = tid; dd < 256; dd += BLOCK) {
+      unsigned acc = s_run[dd];
+      for (int x = 0; x < W; ++x) {
+        unsigned cnt = s_wc[x][dd];
+        s_wc[x][dd] = acc;
+        acc += cnt;
+      }
+      s_run[dd] = acc;
+    }
+    __syncthreads();
+    if (valid) store_slot(out, off[(u64)d * G + blockIdx.x] + s_wc[w][d] + rank, key, c);
+    __syncthreads();
+    for (int dd = tid; dd < 256; dd += BLOCK)
+      for (int x = 0; x < W; ++x) s_wc[x][dd] = 0;
+    __syncthreads();
   }
 }
 
@@ -456,7 +713,7 @@ __global__ void __launch_bounds__(BLOCK) forget_kernel(ForgetArgs a) {
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
   const u64 bound = table_bound<K>(a.in);
-  const u64 capmask = a.out.cap - 1;
+  const u64 ocap = a.out.cap;
   u64 fresh = 0;
   bool full = false;
   for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
@@ -464,7 +721,7 @@ __global__ void __launch_bounds__(BLOCK) forget_kernel(ForgetArgs a) {
     u64 c;
     load_slot(in, i, key, c);
     if (key == 0) continue;
-    int r = hash_add(out, capmask, key_remove(key, a.L, a.q), c);
+    int r = hash_add(out, ocap, key_remove(key, a.L, a.q), c);
     if (r > 0) ++fresh;
     if (r < 0) full = true;
   }
@@ -485,14 +742,14 @@ __global__ void __launch_bounds__(BLOCK) join_build_kernel(JoinArgs a) {
   const Slot<K> *bt = reinterpret_cast<const Slot<K> *>(a.build.slots);
   Slot<K> *idx = reinterpret_cast<Slot<K> *>(a.index);
   const u64 bound = table_bound<K>(a.build);
-  const u64 capmask = a.index_cap - 1;
+  const u64 icap = a.index_cap;
   bool full = false;
   for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
     K key;
     u64 c;
     load_slot(bt, i, key, c);
     if (key == 0) continue;
-    long long h = hash_claim(idx, capmask, phi_key(key, a.L));
+    long long h = hash_claim(idx, icap, phi_key(key, a.L));
     if (h < 0) {
       full = true;
       continue;
@@ -510,7 +767,7 @@ __global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
   const Slot<K> *idx = reinterpret_cast<const Slot<K> *>(a.index);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
   const u64 bound = table_bound<K>(a.probe);
-  const u64 icapmask = a.index_cap - 1, ocapmask = a.out.cap - 1;
+  const u64 icap = a.index_cap, ocap = a.out.cap;
   const K cmask = (K)((1ull << a.L.k) - 1ull);
   u64 pairs = 0, fresh = 0;
   bool full = false;
@@ -519,7 +776,7 @@ __global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
     u64 c2;
     load_slot(pt, i, key, c2);
     if (key == 0) continue;
-    long long h = hash_find(idx, icapmask, phi_key(key, a.L));
+    long long h = hash_find(idx, icap, phi_key(key, a.L));
     if (h < 0) continue;
     const int t = key_trial(key, a.L);
     uint32_t bagc = 0;
@@ -537,7 +794,7 @@ __global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
       if ((C1 & C2) == bagc) {
         ++pairs;
         if (MODE == 1) {
-          int r = hash_add(out, ocapmask, (key & ~cmask) | (K)(C1 | C2), c1 * c2);
+          int r = hash_add(out, ocap, (key & ~cmask) | (K)(C1 | C2), c1 * c2);
           if (r > 0) ++fresh;
           if (r < 0) full = true;
         }
@@ -600,12 +857,41 @@ int grid_for(const DevInfo &d, int block) {
 }
 
 template <typename K, int BLOCK>
-int intro_dispatch(cudaStream_t s, const DevInfo &d, int mode, const IntroArgs &a, u64 *blk_count,
-                   const u64 *blk_base) {
+int intro_dispatch(cudaStream_t s, const DevInfo &d, int mode, int grouped, const IntroArgs &a,
+                   u64 *blk_count, const u64 *blk_base) {
   int grid = grid_for(d, BLOCK);
-  if (mode == 0) intro_kernel<K, 0, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
-  else if (mode == 1) intro_kernel<K, 1, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
-  else intro_kernel<K, 2, BLOCK><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base);
+#define CC_LAUNCH(M, G) intro_kernel<K, M, BLOCK, G><<<grid, BLOCK, 0, s>>>(a, blk_count, blk_base)
+  if (grouped) {
+    if (mode == 0) CC_LAUNCH(0, 1);
+    else if (mode == 1) CC_LAUNCH(1, 1);
+    else CC_LAUNCH(2, 1);
+  } else {
+    if (mode == 0) CC_LAUNCH(0, 0);
+    else if (mode == 1) CC_LAUNCH(1, 0);
+    else CC_LAUNCH(2, 0);
+  }
+#undef CC_LAUNCH
+  return (int)cudaGetLastError();
+}
+
+template <typename K>
+int tuple_sort_impl(cudaStream_t s, const DevInfo &d, const TupleSpec &sp, const void *src,
+                    u64 n_src, u64 n, void *buf_a, void *buf_b, u64 *hist, int *which) {
+  const int G = grid_for(d, 256);
+  const int bits = sp.nsl * sp.L.nb;
+  const void *in = src;
+  u64 n_in = n_src;
+  void *bufs[2] = {buf_a, buf_b};
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    sort_hist_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
+    sort_scan_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
+    sort_scatter_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur]);
+    in = bufs[cur];
+    n_in = n;
+    cur ^= 1;
+  }
+  *which = cur ^ 1;  // buffer written last
   return (int)cudaGetLastError();
 }
 
@@ -632,15 +918,15 @@ int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a) {
   return (int)cudaGetLastError();
 }
 
-int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int block,
-                     const IntroArgs &a, u64 *blk) {
+int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int grouped,
+                     int block, const IntroArgs &a, u64 *blk) {
   int grid = grid_for(d, block);
   u64 *cnt = blk, *base = blk + grid, *total = blk + 2 * grid;
   int r = 0;
-#define CC_INTRO(B)                                                              \
-  if (block == B) {                                                              \
-    r = kw == 1 ? intro_dispatch<u64, B>(s, d, mode, a, cnt, base)               \
-                : intro_dispatch<u128, B>(s, d, mode, a, cnt, base);             \
+#define CC_INTRO(B)                                                                \
+  if (block == B) {                                                                \
+    r = kw == 1 ? intro_dispatch<u64, B>(s, d, mode, grouped, a, cnt, base)        \
+                : intro_dispatch<u128, B>(s, d, mode, grouped, a, cnt, base);      \
   } else
   CC_INTRO(128) CC_INTRO(256) CC_INTRO(512) { return (int)cudaErrorInvalidValue; }
 #undef CC_INTRO
@@ -650,6 +936,24 @@ int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int blo
     r = (int)cudaGetLastError();
   }
   return r;
+}
+
+int sort_grid(const DevInfo &d) { return grid_for(d, 256); }
+
+int launch_tuple_sort(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L, int nsl,
+                      const int *slots, const void *src, unsigned long long n_src,
+                      unsigned long long n, void *buf_a, void *buf_b, unsigned long long *hist,
+                      int *which) {
+  TupleSpec sp;
+  sp.L = L;
+  sp.nsl = nsl;
+  for (int j = 0; j < nsl; ++j) sp.sl[j] = slots[j];
+  if (n == 0 || nsl == 0) {
+    *which = -1;
+    return 0;
+  }
+  return kw == 1 ? tuple_sort_impl<u64>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
+                 : tuple_sort_impl<u128>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
 }
 
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a) {

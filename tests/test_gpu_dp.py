@@ -163,12 +163,29 @@ def test_dp_block_sizes(ctx, block):
 
 
 def test_dp_wide_keys(ctx):
-    """k + max_bag * ceil(log2 n) + ceil(log2 trials) > 64: 128-bit keys."""
-    g = synth.barabasi_albert(3000, 3, 4)
-    pat = synth.random_partial_ktree(8, 3, 2)
-    colours = oracle.colors(3000, 5, 20, seed=8)
-    _check_small(ctx, g, pat, colours, 20, True, 0, tables=True)
-    _check_small(ctx, g, pat, colours, 20, True, 1, tables=False)
+    """k + max_bag * ceil(log2 n) + ceil(log2 trials) > 64: 128-bit keys (14 + 3*17 + 2 bits)."""
+    g = synth.erdos_renyi(100000, 2.0 / 99999, 4)
+    pat = synth.cycle_pattern(5)
+    colours = oracle.colors(100000, 3, 14, seed=8)
+    _check_small(ctx, g, pat, colours, 14, True, 0, tables=True)
+    _check_small(ctx, g, pat, colours, 14, True, 1, tables=False)
+
+
+@pytest.mark.parametrize("name", ["C4", "C5", "G23", "K4", "T3", "C"])
+def test_grouped_equals_plain(ctx, name):
+    """Sorting the child by bag-neighbour images and sharing candidate lists changes nothing."""
+    pat = PATTERNS[name]
+    nF = pat[0]
+    g = synth.barabasi_albert(2000, 4, 3)
+    colours = oracle.colors(2000, 6, nF, seed=21)
+    out = []
+    for group in (0, 1):
+        r = gpu_dp(ctx, g, pat, colours=colours, k=nF, group=group)
+        out.append((r["count"].copy(), r["sizes"].copy()))
+        release(ctx, r)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    ref = oracle.run_dp(g, pat, colours, nF)
+    assert np.array_equal(out[1][0], ref.count)
 
 
 def test_dp_edge_cases(ctx):
