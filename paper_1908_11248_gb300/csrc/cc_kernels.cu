@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(u64 *v, u64 m) {
 template <typename K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(TupleSpec sp, const void *src, u64 n,
                                                              int shift, const u64 *off,
-                                                             void *dst) {
+                                                             void *dst, u64 dst_cap) {
   constexpr int W = BLOCK / 32;
   __shared__ unsigned s_wc[W][256];
   __shared__ unsigned s_run[256];
@@ -686,7 +686,10 @@ __global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(TupleSpec sp, const
       s_run[dd] = acc;
     }
     __syncthreads();
-    if (valid) store_slot(out, off[(u64)d * G + blockIdx.x] + s_wc[w][d] + rank, key, c);
+    if (valid) {
+      const u64 pos = off[(u64)d * G + blockIdx.x] + s_wc[w][d] + rank;
+      if (pos < dst_cap) store_slot(out, pos, key, c);  // more records than announced: dropped
+    }
     __syncthreads();
     for (int dd = tid; dd < 256; dd += BLOCK)
       for (int x = 0; x < W; ++x) s_wc[x][dd] = 0;
@@ -886,7 +889,7 @@ int tuple_sort_impl(cudaStream_t s, const DevInfo &d, const TupleSpec &sp, const
   for (int shift = 0; shift < bits; shift += 8) {
     sort_hist_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
     sort_scan_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
-    sort_scatter_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur]);
+    sort_scatter_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur], n);
     in = bufs[cur];
     n_in = n;
     cur ^= 1;
