@@ -130,8 +130,11 @@ int cc_release_colors(cc_ctx *ctx, int32_t coloring_id);
 typedef struct {
   int32_t degree_filter; /* map y to x only if deg_G(x) >= deg_F(y) (Section 3.2); 1 = on     */
   int32_t retain;        /* keep every node table for cc_enumerate / cc_table_dump            */
-  int32_t fuse;          /* 1: an introduce followed by a forget runs as one kernel, and its  */
-                         /*    table is never stored (its size is still counted)              */
+  int32_t fuse;          /* introduce followed by forget: 0 each node stores its own table;   */
+                         /* 1 the introduce adds its entries, projected, into the forget's     */
+                         /*   hash table; 2 (default) it writes them projected and densely,    */
+                         /*   they are sorted and equal keys reduced.  With 1 and 2 the        */
+                         /*   introduce's table is never stored (its size is still counted)    */
   int32_t use_graph;     /* 1: replay the node kernels from a captured CUDA graph when the     */
                          /*    plan's capacities are known (falls back to planning otherwise)  */
   float load_factor;     /* hash-table fill target in (0, 0.9]; 0 = library default           */
@@ -141,7 +144,7 @@ typedef struct {
                          /*    its child by their images and shares candidate lists per run    */
 } cc_run_opts;
 
-/* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 1, use_graph 0, load factor
+/* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
  * 0.5, block 256, profile 0, group 1). */
 void cc_default_opts(cc_run_opts *opts);
 
@@ -199,7 +202,8 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 #define CC_K_JOIN_COUNT 7
 #define CC_K_JOIN_WRITE 8
 #define CC_K_ROOT 9
-#define CC_K_SORT 10 /* all passes of one child sort by bag-neighbour images */
+#define CC_K_SORT 10   /* all passes of one radix sort of a table's records */
+#define CC_K_REDUCE 11 /* reduce-by-key of sorted records (a forget's merge) */
 
 /* Per-launch device times of a run made with profile = 1, in launch order: node id, kernel
  * kind (CC_K_*), milliseconds between CUDA events recorded on the context's stream just before

@@ -33,7 +33,7 @@ EXPORTS = [
     "cc_nice_decomposition", "cc_check_graph",
 ]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
-                "join_build", "join_count", "join_write", "root", "sort"]
+                "join_build", "join_count", "join_write", "root", "sort", "reduce"]
 
 
 class CCError(RuntimeError):

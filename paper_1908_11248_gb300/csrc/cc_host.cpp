@@ -128,6 +128,9 @@ struct NodeTable {
   u64 cap = 0;
   int hashed = 0;
   bool stored = false;
+  // a dense table sorted with these bag slots most significant (sort_n == 0: no known order)
+  int sort_n = 0;
+  int sort_slots[kMaxBag] = {};
 };
 
 struct Timing {
@@ -531,7 +534,7 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
   R->sizes.assign(N, 0);
   std::vector<bool> made(N, false);
   const int grid = cc::intro_grid(c->dev, block);
-  int rc = ensure_scratch(c, 2 * (size_t)grid + 8);
+  int rc = ensure_scratch(c, 2 * (size_t)std::max(grid, cc::sort_grid(c->dev)) + 8);
   if (rc) return rc;
   u64 *blk = c->d_scratch;
   CUDA_OK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
@@ -575,6 +578,70 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
     return CC_OK;
   };
 
+  // true if table t is sorted with exactly the slots sl[0..n) (in any order) most significant
+  auto sorted_by = [&](const cc::NodeTable &t, int n, const int *sl) {
+    if (t.hashed || t.sort_n < n) return false;
+    for (int j = 0; j < n; ++j) {
+      bool in = false;
+      for (int i = 0; i < n; ++i) in = in || t.sort_slots[i] == sl[j];
+      if (!in) return false;
+    }
+    return true;
+  };
+  // full sort order for the table of forget node f: when the next node introduces a vertex
+  // with bag neighbours, their slots come first so that its runs are contiguous
+  auto forget_order = [&](int f) {
+    const NiceNode &fn = P.nodes[f];
+    cc::SortSpec sp{};
+    sp.L = R->L;
+    sp.b = (int)fn.bag.size();
+    sp.full = 1;
+    sp.nsl = 0;
+    bool used[cc::kMaxBag] = {};
+    const int g = fn.parent;
+    if (g >= 0 && P.nodes[g].type == 1)
+      for (int s = 0; s < sp.b; ++s)
+        if (P.adj[P.nodes[g].vertex] >> fn.bag[s] & 1u) {
+          sp.order[sp.nsl++] = s;
+          used[s] = true;
+        }
+    int o = sp.nsl;
+    for (int s = 0; s < sp.b; ++s)
+      if (!used[s]) sp.order[o++] = s;
+    sp.bits = sp.b * R->L.nb + R->L.tb + R->L.k;
+    return sp;
+  };
+  // sorts the nonempty records of src (n_src slots, m nonempty) into a new buffer *out
+  auto sort_records = [&](int node, const cc::SortSpec &sp, const void *src, u64 n_src, u64 m,
+                          void **out) -> int {
+    const size_t rb = cc::slot_bytes(R->kw);
+    void *ba = c->arena.alloc(std::max<u64>(1, m) * rb);
+    void *bb = c->arena.alloc(std::max<u64>(1, m) * rb);
+    u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev));
+    if (!ba || !bb || !hist) {
+      c->arena.release(ba);
+      c->arena.release(bb);
+      c->arena.release(hist);
+      return CC_ENOMEM;
+    }
+    int which = 0;
+    int r = timed(node, CC_K_SORT, 3 * cc::sort_passes(sp), [&] {
+      return cc::launch_sort_records(c->stream, c->dev, R->kw, sp, src, n_src, m, ba, bb, hist,
+                                     &which);
+    });
+    c->arena.release(hist);
+    if (which < 0) {  // nothing to sort: copy through
+      c->arena.release(bb);
+      if (!r && m) r = cudaMemcpyAsync(ba, src, m * rb, cudaMemcpyDeviceToDevice, c->stream)
+                          ? CC_ECUDA : CC_OK;
+      *out = ba;
+      return r;
+    }
+    *out = which ? bb : ba;
+    c->arena.release(which ? ba : bb);
+    return r;
+  };
+
   for (int x = 0; x < N; ++x) {
     if (made[x]) continue;
     const NiceNode &nd = P.nodes[x];
@@ -603,34 +670,22 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       a.err = c->d_err;
       a.valid = R->d_counters + x;
       a.cand = blk + 2 * grid + 1;
-      // several bag neighbours: sort the child by their images so runs share candidate lists
+      // several bag neighbours: the child must come in runs of equal images of those slots so
+      // that a run shares one candidate list; sort it unless its order already starts with them
       const int grouped = R->opts.group && a.nnb >= 2 && a.nnb * R->L.nb <= 64 && R->sizes[y] > 0;
       void *sorted = nullptr;
-      if (grouped) {
+      if (grouped && !sorted_by(R->tables[y], a.nnb, a.nb_slot)) {
         const u64 m = R->sizes[y];
         const u64 n_src = R->tables[y].hashed ? R->tables[y].cap : m;
-        const size_t rb = cc::slot_bytes(R->kw);
-        void *ba = c->arena.alloc(m * rb), *bb = c->arena.alloc(m * rb);
-        u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev));
-        if (!ba || !bb || !hist) {
-          c->arena.release(ba);
-          c->arena.release(bb);
-          c->arena.release(hist);
-          return CC_ENOMEM;
-        }
-        int which = 0;
-        const int passes = (a.nnb * R->L.nb + 7) / 8;
-        rc = timed(x, CC_K_SORT, 3 * passes, [&] {
-          return cc::launch_tuple_sort(c->stream, c->dev, R->kw, R->L, a.nnb, a.nb_slot,
-                                       R->tables[y].slots, n_src, m, ba, bb, hist, &which);
-        });
-        c->arena.release(hist);
-        sorted = which ? bb : ba;
-        c->arena.release(which ? ba : bb);
-        if (rc) {
-          c->arena.release(sorted);
-          return rc;
-        }
+        cc::SortSpec sp{};
+        sp.L = R->L;
+        sp.b = a.b_in;
+        sp.nsl = a.nnb;
+        for (int j = 0; j < a.nnb; ++j) sp.order[j] = a.nb_slot[j];
+        sp.full = 0;
+        sp.bits = a.nnb * R->L.nb;
+        rc = sort_records(x, sp, R->tables[y].slots, n_src, m, &sorted);
+        if (rc) return rc;
         a.in.slots = sorted;
         a.in.cap = m;
         a.in.hashed = 0;
@@ -652,8 +707,8 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       if (R->opts.profile) R->timings.back().candidates = cand;
       R->sizes[x] = total;
       const int f = nd.parent;
-      const bool fuse = R->opts.fuse && f >= 0 && P.nodes[f].type == 2;
-      if (fuse) {
+      const int fuse = (f >= 0 && P.nodes[f].type == 2) ? R->opts.fuse : 0;
+      if (fuse == 1) {  // add projected entries into the forget's hash table
         rc = new_hash(f, total);
         if (rc) return rc;
         a.out = desc(f);
@@ -671,11 +726,52 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         if (f == N - 1) break;
         continue;
       }
+      if (fuse == 2) {  // write projected entries densely, sort them, reduce equal keys
+        const size_t rb = cc::slot_bytes(R->kw);
+        const u64 cap = std::max<u64>(1, total);
+        void *buf = c->arena.alloc(cap * rb);
+        if (!buf) return CC_ENOMEM;
+        cc::TableDesc tmp{buf, cap, blk + 2 * grid + 3, 0};
+        CUDA_OK(cudaMemcpyAsync(tmp.count, blk + 2 * grid, sizeof(u64), cudaMemcpyDeviceToDevice,
+                                c->stream));
+        a.out = tmp;
+        a.proj_q = pos_in(nd.bag, P.nodes[f].vertex);
+        rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
+          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
+        });
+        if (R->opts.profile && !rc) R->timings.back().candidates = cand;
+        if (!rc) release_child(y);
+        cc::SortSpec sp = forget_order(f);
+        void *srt = nullptr;
+        if (!rc) rc = sort_records(f, sp, buf, total, total, &srt);
+        c->arena.release(buf);
+        if (rc) return rc;
+        void *out = c->arena.alloc(cap * rb);
+        if (!out) {
+          c->arena.release(srt);
+          return CC_ENOMEM;
+        }
+        rc = timed(f, CC_K_REDUCE, 3, [&] {
+          return cc::launch_reduce(c->stream, c->dev, R->kw, srt ? srt : buf, total, blk, out,
+                                   R->d_counters + f);
+        });
+        c->arena.release(srt);
+        if (rc) return rc;
+        R->tables[f] = {out, cap, 0, true};
+        R->tables[f].sort_n = sp.full ? sp.b : 0;
+        for (int j = 0; j < sp.b; ++j) R->tables[f].sort_slots[j] = sp.order[j];
+        made[f] = true;
+        rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
+        if (rc) return rc;
+        if (f == N - 1) break;
+        continue;
+      }
       u64 cap = std::max<u64>(1, total);
       void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
       if (!p) return CC_ENOMEM;
       R->tables[x] = {p, cap, 0, true};
       a.out = desc(x);
+      a.proj_q = -1;
       CUDA_OK(cudaMemcpyAsync(R->d_counters + x, blk + 2 * grid, sizeof(u64),
                               cudaMemcpyDeviceToDevice, c->stream));
       rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
@@ -833,6 +929,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->block = 256;
   o->profile = 0;
   o->group = 1;
+  o->fuse = 2;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {

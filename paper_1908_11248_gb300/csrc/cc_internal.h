@@ -65,6 +65,7 @@ struct IntroArgs {
   int degF;                  // minimum host degree of u's image (0 = off)
   TableDesc out;             // dense (mode 1) or hashed (mode 2) output
   int q;                     // mode 2: slot (in the new bag) of the vertex the parent forgets
+  int proj_q;                // mode 1: if >= 0, write keys with this slot removed
   unsigned long long *valid; // mode 2: number of introduce entries produced
   unsigned long long *cand;  // mode 0: number of candidate vertices examined
   int *err;
@@ -119,15 +120,30 @@ int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a);
 int intro_grid(const DevInfo &d, int block);
 int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int grouped, int block,
                      const IntroArgs &a, unsigned long long *blk);
-// Stable sort of the nonempty records of `src` (n_src slots, n of them nonempty) by the G-vertices
-// of bag slots slots[0..nsl) (nsl * nb <= 64 bits), alternating between buf_a and buf_b (n
-// records each); *which = 0 or 1 names the buffer holding the result.  hist needs
-// 256 * sort_grid(d) words.
+// Sort order of table records: the G-vertices of bag slots order[0..nsl) first (most
+// significant); with full = 1 the remaining slots order[nsl..b) follow, then the trial and the
+// colour set, so that equal keys are adjacent.  bits = total sort-key bits.
+struct SortSpec {
+  KeyLayout L;
+  int b;
+  int nsl;
+  int order[kMaxBag];
+  int full;
+  int bits;
+};
+// Stable LSD radix sort of the nonempty records of `src` (n_src slots, n of them nonempty) into
+// buf_a / buf_b (n records each); *which (0 or 1) names the buffer holding the result.  hist
+// needs 256 * sort_grid(d) words.
 int sort_grid(const DevInfo &d);
-int launch_tuple_sort(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L, int nsl,
-                      const int *slots, const void *src, unsigned long long n_src,
-                      unsigned long long n, void *buf_a, void *buf_b, unsigned long long *hist,
-                      int *which);
+int sort_passes(const SortSpec &sp);
+int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
+                        const void *src, unsigned long long n_src, unsigned long long n,
+                        void *buf_a, void *buf_b, unsigned long long *hist, int *which);
+// One record per run of equal keys of the sorted `src` (n records) with the summed count, written
+// densely to dst; *count receives the number of runs.  blk needs 2 * sort_grid(d) + 1 words.
+int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
+                  unsigned long long n, unsigned long long *blk, void *dst,
+                  unsigned long long *count);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
                 const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write

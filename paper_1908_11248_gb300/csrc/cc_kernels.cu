@@ -19,252 +19,13 @@
 #include <climits>
 #include <cstdint>
 
+#include "cc_device.cuh"
 #include "cc_internal.h"
 
 namespace cc {
 namespace {
 
-typedef unsigned long long u64;
-typedef unsigned __int128 u128;
-
-template <typename K>
-struct alignas(sizeof(K) == 8 ? 16 : 32) Slot {
-  K key;
-  u64 cnt;
-};
-
-// ---- key helpers ------------------------------------------------------------------------
-template <typename K>
-__device__ __forceinline__ K low_mask(int s) {
-  return s >= (int)(8 * sizeof(K)) ? ~(K)0 : (((K)1 << s) - (K)1);
-}
-
-template <typename K>
-__device__ __forceinline__ int key_slot(K key, const KeyLayout &L, int i) {
-  return (int)((key >> (L.k + i * L.nb)) & (K)((1ull << L.nb) - 1ull));
-}
-
-template <typename K>
-__device__ __forceinline__ uint32_t key_mask(K key, const KeyLayout &L) {
-  return (uint32_t)(key & (K)((1ull << L.k) - 1ull));
-}
-
-template <typename K>
-__device__ __forceinline__ int key_trial(K key, const KeyLayout &L) {
-  return L.tb ? (int)(key >> L.tpos) : 0;
-}
-
-template <typename K>
-__device__ __forceinline__ K key_trial_bits(K key, const KeyLayout &L) {
-  return L.tb ? (key >> L.tpos) << L.tpos : (K)0;
-}
-
-// insert vertex v as slot p of a bag that had b slots
-template <typename K>
-__device__ __forceinline__ K key_insert(K key, const KeyLayout &L, int p, int v) {
-  K body = key & low_mask<K>(L.tpos);
-  int lo = L.k + p * L.nb;
-  K lower = body & low_mask<K>(lo);
-  K upper = body >> lo;
-  return lower | ((K)(unsigned)v << lo) | (upper << (lo + L.nb)) | key_trial_bits(key, L);
-}
-
-// drop slot q
-template <typename K>
-__device__ __forceinline__ K key_remove(K key, const KeyLayout &L, int q) {
-  K body = key & low_mask<K>(L.tpos);
-  int lo = L.k + q * L.nb;
-  K lower = body & low_mask<K>(lo);
-  K upper = body >> (lo + L.nb);
-  return lower | (upper << lo) | key_trial_bits(key, L);
-}
-
-// MurmurHash3 64-bit finaliser (Appleby), a published bit mixer
-__device__ __forceinline__ u64 fmix64(u64 x) {
-  x ^= x >> 33;
-  x *= 0xff51afd7ed558ccdull;
-  x ^= x >> 33;
-  x *= 0xc4ceb9fe1a85ec53ull;
-  x ^= x >> 33;
-  return x;
-}
-__device__ __forceinline__ u64 key_hash(u64 k) { return fmix64(k); }
-__device__ __forceinline__ u64 key_hash(u128 k) { return fmix64((u64)k ^ fmix64((u64)(k >> 64))); }
-
-// ---- record load/store (16-byte vector accesses) ---------------------------------------
-__device__ __forceinline__ void load_slot(const Slot<u64> *s, u64 i, u64 &key, u64 &cnt) {
-  ulonglong2 r = reinterpret_cast<const ulonglong2 *>(s)[i];
-  key = r.x;
-  cnt = r.y;
-}
-__device__ __forceinline__ void load_slot(const Slot<u128> *s, u64 i, u128 &key, u64 &cnt) {
-  const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(s) + 2 * i;
-  ulonglong2 a = p[0];
-  key = ((u128)a.y << 64) | a.x;
-  cnt = p[1].x;
-}
-__device__ __forceinline__ void store_slot(Slot<u64> *s, u64 i, u64 key, u64 cnt) {
-  reinterpret_cast<ulonglong2 *>(s)[i] = make_ulonglong2(key, cnt);
-}
-__device__ __forceinline__ void store_slot(Slot<u128> *s, u64 i, u128 key, u64 cnt) {
-  ulonglong2 *p = reinterpret_cast<ulonglong2 *>(s) + 2 * i;
-  p[0] = make_ulonglong2((u64)key, (u64)(key >> 64));
-  p[1] = make_ulonglong2(cnt, 0ull);
-}
-
-template <typename K>
-__device__ __forceinline__ u64 table_bound(const TableDesc &t) {
-  if (t.hashed) return t.cap;
-  u64 c = *t.count;
-  return c < t.cap ? c : t.cap;
-}
-
-// ---- hash table (open addressing, linear probing, key claimed by compare-and-swap) -------
-// The home slot of a key is its 64-bit hash scaled to [0, cap) by a multiply-high (Lemire's
-// range reduction), so capacities need not be powers of two.
-__device__ __forceinline__ u64 home_slot(u64 h, u64 cap) { return __umul64hi(h, cap); }
-__device__ __forceinline__ u64 next_slot(u64 h, u64 cap) { return h + 1 == cap ? 0 : h + 1; }
-
-// Adds count c to key's record.  Returns 1 if the key was new, 0 if it was present, -1 if the
-// table is full.  A new key and its count are installed by one 128-bit compare-and-swap of the
-// whole (key, count) record; later additions are 64-bit atomic adds on the count.
-__device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 cap, u64 key, u64 c) {
-  u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
-    u64 cur = *reinterpret_cast<volatile u64 *>(&slots[h].key);  // 8-byte reads are atomic
-    if (cur == key) {
-      atomicAdd(&slots[h].cnt, c);
-      return 0;
-    }
-    if (cur == 0) {
-      u128 old = atomicCAS(reinterpret_cast<u128 *>(&slots[h]), (u128)0,
-                           (u128)key | ((u128)c << 64));
-      if (old == 0) return 1;
-      if ((u64)old == key) {
-        atomicAdd(&slots[h].cnt, c);
-        return 0;
-      }
-    }
-    h = next_slot(h, cap);
-  }
-  return -1;
-}
-
-__device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 cap, u128 key, u64 c) {
-  u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
-    // a 16-byte plain read is not guaranteed to be single-copy atomic: always compare-and-swap
-    u128 old = atomicCAS(&slots[h].key, (u128)0, key);
-    if (old == 0) {
-      atomicAdd(&slots[h].cnt, c);
-      return 1;
-    }
-    if (old == key) {
-      atomicAdd(&slots[h].cnt, c);
-      return 0;
-    }
-    h = next_slot(h, cap);
-  }
-  return -1;
-}
-
-// find-or-insert; returns the slot index or -1 if the table is full
-template <typename K>
-__device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 cap, K key) {
-  u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
-    K old = atomicCAS(&slots[h].key, (K)0, key);
-    if (old == 0 || old == key) return (long long)h;
-    h = next_slot(h, cap);
-  }
-  return -1;
-}
-
-// lookup in a table no thread is writing; -1 if absent
-template <typename K>
-__device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 cap, K key) {
-  u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
-    K cur;
-    u64 c;
-    load_slot(slots, h, cur, c);
-    if (cur == key) return (long long)h;
-    if (cur == 0) return -1;
-    h = next_slot(h, cap);
-  }
-  return -1;
-}
-
-// ---- block reductions -------------------------------------------------------------------
-template <int BLOCK>
-__device__ __forceinline__ u64 block_sum(u64 v, u64 *s_red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) s_red[w] = v;
-  __syncthreads();
-  u64 t = 0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < BLOCK / 32; ++i) t += s_red[i];
-  return t;  // valid in thread 0
-}
-
-// exclusive prefix of per-thread 64-bit values; s_off[BLOCK] receives the total
-template <int BLOCK>
-__device__ __forceinline__ void block_exclusive_scan(long long v, long long *s_off,
-                                                     long long *s_warp) {
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  long long x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    long long s = lane < BLOCK / 32 ? s_warp[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < BLOCK / 32) s_warp[lane] = s;  // inclusive warp totals
-  }
-  __syncthreads();
-  long long before = (w ? s_warp[w - 1] : 0) + x - v;
-  s_off[threadIdx.x] = before;
-  if (threadIdx.x == BLOCK - 1) s_off[BLOCK] = before + v;
-  __syncthreads();
-}
-
-// exclusive rank of a flag within the block (deterministic order), and the block's count
-template <int BLOCK>
-__device__ __forceinline__ int block_flag_rank(bool f, int *s_wc, int &total) {
-  unsigned bal = __ballot_sync(0xffffffffu, f);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();  // previous readers of s_wc are done
-  if (lane == 0) s_wc[w] = __popc(bal);
-  __syncthreads();
-  int before = 0;
-  total = 0;
-  for (int i = 0; i < BLOCK / 32; ++i) {
-    int c = s_wc[i];
-    before += i < w ? c : 0;
-    total += c;
-  }
-  return before + __popc(bal & ((1u << lane) - 1u));
-}
-
-__device__ __forceinline__ bool adjacent(const GraphDev &G, int a, int v) {
-  int lo = G.row_ptr[a], hi = G.row_ptr[a + 1];
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    int c = __ldg(G.col + mid);
-    if (c < v) lo = mid + 1;
-    else if (c > v) hi = mid;
-    else return true;
-  }
-  return false;
-}
+using namespace dev;
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) and the colouring of Section 2.1 -----------------
 __global__ void color_kernel(uint8_t *out, int32_t n, int32_t trials, int32_t k, uint32_t key0,
@@ -362,7 +123,9 @@ __device__ __forceinline__ void emit(const IntroArgs &a, S &sm, EmitState &st, b
     int rank = block_flag_rank<BLOCK>(valid, sm.wc, tot);
     if (valid) {
       u64 pos = st.cursor + (u64)rank;
-      if (pos < a.out.cap) store_slot(reinterpret_cast<Slot<K> *>(a.out.slots), pos, okey, oc);
+      if (pos < a.out.cap)
+        store_slot(reinterpret_cast<Slot<K> *>(a.out.slots), pos,
+                   a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
       else st.full = true;
     }
     st.cursor += (u64)tot;
@@ -415,7 +178,7 @@ __device__ __forceinline__ void plain_tile(const IntroArgs &a, S &sm, EmitState 
   sm.anc[threadIdx.x] = anc;
   block_exclusive_scan<BLOCK>(nc, sm.off, sm.warp);
   const long long total = sm.off[BLOCK];
-  st.examined += (u64)total;
+  if (threadIdx.x == 0) st.examined += (u64)total;  // block-uniform: count once
   for (long long j0 = 0; j0 < total; j0 += BLOCK) {
     const long long j = j0 + threadIdx.x;
     bool valid = false;
@@ -490,7 +253,7 @@ __device__ __forceinline__ bool grouped_tile(const IntroArgs &a, S &sm, EmitStat
   sm.head[tid] = h;
   block_exclusive_scan<BLOCK>(nc, sm.off, sm.warp);
   const long long total = sm.off[BLOCK];
-  st.examined += (u64)total;
+  if (threadIdx.x == 0) st.examined += (u64)total;  // block-uniform: count once
   int vtotal = 0;
   for (long long j0 = 0; j0 < total; j0 += BLOCK) {
     const long long j = j0 + tid;
@@ -581,119 +344,6 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
     if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
     u64 f = block_sum<BLOCK>(st.fresh, sm.red);
     if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
-  }
-}
-
-// ---- stable LSD radix sort of table records by the images of chosen bag slots ---------------
-// Sorts the nonempty records of a table (holes are dropped) by the tuple of the G-vertices in
-// slots `sl[0..nsl)` (first slot most significant), eight bits per pass.  Each of G blocks owns
-// one contiguous range of the input; per pass: a per-block digit histogram, one exclusive scan
-// over (digit, block), and a scatter that ranks equal digits in input order (warp match plus
-// per-warp counts), so every pass is stable.
-struct TupleSpec {
-  KeyLayout L;
-  int nsl;
-  int sl[kMaxBag];
-};
-
-template <typename K>
-__device__ __forceinline__ u64 spec_tuple(K key, const TupleSpec &sp) {
-  u64 t = 0;
-#pragma unroll
-  for (int j = 0; j < kMaxBag; ++j)
-    if (j < sp.nsl) t = (t << sp.L.nb) | (u64)key_slot(key, sp.L, sp.sl[j]);
-  return t;
-}
-
-template <typename K, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) sort_hist_kernel(TupleSpec sp, const void *src, u64 n,
-                                                          int shift, u64 *hist) {
-  __shared__ unsigned s_h[256];
-  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
-  for (int d = threadIdx.x; d < 256; d += BLOCK) s_h[d] = 0;
-  __syncthreads();
-  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
-  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  for (u64 i = lo + threadIdx.x; i < hi; i += BLOCK) {
-    K key;
-    u64 c;
-    load_slot(in, i, key, c);
-    if (key == 0) continue;
-    atomicAdd(&s_h[(spec_tuple(key, sp) >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += BLOCK) hist[(u64)d * G + blockIdx.x] = s_h[d];
-}
-
-// exclusive scan of m values in place (one block of 1024 threads)
-__global__ void __launch_bounds__(1024) sort_scan_kernel(u64 *v, u64 m) {
-  __shared__ u64 s[1024];
-  const u64 per = (m + 1023) / 1024;
-  const u64 lo = threadIdx.x * per, hi = min(m, lo + per);
-  u64 sum = 0;
-  for (u64 i = lo; i < hi; ++i) sum += v[i];
-  s[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    u64 y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
-    __syncthreads();
-    s[threadIdx.x] += y;
-    __syncthreads();
-  }
-  u64 run = s[threadIdx.x] - sum;
-  for (u64 i = lo; i < hi; ++i) {
-    u64 x = v[i];
-    v[i] = run;
-    run += x;
-  }
-}
-
-template <typename K, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(TupleSpec sp, const void *src, u64 n,
-                                                             int shift, const u64 *off,
-                                                             void *dst, u64 dst_cap) {
-  constexpr int W = BLOCK / 32;
-  __shared__ unsigned s_wc[W][256];
-  __shared__ unsigned s_run[256];
-  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
-  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int d = tid; d < 256; d += BLOCK) {
-    s_run[d] = 0;
-    for (int x = 0; x < W; ++x) s_wc[x][d] = 0;
-  }
-  __syncthreads();
-  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
-  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  for (u64 base = lo; base < hi; base += BLOCK) {
-    const u64 i = base + tid;
-    K key = 0;
-    u64 c = 0;
-    if (i < hi) load_slot(in, i, key, c);
-    const bool valid = key != 0;
-    const int d = valid ? (int)((spec_tuple(key, sp) >> shift) & 255u) : 256 + lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && lane == __ffs(peers) - 1) s_wc[w][d] = __popc(peers);
-    __syncthreads();
-    for (int dd = tid; dd < 256; dd += BLOCK) {
-      unsigned acc = s_run[dd];
-      for (int x = 0; x < W; ++x) {
-        unsigned cnt = s_wc[x][dd];
-        s_wc[x][dd] = acc;
-        acc += cnt;
-      }
-      s_run[dd] = acc;
-    }
-    __syncthreads();
-    if (valid) {
-      const u64 pos = off[(u64)d * G + blockIdx.x] + s_wc[w][d] + rank;
-      if (pos < dst_cap) store_slot(out, pos, key, c);  // more records than announced: dropped
-    }
-    __syncthreads();
-    for (int dd = tid; dd < 256; dd += BLOCK)
-      for (int x = 0; x < W; ++x) s_wc[x][dd] = 0;
-    __syncthreads();
   }
 }
 
@@ -877,27 +527,6 @@ int intro_dispatch(cudaStream_t s, const DevInfo &d, int mode, int grouped, cons
   return (int)cudaGetLastError();
 }
 
-template <typename K>
-int tuple_sort_impl(cudaStream_t s, const DevInfo &d, const TupleSpec &sp, const void *src,
-                    u64 n_src, u64 n, void *buf_a, void *buf_b, u64 *hist, int *which) {
-  const int G = grid_for(d, 256);
-  const int bits = sp.nsl * sp.L.nb;
-  const void *in = src;
-  u64 n_in = n_src;
-  void *bufs[2] = {buf_a, buf_b};
-  int cur = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
-    sort_hist_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
-    sort_scan_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
-    sort_scatter_kernel<K, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur], n);
-    in = bufs[cur];
-    n_in = n;
-    cur ^= 1;
-  }
-  *which = cur ^ 1;  // buffer written last
-  return (int)cudaGetLastError();
-}
-
 }  // namespace
 
 size_t slot_bytes(int kw) { return kw == 1 ? sizeof(Slot<u64>) : sizeof(Slot<u128>); }
@@ -939,24 +568,6 @@ int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int gro
     r = (int)cudaGetLastError();
   }
   return r;
-}
-
-int sort_grid(const DevInfo &d) { return grid_for(d, 256); }
-
-int launch_tuple_sort(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L, int nsl,
-                      const int *slots, const void *src, unsigned long long n_src,
-                      unsigned long long n, void *buf_a, void *buf_b, unsigned long long *hist,
-                      int *which) {
-  TupleSpec sp;
-  sp.L = L;
-  sp.nsl = nsl;
-  for (int j = 0; j < nsl; ++j) sp.sl[j] = slots[j];
-  if (n == 0 || nsl == 0) {
-    *which = -1;
-    return 0;
-  }
-  return kw == 1 ? tuple_sort_impl<u64>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
-                 : tuple_sort_impl<u128>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
 }
 
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a) {

@@ -1,0 +1,295 @@
+// Sorting and reduce-by-key of table records.
+//
+// The forget rule (Section 3.1) merges entries whose mappings become equal once the forgotten
+// vertex is dropped.  Here the introduce below a forget writes its entries already projected
+// (slot of the forgotten vertex removed), this file sorts them so that equal keys become
+// adjacent, and reduce-by-key sums the counts of each run into one entry.  The sort order is
+// chosen for the consumer: the G-vertices of the slots that the next introduce's vertex is
+// adjacent to come first, so that runs of equal bag-neighbour images are contiguous and share
+// their candidate lists (cc_kernels.cu, grouped introduce).
+//
+// Radix sort: least-significant digit first, 8 bits per pass, G blocks each owning one
+// contiguous range of the input.  A pass is a per-block digit histogram, one exclusive scan
+// over (digit, block) in digit-major order, and a scatter.  The scatter reads a tile of
+// records, ranks equal digits in input order (warp match plus per-warp counts), stages the tile
+// in shared memory grouped by digit and writes each digit's run with consecutive threads, so
+// global writes are coalesced.  Every pass is stable, hence so is the sort.
+#include <cstdint>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace cc {
+namespace {
+
+using namespace dev;
+
+template <typename SK, typename K>
+__device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
+  SK s = 0;
+  const int ns = sp.full ? sp.b : sp.nsl;
+#pragma unroll
+  for (int j = 0; j < kMaxBag; ++j)
+    if (j < ns) s = (s << sp.L.nb) | (SK)(unsigned)key_slot(key, sp.L, sp.order[j]);
+  if (sp.full) {
+    if (sp.L.tb) s = (s << sp.L.tb) | (SK)(unsigned)key_trial(key, sp.L);
+    s = (s << sp.L.k) | (SK)key_mask(key, sp.L);
+  }
+  return s;
+}
+
+template <typename K, typename SK, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) sort_hist_kernel(SortSpec sp, const void *src, u64 n,
+                                                          int shift, u64 *hist) {
+  __shared__ unsigned s_h[256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  for (int d = threadIdx.x; d < 256; d += BLOCK) s_h[d] = 0;
+  __syncthreads();
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (u64 i = lo + threadIdx.x; i < hi; i += BLOCK) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    atomicAdd(&s_h[(unsigned)(sort_key<SK>(key, sp) >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += BLOCK) hist[(u64)d * G + blockIdx.x] = s_h[d];
+}
+
+// exclusive scan of m values in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) scan_inplace_kernel(u64 *v, u64 m) {
+  __shared__ u64 s[1024];
+  const u64 per = (m + 1023) / 1024;
+  const u64 lo = threadIdx.x * per, hi = min(m, lo + per);
+  u64 sum = 0;
+  for (u64 i = lo; i < hi; ++i) sum += v[i];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    u64 y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += y;
+    __syncthreads();
+  }
+  u64 run = s[threadIdx.x] - sum;
+  for (u64 i = lo; i < hi; ++i) {
+    u64 x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+template <typename K, typename SK, int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const void *src, u64 n,
+                                                             int shift, const u64 *off,
+                                                             void *dst, u64 dst_cap) {
+  static_assert(BLOCK == 256, "one thread per digit");
+  constexpr int W = BLOCK / 32, TILE = BLOCK * ITEMS;
+  __shared__ Slot<K> s_stage[TILE];
+  __shared__ unsigned char s_sdig[TILE];
+  __shared__ unsigned s_wc[W][256];
+  __shared__ unsigned s_thist[256], s_tstart[256], s_trun[256], s_wsum[W];
+  __shared__ u64 s_brun[256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  s_brun[tid] = 0;
+  for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (u64 tb = lo; tb < hi; tb += TILE) {
+    K key[ITEMS];
+    u64 cnt[ITEMS];
+    int dig[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const u64 i = tb + (u64)j * BLOCK + tid;
+      key[j] = 0;
+      cnt[j] = 0;
+      if (i < hi) load_slot(in, i, key[j], cnt[j]);
+      dig[j] = key[j] != 0 ? (int)((unsigned)(sort_key<SK>(key[j], sp) >> shift) & 255u) : -1;
+    }
+    s_thist[tid] = 0;
+    s_trun[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+      if (dig[j] >= 0) atomicAdd(&s_thist[dig[j]], 1u);
+    __syncthreads();
+    {  // exclusive scan of the tile histogram, thread d owns digit d
+      unsigned v = s_thist[tid], x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[w] = x;
+      __syncthreads();
+      unsigned before = 0;
+      for (int q = 0; q < w; ++q) before += s_wsum[q];
+      s_tstart[tid] = before + x - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int d = dig[j];
+      const unsigned peers = __match_any_sync(0xffffffffu, d >= 0 ? d : 256 + lane);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      if (d >= 0 && lane == __ffs(peers) - 1) s_wc[w][d] = __popc(peers);
+      __syncthreads();
+      {
+        unsigned acc = s_trun[tid];
+        for (int x = 0; x < W; ++x) {
+          unsigned c = s_wc[x][tid];
+          s_wc[x][tid] = acc;
+          acc += c;
+        }
+        s_trun[tid] = acc;
+      }
+      __syncthreads();
+      if (d >= 0) {
+        const unsigned local = s_tstart[d] + s_wc[w][d] + rank;
+        s_stage[local].key = key[j];
+        s_stage[local].cnt = cnt[j];
+        s_sdig[local] = (unsigned char)d;
+      }
+      __syncthreads();
+      for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+      __syncthreads();
+    }
+    const unsigned tcount = s_tstart[255] + s_thist[255];
+    for (unsigned i = tid; i < tcount; i += BLOCK) {
+      const int d = s_sdig[i];
+      const u64 pos = off[(u64)d * G + blockIdx.x] + s_brun[d] + (i - s_tstart[d]);
+      if (pos < dst_cap) store_slot(out, pos, s_stage[i].key, s_stage[i].cnt);
+    }
+    __syncthreads();
+    s_brun[tid] += s_thist[tid];
+    __syncthreads();
+  }
+}
+
+// ---- reduce by key: equal keys are adjacent; one record per run with the summed count ------
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, u64 n, u64 *blk) {
+  __shared__ u64 s_red[BLOCK / 32];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  u64 heads = 0;
+  for (u64 i = lo + threadIdx.x; i < hi; i += BLOCK) {
+    K key, prev = 0;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (i > 0) load_slot(in, i - 1, prev, c);
+    heads += key != prev;
+  }
+  u64 s = block_sum<BLOCK>(heads, s_red);
+  if (threadIdx.x == 0) blk[blockIdx.x] = s;
+}
+
+// exclusive scan of the per-block counts (one thread); bases at blk[G..2G), total at blk[2G]
+__global__ void blk_scan_kernel(u64 *blk, int G) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    u64 s = 0;
+    for (int i = 0; i < G; ++i) {
+      blk[G + i] = s;
+      s += blk[i];
+    }
+    blk[2 * G] = s;
+  }
+}
+
+template <typename K, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, u64 n, const u64 *blk,
+                                                             void *dst, u64 *count) {
+  __shared__ int s_wc[BLOCK / 32];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const u64 G = gridDim.x, chunk = (n + G - 1) / G;
+  const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  u64 cursor = blk[G + blockIdx.x];
+  for (u64 base = lo; base < hi; base += BLOCK) {
+    const u64 i = base + threadIdx.x;
+    bool head = false;
+    K key = 0;
+    u64 sum = 0;
+    if (i < hi) {
+      K prev = 0;
+      u64 c;
+      load_slot(in, i, key, sum);
+      if (i > 0) load_slot(in, i - 1, prev, c);
+      head = key != prev;
+      if (head)  // the run may continue past this block's range
+        for (u64 j = i + 1; j < n; ++j) {
+          K kj;
+          load_slot(in, j, kj, c);
+          if (kj != key) break;
+          sum += c;
+        }
+    }
+    int tot;
+    const int rank = block_flag_rank<BLOCK>(head, s_wc, tot);
+    if (head) store_slot(out, cursor + rank, key, sum);
+    cursor += (u64)tot;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = blk[2 * G];
+}
+
+int grid256(const DevInfo &d) { return d.sms * d.blocks_per_sm; }
+
+template <typename K, typename SK, int ITEMS>
+int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *src, u64 n_src,
+              u64 n, void *buf_a, void *buf_b, u64 *hist, int *which) {
+  const int G = grid256(d);
+  const void *in = src;
+  u64 n_in = n_src;
+  void *bufs[2] = {buf_a, buf_b};
+  int cur = 0;
+  for (int shift = 0; shift < sp.bits; shift += 8) {
+    sort_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
+    scan_inplace_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
+    sort_scatter_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur],
+                                                             n);
+    in = bufs[cur];
+    n_in = n;
+    cur ^= 1;
+  }
+  *which = cur ^ 1;
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int sort_grid(const DevInfo &d) { return grid256(d); }
+
+int sort_passes(const SortSpec &sp) { return (sp.bits + 7) / 8; }
+
+int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
+                        const void *src, unsigned long long n_src, unsigned long long n,
+                        void *buf_a, void *buf_b, unsigned long long *hist, int *which) {
+  *which = -1;
+  if (n == 0 || sp.bits == 0) return 0;
+  if (kw == 1) {
+    return sp.bits <= 64 ? sort_impl<u64, u64, 8>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
+                         : sort_impl<u64, u128, 8>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
+  }
+  return sp.bits <= 64 ? sort_impl<u128, u64, 4>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
+                       : sort_impl<u128, u128, 4>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
+}
+
+int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
+                  unsigned long long n, unsigned long long *blk, void *dst,
+                  unsigned long long *count) {
+  const int G = grid256(d);
+  if (n == 0) return (int)cudaMemsetAsync(count, 0, sizeof(u64), s);
+  if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk);
+  else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk);
+  blk_scan_kernel<<<1, 32, 0, s>>>(blk, G);
+  if (kw == 1) reduce_write_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk, dst, count);
+  else reduce_write_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk, dst, count);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace cc

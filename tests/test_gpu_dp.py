@@ -132,17 +132,24 @@ def _check_small(ctx, g, pat, colours, k, df, fuse, block=256, tables=True):
         assert np.array_equal(r["count"], ref.count)
         assert np.array_equal(r["exists"], ref.exists)
         assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
-        if tables and not fuse:
+        if tables:
             want = oracle_tables(ref, r["nodes"], T)
+            dumped = 0
             for x, nd in enumerate(r["nodes"]):
-                got = gpu_table(ctx, r, x, len(nd[4]), int(r["sizes"][x]) + 1)
+                try:
+                    got = gpu_table(ctx, r, x, len(nd[4]), int(r["sizes"][x]) + 1)
+                except cc.CCError as ex:  # an introduce fused into its forget stores no table
+                    assert fuse and ex.code == cc.CC_EINVAL and nd[0] == cc.INTRODUCE
+                    continue
+                dumped += 1
                 assert got == want[x], (x, nd)
+            assert dumped >= len(r["nodes"]) // 2
     finally:
         release(ctx, r)
 
 
 @pytest.mark.parametrize("name", sorted(PATTERNS))
-@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("fuse", [0, 1, 2])
 def test_dp_small_parity(ctx, name, fuse):
     pat = PATTERNS[name]
     nF = pat[0]
@@ -158,8 +165,8 @@ def test_dp_block_sizes(ctx, block):
     g = synth.barabasi_albert(500, 3, 2)
     pat = synth.grid_pattern(2, 3)
     colours = oracle.colors(500, 4, 6, seed=3)
-    _check_small(ctx, g, pat, colours, 6, True, 0, block=block)
-    _check_small(ctx, g, pat, colours, 6, True, 1, block=block)
+    for fuse in (0, 1, 2):
+        _check_small(ctx, g, pat, colours, 6, True, fuse, block=block)
 
 
 def test_dp_wide_keys(ctx):
@@ -167,11 +174,11 @@ def test_dp_wide_keys(ctx):
     g = synth.erdos_renyi(100000, 2.0 / 99999, 4)
     pat = synth.cycle_pattern(5)
     colours = oracle.colors(100000, 3, 14, seed=8)
-    _check_small(ctx, g, pat, colours, 14, True, 0, tables=True)
-    _check_small(ctx, g, pat, colours, 14, True, 1, tables=False)
+    for fuse in (0, 1, 2):
+        _check_small(ctx, g, pat, colours, 14, True, fuse, tables=fuse != 1)
 
 
-@pytest.mark.parametrize("name", ["C4", "C5", "G23", "K4", "T3", "C"])
+@pytest.mark.parametrize("name", ["C4", "C5", "G23", "K4", "T3", "B"])
 def test_grouped_equals_plain(ctx, name):
     """Sorting the child by bag-neighbour images and sharing candidate lists changes nothing."""
     pat = PATTERNS[name]
@@ -258,7 +265,7 @@ def test_workload_er200_c5(ctx):
     pat = synth.make_pattern(w["pattern"])
     z = oracle.colors(200, 1, 5, w["seed"])
     ref = oracle.run_dp(g, pat, z, 5)
-    for fuse in (0, 1):
+    for fuse in (0, 1, 2):
         r = gpu_dp(ctx, g, pat, seed=w["seed"], trials=1, k=5, fuse=fuse, retain=1)
         assert np.array_equal(r["colours"], z)
         assert np.array_equal(r["count"], ref.count) and int(ref.count[0]) > 0
