@@ -254,5 +254,21 @@ static __device__ __forceinline__ bool adjacent(const GraphDev &G, int a, int v)
 }
 
 
+// The value records are sorted by (SortSpec): the G-vertices of slots order[0..) first, then,
+// for a full order, the trial and the colour set.
+template <typename SK, typename K>
+__device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
+  SK s = 0;
+  const int ns = sp.full ? sp.b : sp.nsl;
+#pragma unroll
+  for (int j = 0; j < kMaxBag; ++j)
+    if (j < ns) s = (s << sp.L.nb) | (SK)(unsigned)key_slot(key, sp.L, sp.order[j]);
+  if (sp.full) {
+    if (sp.L.tb) s = (s << sp.L.tb) | (SK)(unsigned)key_trial(key, sp.L);
+    s = (s << sp.L.k) | (SK)key_mask(key, sp.L);
+  }
+  return s;
+}
+
 }  // namespace dev
 }  // namespace cc

@@ -20,11 +20,6 @@
 #include "../../include/cc.h"
 #include "cc_internal.h"
 
-namespace cc {
-int enumerate_run(struct Ctx *ctx, struct Run *run, uint64_t limit, int32_t *h_out,
-                  uint64_t *n_out, uint64_t *n_total);
-}
-
 using cc::DevInfo;
 using cc::KeyLayout;
 using cc::TableDesc;
@@ -851,6 +846,204 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
   return CC_OK;
 }
 
+// ---- reconstruction driver (Section 4): pre-order steps over device state arrays -----------
+int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_out,
+                  uint64_t *n_total) {
+  const Pattern &P = c->patterns.at(R->pattern);
+  const cc::Coloring &col = c->colorings.at(R->coloring);
+  const int N = (int)P.nodes.size();
+  const int nF = P.nF;
+  // node descriptors
+  std::vector<cc::EnumNode> en(N);
+  std::vector<int> vstar(N, 0), joins_below(N, 0);
+  std::vector<uint32_t> vs(N, 0);
+  for (int x = 0; x < N; ++x) {
+    const NiceNode &nd = P.nodes[x];
+    uint32_t m = 0;
+    for (int u : nd.bag) m |= 1u << u;
+    if (nd.child0 >= 0) m |= vs[nd.child0];
+    if (nd.child1 >= 0) m |= vs[nd.child1];
+    vs[x] = m;
+    int jb = 0;
+    if (nd.child0 >= 0) jb = std::max(jb, joins_below[nd.child0]);
+    if (nd.child1 >= 0) jb = std::max(jb, joins_below[nd.child1]);
+    joins_below[x] = jb + (nd.type == 3 ? 1 : 0);
+    cc::EnumNode &e = en[x];
+    e = cc::EnumNode{};
+    e.type = nd.type;
+    e.child0 = nd.child0;
+    e.child1 = nd.child1;
+    e.vertex = nd.vertex;
+    e.b = (int)nd.bag.size();
+    for (int s = 0; s < e.b; ++s) e.bag[s] = nd.bag[s];
+    e.vstar = __builtin_popcount(m);
+    if (nd.type == 1) {
+      const NiceNode &ch = P.nodes[nd.child0];
+      e.p = pos_in(nd.bag, nd.vertex);
+      for (size_t s = 0; s < ch.bag.size(); ++s)
+        if (P.adj[nd.vertex] >> ch.bag[s] & 1u) e.nb_slot[e.nnb++] = (int)s;
+      e.degF = R->opts.degree_filter ? P.deg[nd.vertex] : 0;
+    } else if (nd.type == 2) {
+      for (int w : nd.bag)
+        if (P.adj[nd.vertex] >> w & 1u) e.nb_slot[e.nnb++] = w;
+    }
+    const cc::NodeTable &t = R->tables[x];
+    if (nd.type != 1 && !t.slots) return CC_EINVAL;  // tables were not kept
+    e.slots = t.slots;
+    e.cap = t.cap;
+    e.count = R->sizes[x];
+    e.hashed = t.hashed;
+    e.sorted = !t.hashed && t.sort_n == (int)nd.bag.size() && nd.type != 0;
+    if (e.sorted) {
+      e.spec.L = R->L;
+      e.spec.b = e.b;
+      e.spec.nsl = t.sort_n;
+      for (int s = 0; s < e.b; ++s) e.spec.order[s] = t.sort_slots[s];
+      e.spec.full = 1;
+      e.spec.bits = e.b * R->L.nb + R->L.tb + R->L.k;
+    }
+    if (nd.type != 0 && nd.type != 1 && !e.hashed && !e.sorted) return CC_EINVAL;
+  }
+  const int D = std::max(1, joins_below[N - 1]);
+  const int RW = 3 + D + nF;
+  // pre-order of the nice decomposition from the root
+  std::vector<int> pre, stack{N - 1};
+  while (!stack.empty()) {
+    int x = stack.back();
+    stack.pop_back();
+    pre.push_back(x);
+    if (P.nodes[x].child1 >= 0) stack.push_back(P.nodes[x].child1);
+    if (P.nodes[x].child0 >= 0) stack.push_back(P.nodes[x].child0);
+  }
+  std::vector<void *> owned;
+  auto cleanup = [&]() {
+    for (void *p : owned) c->arena.release(p);
+    owned.clear();
+  };
+  auto take = [&](size_t bytes) -> void * {
+    void *p = c->arena.alloc(bytes);
+    if (p) owned.push_back(p);
+    return p;
+  };
+  auto drop = [&](void *p) {
+    for (auto it = owned.begin(); it != owned.end(); ++it)
+      if (*it == p) {
+        owned.erase(it);
+        break;
+      }
+    c->arena.release(p);
+  };
+  cc::EnumNode *d_nodes = (cc::EnumNode *)take(sizeof(cc::EnumNode) * N);
+  u64 *scratch = (u64 *)take(sizeof(u64) * (cc::scan_scratch_words(c->dev) + 8));
+  if (!d_nodes || !scratch) {
+    cleanup();
+    return CC_ENOMEM;
+  }
+  if (cudaMemcpyAsync(d_nodes, en.data(), sizeof(cc::EnumNode) * N, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess) {
+    cleanup();
+    return CC_ECUDA;
+  }
+  cc::EnumArgs a{};
+  a.G = cc::GraphDev{c->d_row_ptr, c->d_col, col.d_colors, c->n};
+  a.L = R->L;
+  a.nodes = d_nodes;
+  a.nF = nF;
+  a.R = RW;
+  a.D = D;
+  // root states
+  u64 n_cur = R->sizes[N - 1];
+  int *cur = (int *)take(std::max<u64>(1, n_cur) * RW * sizeof(int));
+  if (!cur) {
+    cleanup();
+    return CC_ENOMEM;
+  }
+  a.out = cur;
+  a.n_in = n_cur;
+  u64 *d_n = scratch + cc::scan_scratch_words(c->dev);
+  int rc = CC_OK;
+  if (cudaMemsetAsync(d_n, 0, sizeof(u64), c->stream) != cudaSuccess) rc = CC_ECUDA;
+  const cc::NodeTable &rt = R->tables[N - 1];
+  const u64 rbound = rt.hashed ? rt.cap : R->sizes[N - 1];
+  if (!rc && cc::launch_enum_init(c->stream, c->dev, R->kw, a, rt.slots, rbound, d_n)) rc = CC_ECUDA;
+  c->launches++;
+  for (size_t i = 0; i < pre.size() && !rc; ++i) {
+    a.x = pre[i];
+    a.in = cur;
+    a.n_in = n_cur;
+    unsigned *cnt = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
+    u64 *off = (u64 *)take((n_cur + 1) * sizeof(u64));
+    if (!cnt || !off) {
+      rc = CC_ENOMEM;
+      break;
+    }
+    a.cnt = cnt;
+    if (cc::launch_enum_step(c->stream, c->dev, R->kw, 0, a) ||
+        cc::launch_scan_u32(c->stream, c->dev, cnt, n_cur, off, scratch)) {
+      rc = CC_ECUDA;
+      break;
+    }
+    c->launches += 4;
+    u64 n_next = 0;
+    rc = read_u64(c, off + n_cur, &n_next);
+    if (rc) break;
+    int *next = (int *)take(std::max<u64>(1, n_next) * RW * sizeof(int));
+    if (!next) {
+      rc = CC_ENOMEM;
+      break;
+    }
+    a.out = next;
+    a.off = off;
+    if (cc::launch_enum_step(c->stream, c->dev, R->kw, 1, a)) {
+      rc = CC_ECUDA;
+      break;
+    }
+    c->launches++;
+    drop(cnt);
+    drop(off);
+    drop(cur);
+    cur = next;
+    n_cur = n_next;
+  }
+  // the union over trials in lexicographic order without repeats
+  if (!rc) {
+    int *rows = (int *)take(std::max<u64>(1, n_cur) * nF * sizeof(int));
+    unsigned *perm = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
+    unsigned *tmp = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
+    u64 *hist = (u64 *)take(256 * 2 * (size_t)c->dev.sms * sizeof(u64));
+    unsigned *flag = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
+    u64 *off = (u64 *)take((n_cur + 1) * sizeof(u64));
+    const u64 lim = std::min<u64>(limit, n_cur);
+    int *out = (int *)take(std::max<u64>(1, lim) * nF * sizeof(int));
+    if (!rows || !perm || !tmp || !hist || !flag || !off || !out) {
+      rc = CC_ENOMEM;
+    } else {
+      unsigned *sorted = nullptr;
+      if (cc::launch_rows_extract(c->stream, c->dev, cur, n_cur, RW, D, nF, rows, perm) ||
+          cc::launch_rows_sort(c->stream, c->dev, rows, nF, R->L.nb, n_cur, perm, tmp, hist,
+                               &sorted) ||
+          cc::launch_rows_heads(c->stream, c->dev, rows, nF, sorted, n_cur, flag) ||
+          cc::launch_scan_u32(c->stream, c->dev, flag, n_cur, off, scratch) ||
+          cc::launch_rows_gather(c->stream, c->dev, rows, nF, sorted, n_cur, flag, off, lim, out))
+        rc = CC_ECUDA;
+      c->launches += 10;
+      u64 distinct = 0;
+      if (!rc) rc = read_u64(c, off + n_cur, &distinct);
+      if (!rc) {
+        const u64 m = std::min<u64>(limit, distinct);
+        if (m && cudaMemcpyAsync(h_out, out, m * nF * sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream) != cudaSuccess)
+          rc = CC_ECUDA;
+        if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CC_ECUDA;
+        *n_out = m;
+        *n_total = distinct;
+      }
+    }
+  }
+  cleanup();
+  return rc;
+}
+
 int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **out) {
   auto pi = c->patterns.find(pid);
   auto ci = c->colorings.find(cid);
@@ -1318,8 +1511,8 @@ int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, ui
   if (!c || !n_out || !n_total || (limit && !h_out)) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
-  if (!R->retained || R->opts.fuse) return CC_EINVAL;
-  return cc::enumerate_run(c, R, limit, h_out, n_out, n_total);
+  if (!R->retained) return CC_EINVAL;
+  return enumerate_run(c, R, limit, h_out, n_out, n_total);
 }
 
 int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,

@@ -153,6 +153,56 @@ int launch_unpack(cudaStream_t s, const DevInfo &d, int kw, const KeyLayout &L,
                   int32_t *phi, uint32_t *mask, unsigned long long *cnt,
                   unsigned long long *n_out);
 
+// ---- reconstruction (cc_enum.cu) ---------------------------------------------------------
+// A node as the top-down walk sees it, with its stored table (if any).
+struct EnumNode {
+  int type, child0, child1, vertex;
+  int b;                  // bag size
+  int bag[kMaxBag];       // F-vertices of the bag, slot order
+  int p;                  // introduce: slot of the introduced vertex
+  int nnb;                // introduce: bag neighbours (child-bag slots in nb_slot);
+  int nb_slot[kMaxBag];   // forget: F-neighbours of the forgotten vertex in the bag (F-vertex ids)
+  int degF;               // introduce: degree filter bound (0 = off)
+  int vstar;              // |V*_x|
+  const void *slots;      // stored table (leaf: indexed by trial * n + v)
+  unsigned long long cap, count;
+  int hashed, sorted;
+  SortSpec spec;          // order of a sorted table
+};
+
+struct EnumArgs {
+  GraphDev G;
+  KeyLayout L;
+  const EnumNode *nodes;  // device array
+  int x;                  // node processed by this step
+  int nF, R, D;           // state = R ints: trial, colour set, depth, stack[D], Phi[nF]
+  const int *in;
+  unsigned long long n_in;
+  int *out;
+  const unsigned long long *off;  // write pass: first output state of each input state
+  unsigned *cnt;                  // count pass: output states per input state
+};
+
+int launch_enum_init(cudaStream_t s, const DevInfo &d, int kw, const EnumArgs &a,
+                     const void *root, unsigned long long bound, unsigned long long *n);
+int launch_enum_step(cudaStream_t s, const DevInfo &d, int kw, int mode, const EnumArgs &a);
+size_t scan_scratch_words(const DevInfo &d);
+// exclusive scan of n u32 values into off[0..n) and the total into off[n]
+int launch_scan_u32(cudaStream_t s, const DevInfo &d, const unsigned *v, unsigned long long n,
+                    unsigned long long *off, unsigned long long *scratch);
+int launch_rows_extract(cudaStream_t s, const DevInfo &d, const int *states,
+                        unsigned long long n, int R, int D, int nF, int *rows, unsigned *perm);
+// lexicographic order of the rows (nF ints each, values < 2^nb) as a permutation; *result is
+// perm or tmp.  hist needs 256 * 2 * sms words.
+int launch_rows_sort(cudaStream_t s, const DevInfo &d, const int *rows, int nF, int nb,
+                     unsigned long long n, unsigned *perm, unsigned *tmp, unsigned long long *hist,
+                     unsigned **result);
+int launch_rows_heads(cudaStream_t s, const DevInfo &d, const int *rows, int nF,
+                      const unsigned *perm, unsigned long long n, unsigned *flag);
+int launch_rows_gather(cudaStream_t s, const DevInfo &d, const int *rows, int nF,
+                       const unsigned *perm, unsigned long long n, const unsigned *flag,
+                       const unsigned long long *off, unsigned long long limit, int *out);
+
 size_t slot_bytes(int kw);       // bytes of one table record for 1- or 2-word keys
 size_t index_slot_bytes(int kw); // bytes of one join-index record
 

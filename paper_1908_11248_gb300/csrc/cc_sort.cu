@@ -24,20 +24,6 @@ namespace {
 
 using namespace dev;
 
-template <typename SK, typename K>
-__device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
-  SK s = 0;
-  const int ns = sp.full ? sp.b : sp.nsl;
-#pragma unroll
-  for (int j = 0; j < kMaxBag; ++j)
-    if (j < ns) s = (s << sp.L.nb) | (SK)(unsigned)key_slot(key, sp.L, sp.order[j]);
-  if (sp.full) {
-    if (sp.L.tb) s = (s << sp.L.tb) | (SK)(unsigned)key_trial(key, sp.L);
-    s = (s << sp.L.k) | (SK)key_mask(key, sp.L);
-  }
-  return s;
-}
-
 template <typename K, typename SK, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) sort_hist_kernel(SortSpec sp, const void *src, u64 n,
                                                           int shift, u64 *hist) {
