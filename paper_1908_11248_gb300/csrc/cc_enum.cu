@@ -266,26 +266,47 @@ __global__ void rows_hist_kernel(const int *rows, int nF, const unsigned *perm, 
   for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(u64)d * G + blockIdx.x] = h[d];
 }
 
-__global__ void rows_scan_kernel(u64 *v, u64 m) {
-  __shared__ u64 s[1024];
-  const u64 per = (m + 1023) / 1024;
-  const u64 lo = threadIdx.x * per, hi = min(m, lo + per);
-  u64 sum = 0;
-  for (u64 i = lo; i < hi; ++i) sum += v[i];
-  s[threadIdx.x] = sum;
+__global__ void __launch_bounds__(256) rows_row_scan_kernel(u64 *hist, int G) {
+  __shared__ u64 s_w[8];
+  __shared__ u64 s_carry;
+  u64 *row = hist + (u64)blockIdx.x * G;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    u64 y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+  for (int base = 0; base < G; base += 256) {
+    const int i = base + threadIdx.x;
+    const u64 v = i < G ? row[i] : 0;
+    u64 x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
     __syncthreads();
-    s[threadIdx.x] += y;
+    u64 before = s_carry;
+    for (int q = 0; q < w; ++q) before += s_w[q];
+    if (i < G) row[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == 255) s_carry = before + x;
     __syncthreads();
   }
-  u64 run = s[threadIdx.x] - sum;
-  for (u64 i = lo; i < hi; ++i) {
-    u64 x = v[i];
-    v[i] = run;
-    run += x;
+  if (threadIdx.x == 0) hist[(u64)256 * G + 256 + blockIdx.x] = s_carry;
+}
+
+__global__ void __launch_bounds__(256) rows_digit_base_kernel(u64 *hist, int G) {
+  __shared__ u64 s_w[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u64 v = hist[(u64)256 * G + 256 + threadIdx.x];
+  u64 x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  u64 before = 0;
+  for (int q = 0; q < w; ++q) before += s_w[q];
+  hist[(u64)256 * G + threadIdx.x] = before + x - v;
 }
 
 __global__ void __launch_bounds__(256) rows_scatter_kernel(const int *rows, int nF,
@@ -318,7 +339,7 @@ __global__ void __launch_bounds__(256) rows_scatter_kernel(const int *rows, int 
     }
     s_run[tid] = acc;
     __syncthreads();
-    if (valid) out[off[(u64)d * G + blockIdx.x] + s_wc[w][d] + rank] = p;
+    if (valid) out[off[(u64)d * G + blockIdx.x] + off[256 * G + d] + s_wc[w][d] + rank] = p;
     __syncthreads();
     for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
     __syncthreads();
@@ -414,7 +435,8 @@ int launch_rows_sort(cudaStream_t s, const DevInfo &d, const int *rows, int nF, 
     for (int col = nF - 1; col >= 0; --col)
       for (int shift = 0; shift < nb; shift += 8) {
         rows_hist_kernel<<<G, 256, 0, s>>>(rows, nF, in, n, col, shift, hist);
-        rows_scan_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
+        rows_row_scan_kernel<<<256, 256, 0, s>>>(hist, G);
+        rows_digit_base_kernel<<<1, 256, 0, s>>>(hist, G);
         rows_scatter_kernel<<<G, 256, 0, s>>>(rows, nF, in, n, col, shift, hist, out);
         unsigned *t = in;
         in = out;

@@ -612,7 +612,7 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
     const size_t rb = cc::slot_bytes(R->kw);
     void *ba = c->arena.alloc(std::max<u64>(1, m) * rb);
     void *bb = c->arena.alloc(std::max<u64>(1, m) * rb);
-    u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev));
+    u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev) + 512);
     if (!ba || !bb || !hist) {
       c->arena.release(ba);
       c->arena.release(bb);
@@ -1010,7 +1010,7 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
     int *rows = (int *)take(std::max<u64>(1, n_cur) * nF * sizeof(int));
     unsigned *perm = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
     unsigned *tmp = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
-    u64 *hist = (u64 *)take(256 * 2 * (size_t)c->dev.sms * sizeof(u64));
+    u64 *hist = (u64 *)take((256 * 2 * (size_t)c->dev.sms + 512) * sizeof(u64));
     unsigned *flag = (unsigned *)take(std::max<u64>(1, n_cur) * sizeof(unsigned));
     u64 *off = (u64 *)take((n_cur + 1) * sizeof(u64));
     const u64 lim = std::min<u64>(limit, n_cur);

@@ -133,7 +133,7 @@ struct SortSpec {
 };
 // Stable LSD radix sort of the nonempty records of `src` (n_src slots, n of them nonempty) into
 // buf_a / buf_b (n records each); *which (0 or 1) names the buffer holding the result.  hist
-// needs 256 * sort_grid(d) words.
+// needs 256 * sort_grid(d) + 512 words.
 int sort_grid(const DevInfo &d);
 int sort_passes(const SortSpec &sp);
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,

@@ -44,27 +44,51 @@ __global__ void __launch_bounds__(BLOCK) sort_hist_kernel(SortSpec sp, const voi
   for (int d = threadIdx.x; d < 256; d += BLOCK) hist[(u64)d * G + blockIdx.x] = s_h[d];
 }
 
-// exclusive scan of m values in place (one block of 1024 threads)
-__global__ void __launch_bounds__(1024) scan_inplace_kernel(u64 *v, u64 m) {
-  __shared__ u64 s[1024];
-  const u64 per = (m + 1023) / 1024;
-  const u64 lo = threadIdx.x * per, hi = min(m, lo + per);
-  u64 sum = 0;
-  for (u64 i = lo; i < hi; ++i) sum += v[i];
-  s[threadIdx.x] = sum;
+// Offsets of the (digit, block) histogram, digit-major.  Block d scans row d (the counts of
+// digit d over the G blocks) in place and writes the row total; then one block turns the 256
+// row totals into digit bases at hist[256 * G + d].  A scatter's offset for (d, b) is
+// hist[d * G + b] + hist[256 * G + d].
+__global__ void __launch_bounds__(256) row_scan_kernel(u64 *hist, int G) {
+  __shared__ u64 s_w[8];
+  __shared__ u64 s_carry;
+  u64 *row = hist + (u64)blockIdx.x * G;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    u64 y = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+  for (int base = 0; base < G; base += 256) {
+    const int i = base + threadIdx.x;
+    const u64 v = i < G ? row[i] : 0;
+    u64 x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
     __syncthreads();
-    s[threadIdx.x] += y;
+    u64 before = s_carry;
+    for (int q = 0; q < w; ++q) before += s_w[q];
+    if (i < G) row[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == 255) s_carry = before + x;
     __syncthreads();
   }
-  u64 run = s[threadIdx.x] - sum;
-  for (u64 i = lo; i < hi; ++i) {
-    u64 x = v[i];
-    v[i] = run;
-    run += x;
+  if (threadIdx.x == 0) hist[(u64)256 * G + 256 + blockIdx.x] = s_carry;
+}
+
+__global__ void __launch_bounds__(256) digit_base_kernel(u64 *hist, int G) {
+  __shared__ u64 s_w[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u64 v = hist[(u64)256 * G + 256 + threadIdx.x];
+  u64 x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  u64 before = 0;
+  for (int q = 0; q < w; ++q) before += s_w[q];
+  hist[(u64)256 * G + threadIdx.x] = before + x - v;
 }
 
 template <typename K, typename SK, int BLOCK, int ITEMS>
@@ -147,7 +171,7 @@ __global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const 
     const unsigned tcount = s_tstart[255] + s_thist[255];
     for (unsigned i = tid; i < tcount; i += BLOCK) {
       const int d = s_sdig[i];
-      const u64 pos = off[(u64)d * G + blockIdx.x] + s_brun[d] + (i - s_tstart[d]);
+      const u64 pos = off[(u64)d * G + blockIdx.x] + off[256 * G + d] + s_brun[d] + (i - s_tstart[d]);
       if (pos < dst_cap) store_slot(out, pos, s_stage[i].key, s_stage[i].cnt);
     }
     __syncthreads();
@@ -235,7 +259,8 @@ int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *
   int cur = 0;
   for (int shift = 0; shift < sp.bits; shift += 8) {
     sort_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
-    scan_inplace_kernel<<<1, 1024, 0, s>>>(hist, (u64)256 * G);
+    row_scan_kernel<<<256, 256, 0, s>>>(hist, G);
+    digit_base_kernel<<<1, 256, 0, s>>>(hist, G);
     sort_scatter_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur],
                                                              n);
     in = bufs[cur];
