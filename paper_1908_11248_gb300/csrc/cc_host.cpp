@@ -126,6 +126,15 @@ struct NodeTable {
   // a dense table sorted with these bag slots most significant (sort_n == 0: no known order)
   int sort_n = 0;
   int sort_slots[kMaxBag] = {};
+  // scan bound of a dense table written in chunks (holes up to it); null: the entry counter
+  unsigned long long *bound = nullptr;
+};
+
+// Capacities learned from exact runs of one (pattern, graph, trials, colours, options): the
+// largest table sizes and join pair counts seen, per node.
+struct Plan {
+  std::vector<u64> entries, pairs;
+  int runs = 0;
 };
 
 struct Timing {
@@ -142,11 +151,14 @@ struct Run {
   int kw = 1;
   int32_t trials = 0;
   std::vector<NodeTable> tables;
-  u64 *d_counters = nullptr;  // one per node
+  // per node, four words each: entries, chunk cursor, join pairs, candidates examined
+  u64 *d_counters = nullptr;
   unsigned *d_exists = nullptr;
   u64 *d_count = nullptr;
-  std::vector<u64> sizes;
+  std::vector<u64> sizes, pairs;
+  std::vector<std::pair<const u64 *, u64>> checks;  // planned runs: device word <= capacity
   bool retained = false;
+  bool planned = false;
 };
 
 struct Ctx {
@@ -160,6 +172,9 @@ struct Ctx {
   int32_t *d_row_ptr = nullptr, *d_col = nullptr;
   std::vector<int32_t> h_row_ptr, h_col;
   int *d_err = nullptr;
+  u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
+  int graph_version = 0;
+  std::map<std::vector<long long>, Plan> plans;
   u64 *d_scratch = nullptr;  // small per-call scratch (block counts, pair counter)
   size_t scratch_words = 0;
   std::map<int32_t, Pattern> patterns;
@@ -518,21 +533,41 @@ int pos_in(const std::vector<int32_t> &bag, int u) {
 }
 
 // ---- the planner: node by node in post-order, exact capacities ----------------------------
-int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
+int finish_run(Ctx *c, Run *R);
+
+// Runs every node of the nice decomposition in post-order (Section 3.1).
+//
+// Exact mode (plan == nullptr): introduces first count their entries and joins their colour-set
+// pairs; every table gets exactly the room it needs, and sizes are read back node by node.
+// Planned mode: capacities come from earlier exact runs of the same pattern, graph, trials,
+// colours and options (a little larger); there are no count passes and no host reads until the
+// end, introduces append in chunks (leaving holes that consumers skip), and all sizes stay on
+// the device.  If any table outgrew its planned room the run reports CC_ECAPACITY and the
+// caller repeats it in exact mode.
+int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const cc::Plan *plan) {
   const int N = (int)P.nodes.size();
   const int32_t n = c->n;
   const float lf = R->opts.load_factor;
   const int block = R->opts.block;
   const int df = R->opts.degree_filter;
+  const bool planned = plan != nullptr;
   cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n};
   R->tables.assign(N, {});
   R->sizes.assign(N, 0);
+  R->pairs.assign(N, 0);
+  R->checks.clear();
   std::vector<bool> made(N, false);
   const int grid = cc::intro_grid(c->dev, block);
   int rc = ensure_scratch(c, 2 * (size_t)std::max(grid, cc::sort_grid(c->dev)) + 8);
   if (rc) return rc;
   u64 *blk = c->d_scratch;
+  u64 *cursor = R->d_counters + N;      // per node: chunked-append cursor (scan bound)
+  u64 *pairs_dev = R->d_counters + 2 * N;  // per join: matching colour-set pairs
   CUDA_OK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  const size_t rb = cc::slot_bytes(R->kw);
+  // planned room for a quantity last seen at v (plus slack for chunked appends)
+  const u64 chunk_slack = (u64)grid * 2048;
+  auto room = [&](u64 v) { return v + v / 4 + 4096; };
 
   // every launch goes through `timed`: it counts the launch and, when profiling, brackets it
   // with CUDA events on the context's stream
@@ -560,25 +595,26 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
     TableDesc t;
     t.slots = R->tables[x].slots;
     t.cap = R->tables[x].cap;
-    t.count = R->d_counters + x;
+    t.count = R->tables[x].bound ? R->tables[x].bound : R->d_counters + x;
     t.hashed = R->tables[x].hashed;
     return t;
   };
-  auto new_hash = [&](int x, u64 entries) -> int {
-    u64 cap = hash_cap(entries, lf);
-    void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+  // entries of node x: exact size, or planned room
+  auto entries = [&](int x) { return planned ? room(plan->entries[x]) : R->sizes[x]; };
+  auto new_hash = [&](int x, u64 keys) -> int {
+    u64 cap = hash_cap(keys, lf);
+    void *p = c->arena.alloc(cap * rb);
     if (!p) return CC_ENOMEM;
-    CUDA_OK(cudaMemsetAsync(p, 0, cap * cc::slot_bytes(R->kw), c->stream));
+    CUDA_OK(cudaMemsetAsync(p, 0, cap * rb, c->stream));
     R->tables[x] = {p, cap, 1, true};
     return CC_OK;
   };
-
   // true if table t is sorted with exactly the slots sl[0..n) (in any order) most significant
-  auto sorted_by = [&](const cc::NodeTable &t, int n, const int *sl) {
-    if (t.hashed || t.sort_n < n) return false;
-    for (int j = 0; j < n; ++j) {
+  auto sorted_by = [&](const cc::NodeTable &t, int m, const int *sl) {
+    if (t.hashed || t.sort_n < m) return false;
+    for (int j = 0; j < m; ++j) {
       bool in = false;
-      for (int i = 0; i < n; ++i) in = in || t.sort_slots[i] == sl[j];
+      for (int i = 0; i < m; ++i) in = in || t.sort_slots[i] == sl[j];
       if (!in) return false;
     }
     return true;
@@ -606,12 +642,12 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
     sp.bits = sp.b * R->L.nb + R->L.tb + R->L.k;
     return sp;
   };
-  // sorts the nonempty records of src (n_src slots, m nonempty) into a new buffer *out
-  auto sort_records = [&](int node, const cc::SortSpec &sp, const void *src, u64 n_src, u64 m,
-                          void **out) -> int {
-    const size_t rb = cc::slot_bytes(R->kw);
-    void *ba = c->arena.alloc(std::max<u64>(1, m) * rb);
-    void *bb = c->arena.alloc(std::max<u64>(1, m) * rb);
+  // sorts the records of src (scan bound *n_src, at most src_cap slots, *n of them nonempty,
+  // at most cap) into a new buffer *out of cap records
+  auto sort_records = [&](int node, const cc::SortSpec &sp, const void *src, const u64 *n_src,
+                          u64 src_cap, const u64 *nn, u64 cap, void **out) -> int {
+    void *ba = c->arena.alloc(std::max<u64>(1, cap) * rb);
+    void *bb = c->arena.alloc(std::max<u64>(1, cap) * rb);
     u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev) + 512);
     if (!ba || !bb || !hist) {
       c->arena.release(ba);
@@ -620,21 +656,18 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       return CC_ENOMEM;
     }
     int which = 0;
-    int r = timed(node, CC_K_SORT, 3 * cc::sort_passes(sp), [&] {
-      return cc::launch_sort_records(c->stream, c->dev, R->kw, sp, src, n_src, m, ba, bb, hist,
-                                     &which);
+    int r = timed(node, CC_K_SORT, 4 * cc::sort_passes(sp), [&] {
+      return cc::launch_sort_records(c->stream, c->dev, R->kw, sp, src, n_src, src_cap, nn, cap,
+                                     ba, bb, hist, &which);
     });
     c->arena.release(hist);
-    if (which < 0) {  // nothing to sort: copy through
-      c->arena.release(bb);
-      if (!r && m) r = cudaMemcpyAsync(ba, src, m * rb, cudaMemcpyDeviceToDevice, c->stream)
-                          ? CC_ECUDA : CC_OK;
-      *out = ba;
-      return r;
-    }
-    *out = which ? bb : ba;
     c->arena.release(which ? ba : bb);
+    *out = which ? bb : ba;
     return r;
+  };
+  // in planned mode, device word `w` must end at most `cap`
+  auto check = [&](const u64 *w, u64 cap) {
+    if (planned) R->checks.push_back({w, cap});
   };
 
   for (int x = 0; x < N; ++x) {
@@ -642,11 +675,11 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
     const NiceNode &nd = P.nodes[x];
     if (nd.type == 0) {  // leaf
       u64 cap = std::max<u64>(1, (u64)n * (u64)R->trials);
-      void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+      void *p = c->arena.alloc(cap * rb);
       if (!p) return CC_ENOMEM;
       R->tables[x] = {p, cap, 1, true};
       cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), c->d_err};
-      if (n == 0) CUDA_OK(cudaMemsetAsync(p, 0, cc::slot_bytes(R->kw), c->stream));
+      if (n == 0) CUDA_OK(cudaMemsetAsync(p, 0, rb, c->stream));
       rc = timed(x, CC_K_LEAF, 1, [&] { return cc::launch_leaf(c->stream, c->dev, R->kw, a); });
       if (rc) return rc;
     } else if (nd.type == 1) {  // introduce
@@ -663,15 +696,14 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
       a.degF = df ? P.deg[nd.vertex] : 0;
       a.err = c->d_err;
-      a.valid = R->d_counters + x;
-      a.cand = blk + 2 * grid + 1;
+      a.cand = R->d_counters + 3 * N + x;  // candidates examined (count pass, or planned)
+      a.proj_q = -1;
+      a.q = -1;
       // several bag neighbours: the child must come in runs of equal images of those slots so
       // that a run shares one candidate list; sort it unless its order already starts with them
-      const int grouped = R->opts.group && a.nnb >= 2 && a.nnb * R->L.nb <= 64 && R->sizes[y] > 0;
+      const int grouped = R->opts.group && a.nnb >= 2 && a.nnb * R->L.nb <= 64;
       void *sorted = nullptr;
       if (grouped && !sorted_by(R->tables[y], a.nnb, a.nb_slot)) {
-        const u64 m = R->sizes[y];
-        const u64 n_src = R->tables[y].hashed ? R->tables[y].cap : m;
         cc::SortSpec sp{};
         sp.L = R->L;
         sp.b = a.b_in;
@@ -679,36 +711,56 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         for (int j = 0; j < a.nnb; ++j) sp.order[j] = a.nb_slot[j];
         sp.full = 0;
         sp.bits = a.nnb * R->L.nb;
-        rc = sort_records(x, sp, R->tables[y].slots, n_src, m, &sorted);
+        const cc::NodeTable &ty = R->tables[y];
+        const u64 m = entries(y);
+        check(R->d_counters + y, m);
+        rc = sort_records(x, sp, ty.slots, ty.hashed ? c->d_ones : desc(y).count, ty.cap,
+                          R->d_counters + y, m, &sorted);
         if (rc) return rc;
-        a.in.slots = sorted;
-        a.in.cap = m;
-        a.in.hashed = 0;
+        a.in = TableDesc{sorted, std::max<u64>(1, m), R->d_counters + y, 0};
       }
       struct SortedGuard {
         Ctx *c;
         void *p;
         ~SortedGuard() { c->arena.release(p); }
       } sorted_guard{c, sorted};
-      CUDA_OK(cudaMemsetAsync(a.cand, 0, sizeof(u64), c->stream));
-      rc = timed(x, CC_K_INTRO_COUNT, 2, [&] {
-        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 0, grouped, block, a, blk);
-      });
-      if (rc) return rc;
       u64 total = 0, cand = 0;
-      rc = read_u64(c, blk + 2 * grid, &total);
-      if (!rc) rc = read_u64(c, a.cand, &cand);
-      if (rc) return rc;
-      if (R->opts.profile) R->timings.back().candidates = cand;
-      R->sizes[x] = total;
+      if (!planned) {
+        rc = timed(x, CC_K_INTRO_COUNT, 2, [&] {
+          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 0, grouped, block, a, blk);
+        });
+        if (rc) return rc;
+        rc = read_u64(c, blk + 2 * grid, &total);
+        if (!rc) rc = read_u64(c, a.cand, &cand);
+        if (rc) return rc;
+        if (R->opts.profile) R->timings.back().candidates = cand;
+        R->sizes[x] = total;
+      }
+      // room for this introduce's entries: exact, or planned plus chunk slack
+      const u64 raw = planned ? room(plan->entries[x]) + chunk_slack : std::max<u64>(1, total);
+      if (planned) check(R->d_counters + x, room(plan->entries[x]));
+      auto write_dense = [&](void *buf, u64 cap, int proj) -> int {
+        a.out = TableDesc{buf, cap, nullptr, 0};
+        a.proj_q = proj;
+        a.valid = R->d_counters + x;
+        a.cursor = planned ? cursor + x : nullptr;
+        a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
+        if (planned) check(cursor + x, cap);
+        int r = timed(x, CC_K_INTRO_WRITE, 1, [&] {
+          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
+        });
+        if (R->opts.profile && !r) R->timings.back().candidates = cand;
+        return r;
+      };
       const int f = nd.parent;
       const int fuse = (f >= 0 && P.nodes[f].type == 2) ? R->opts.fuse : 0;
       if (fuse == 1) {  // add projected entries into the forget's hash table
-        rc = new_hash(f, total);
+        rc = new_hash(f, planned ? room(plan->entries[f]) : total);
         if (rc) return rc;
         a.out = desc(f);
         a.q = pos_in(nd.bag, P.nodes[f].vertex);
-        CUDA_OK(cudaMemsetAsync(R->d_counters + x, 0, sizeof(u64), c->stream));
+        a.valid = R->d_counters + x;
+        a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
         rc = timed(x, CC_K_INTRO_FUSED, 1, [&] {
           return cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a, blk);
         });
@@ -716,69 +768,58 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         if (R->opts.profile) R->timings.back().candidates = cand;
         made[f] = true;
         release_child(y);
-        rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
-        if (rc) return rc;
+        if (!planned) {
+          rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
+          if (rc) return rc;
+        }
         if (f == N - 1) break;
         continue;
       }
       if (fuse == 2) {  // write projected entries densely, sort them, reduce equal keys
-        const size_t rb = cc::slot_bytes(R->kw);
-        const u64 cap = std::max<u64>(1, total);
-        void *buf = c->arena.alloc(cap * rb);
+        void *buf = c->arena.alloc(raw * rb);
         if (!buf) return CC_ENOMEM;
-        cc::TableDesc tmp{buf, cap, blk + 2 * grid + 3, 0};
-        CUDA_OK(cudaMemcpyAsync(tmp.count, blk + 2 * grid, sizeof(u64), cudaMemcpyDeviceToDevice,
-                                c->stream));
-        a.out = tmp;
-        a.proj_q = pos_in(nd.bag, P.nodes[f].vertex);
-        rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
-        });
-        if (R->opts.profile && !rc) R->timings.back().candidates = cand;
+        rc = write_dense(buf, raw, pos_in(nd.bag, P.nodes[f].vertex));
         if (!rc) release_child(y);
         cc::SortSpec sp = forget_order(f);
         void *srt = nullptr;
-        if (!rc) rc = sort_records(f, sp, buf, total, total, &srt);
+        // scan bound of the written buffer: its cursor when appended in chunks
+        const u64 *bound = planned ? cursor + x : R->d_counters + x;
+        if (!rc) rc = sort_records(f, sp, buf, bound, raw, R->d_counters + x, raw, &srt);
         c->arena.release(buf);
         if (rc) return rc;
-        void *out = c->arena.alloc(cap * rb);
+        void *out = c->arena.alloc(raw * rb);
         if (!out) {
           c->arena.release(srt);
           return CC_ENOMEM;
         }
         rc = timed(f, CC_K_REDUCE, 3, [&] {
-          return cc::launch_reduce(c->stream, c->dev, R->kw, srt ? srt : buf, total, blk, out,
+          return cc::launch_reduce(c->stream, c->dev, R->kw, srt, R->d_counters + x, blk, out,
                                    R->d_counters + f);
         });
         c->arena.release(srt);
         if (rc) return rc;
-        R->tables[f] = {out, cap, 0, true};
-        R->tables[f].sort_n = sp.full ? sp.b : 0;
+        R->tables[f] = {out, raw, 0, true};
+        R->tables[f].sort_n = sp.b;
         for (int j = 0; j < sp.b; ++j) R->tables[f].sort_slots[j] = sp.order[j];
         made[f] = true;
-        rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
-        if (rc) return rc;
+        if (!planned) {
+          rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
+          if (rc) return rc;
+        }
         if (f == N - 1) break;
         continue;
       }
-      u64 cap = std::max<u64>(1, total);
-      void *p = c->arena.alloc(cap * cc::slot_bytes(R->kw));
+      void *p = c->arena.alloc(raw * rb);
       if (!p) return CC_ENOMEM;
-      R->tables[x] = {p, cap, 0, true};
-      a.out = desc(x);
-      a.proj_q = -1;
-      CUDA_OK(cudaMemcpyAsync(R->d_counters + x, blk + 2 * grid, sizeof(u64),
-                              cudaMemcpyDeviceToDevice, c->stream));
-      rc = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-        return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
-      });
+      rc = write_dense(p, raw, -1);
       if (rc) return rc;
-      if (R->opts.profile) R->timings.back().candidates = cand;
+      R->tables[x] = {p, raw, 0, true};
+      if (planned) R->tables[x].bound = cursor + x;  // holes: scan up to the cursor
       release_child(y);
-      continue;  // size already known
+      continue;  // size already known (exact) or on the device (planned)
     } else if (nd.type == 2) {  // forget
       const int y = nd.child0;
-      rc = new_hash(x, R->sizes[y]);
+      rc = new_hash(x, entries(y));
       if (rc) return rc;
       cc::ForgetArgs a{R->L, desc(y), (int)P.nodes[y].bag.size(),
                        pos_in(P.nodes[y].bag, nd.vertex), desc(x), c->d_err};
@@ -788,9 +829,9 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       release_child(y);
     } else {  // join
       int y = nd.child0, z = nd.child1;
-      if (R->sizes[y] > R->sizes[z]) std::swap(y, z);  // chain the smaller child
-      u64 icap = hash_cap(R->sizes[y], lf);
-      u64 bound_y = R->tables[y].hashed ? R->tables[y].cap : R->sizes[y];
+      if (entries(y) > entries(z)) std::swap(y, z);  // chain the smaller child
+      u64 icap = hash_cap(entries(y), lf);
+      u64 bound_y = R->tables[y].hashed || planned ? R->tables[y].cap : R->sizes[y];
       void *index = c->arena.alloc(icap * cc::index_slot_bytes(R->kw));
       u64 *next = arena_alloc<u64>(c, std::max<u64>(1, bound_y));
       if (!index || !next) {
@@ -799,8 +840,7 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
         return CC_ENOMEM;
       }
       CUDA_OK(cudaMemsetAsync(index, 0, icap * cc::index_slot_bytes(R->kw), c->stream));
-      u64 *pairs = blk + 2 * grid + 2;
-      CUDA_OK(cudaMemsetAsync(pairs, 0, sizeof(u64), c->stream));
+      u64 *pairs = pairs_dev + x;
       cc::JoinArgs a{};
       a.G = G;
       a.L = R->L;
@@ -814,11 +854,14 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       a.err = c->d_err;
       rc = timed(x, CC_K_JOIN_BUILD, 1,
                  [&] { return cc::launch_join(c->stream, c->dev, R->kw, 0, block, a); });
-      if (!rc)
+      u64 np = 0;
+      if (!rc && !planned) {
         rc = timed(x, CC_K_JOIN_COUNT, 1,
                    [&] { return cc::launch_join(c->stream, c->dev, R->kw, 1, block, a); });
-      u64 np = 0;
-      if (!rc) rc = read_u64(c, pairs, &np);
+        if (!rc) rc = read_u64(c, pairs, &np);
+        R->pairs[x] = np;
+      }
+      if (planned) np = room(plan->pairs[x]);
       if (!rc) rc = new_hash(x, np);
       if (!rc) {
         a.out = desc(x);
@@ -831,16 +874,38 @@ int run_plan(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col) {
       release_child(y);
       release_child(z);
     }
-    rc = read_u64(c, R->d_counters + x, &R->sizes[x]);
-    if (rc) return rc;
+    if (!planned) {
+      rc = read_u64(c, R->d_counters + x, &R->sizes[x]);
+      if (rc) return rc;
+    }
   }
   // root test (Section 3.1): per trial, nonempty root table and the sum of its counts
   cc::RootArgs ra{R->L, desc(N - 1), R->d_exists, R->d_count};
   rc = timed(N - 1, CC_K_ROOT, 1, [&] { return cc::launch_root(c->stream, c->dev, R->kw, ra); });
   if (rc) return rc;
+  return finish_run(c, R);
+}
+
+// reads the error word and, for planned runs, the sizes and capacity checks
+int finish_run(Ctx *c, Run *R) {
+  const int N = (int)R->sizes.size();
   int herr = 0;
+  std::vector<u64> words(4 * (size_t)N);
   CUDA_OK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaMemcpyAsync(words.data(), R->d_counters, words.size() * sizeof(u64),
+                          cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaStreamSynchronize(c->stream));
+  for (int x = 0; x < N; ++x) {
+    R->sizes[x] = words[x];
+    if (words[2 * N + x]) R->pairs[x] = words[2 * N + x];
+  }
+  for (auto &t : R->timings)
+    if (t.kind == CC_K_INTRO_COUNT || t.kind == CC_K_INTRO_WRITE || t.kind == CC_K_INTRO_FUSED)
+      t.candidates = words[3 * (size_t)N + t.node];
+  for (const auto &chk : R->checks) {
+    const u64 v = words[chk.first - R->d_counters];
+    if (v > chk.second) herr |= cc::kErrOverflow;
+  }
   if (herr & cc::kErrTimeout) return CC_ETIMEOUT;
   if (herr) return CC_ECAPACITY;
   return CC_OK;
@@ -1072,22 +1137,56 @@ int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **ou
   R->kw = width <= 64 ? 1 : 2;
   const int N = (int)P.nodes.size();
   col.refs++;  // released by free_run
-  R->d_counters = arena_alloc<u64>(c, N);
+  R->d_counters = arena_alloc<u64>(c, 4 * (size_t)N);
   R->d_exists = arena_alloc<unsigned>(c, col.trials);
   R->d_count = arena_alloc<u64>(c, col.trials);
   if (!R->d_counters || !R->d_exists || !R->d_count) {
     free_run(c, R.get());
     return CC_ENOMEM;
   }
-  CUDA_OK(cudaMemsetAsync(R->d_counters, 0, N * sizeof(u64), c->stream));
-  CUDA_OK(cudaMemsetAsync(R->d_exists, 0, col.trials * sizeof(unsigned), c->stream));
-  CUDA_OK(cudaMemsetAsync(R->d_count, 0, col.trials * sizeof(u64), c->stream));
   R->retained = R->opts.retain != 0;
-  int rc = run_plan(c, R.get(), P, col);
+  const std::vector<long long> key = {pid, c->graph_version, col.trials, col.k,
+                                      R->opts.degree_filter, R->opts.fuse, R->opts.group,
+                                      R->opts.block, (long long)(R->opts.load_factor * 1000)};
+  auto reset = [&]() -> int {
+    for (auto &t : R->tables)
+      if (t.slots) c->arena.release(t.slots);
+    R->tables.clear();
+    for (auto &t : R->timings) {
+      cudaEventDestroy(t.start);
+      cudaEventDestroy(t.stop);
+    }
+    R->timings.clear();
+    CUDA_OK(cudaMemsetAsync(R->d_counters, 0, 4 * (size_t)N * sizeof(u64), c->stream));
+    CUDA_OK(cudaMemsetAsync(R->d_exists, 0, col.trials * sizeof(unsigned), c->stream));
+    CUDA_OK(cudaMemsetAsync(R->d_count, 0, col.trials * sizeof(u64), c->stream));
+    return CC_OK;
+  };
+  int rc = reset();
+  auto pl = c->plans.find(key);
+  R->planned = pl != c->plans.end() && pl->second.runs > 0;
+  if (!rc && R->planned) {
+    rc = run_nodes(c, R.get(), P, col, &pl->second);
+    if (rc == CC_ECAPACITY || rc == CC_ENOMEM) {  // outgrew the plan: plan again, exactly
+      R->planned = false;
+      rc = reset();
+      if (!rc) rc = run_nodes(c, R.get(), P, col, nullptr);
+    }
+  } else if (!rc) {
+    rc = run_nodes(c, R.get(), P, col, nullptr);
+  }
   if (rc) {
     free_run(c, R.get());
     return rc;
   }
+  cc::Plan &plan = c->plans[key];
+  plan.entries.resize(N, 0);
+  plan.pairs.resize(N, 0);
+  for (int x = 0; x < N; ++x) {
+    plan.entries[x] = std::max(plan.entries[x], R->sizes[x]);
+    plan.pairs[x] = std::max(plan.pairs[x], R->pairs[x]);
+  }
+  plan.runs++;
   *out = R.release();
   return CC_OK;
 }
@@ -1150,7 +1249,9 @@ int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t aren
   }
   c->arena.init(base, arena_bytes);
   c->d_err = arena_alloc<int>(c, 1);
-  if (!c->d_err || ensure_scratch(c, 4096)) {
+  c->d_ones = arena_alloc<u64>(c, 1);
+  if (c->d_ones) cudaMemsetAsync(c->d_ones, 0xff, sizeof(u64), c->stream);
+  if (!c->d_err || !c->d_ones || ensure_scratch(c, 4096)) {
     if (c->owned_arena) cudaFree(c->owned_arena);
     delete c;
     return CC_ENOMEM;
@@ -1213,6 +1314,8 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   if (m2 > 0)
     CUDA_OK(cudaMemcpyAsync(c->d_col, h_col, (size_t)m2 * sizeof(int32_t),
                             cudaMemcpyHostToDevice, c->stream));
+  c->graph_version++;
+  c->plans.clear();
   c->h_row_ptr.assign(h_row_ptr, h_row_ptr + n + 1);
   c->h_col.assign(h_col, h_col + m2);
   c->n = n;

@@ -66,7 +66,8 @@ struct IntroArgs {
   TableDesc out;             // dense (mode 1) or hashed (mode 2) output
   int q;                     // mode 2: slot (in the new bag) of the vertex the parent forgets
   int proj_q;                // mode 1: if >= 0, write keys with this slot removed
-  unsigned long long *valid; // mode 2: number of introduce entries produced
+  unsigned long long *cursor;  // mode 1: non-null = chunked append from this cursor (no bases)
+  unsigned long long *valid; // modes 1, 2: number of introduce entries produced (if non-null)
   unsigned long long *cand;  // mode 0: number of candidate vertices examined
   int *err;
 };
@@ -136,13 +137,17 @@ struct SortSpec {
 // needs 256 * sort_grid(d) + 512 words.
 int sort_grid(const DevInfo &d);
 int sort_passes(const SortSpec &sp);
+// The record counts live on the device: the first pass scans min(*n_src, src_cap) slots of
+// src (holes skipped), later passes *n records.  buf_a / buf_b hold buf_cap records.
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
-                        const void *src, unsigned long long n_src, unsigned long long n,
-                        void *buf_a, void *buf_b, unsigned long long *hist, int *which);
+                        const void *src, const unsigned long long *n_src,
+                        unsigned long long src_cap, const unsigned long long *n,
+                        unsigned long long buf_cap, void *buf_a, void *buf_b,
+                        unsigned long long *hist, int *which);
 // One record per run of equal keys of the sorted `src` (n records) with the summed count, written
 // densely to dst; *count receives the number of runs.  blk needs 2 * sort_grid(d) + 1 words.
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
-                  unsigned long long n, unsigned long long *blk, void *dst,
+                  const unsigned long long *n, unsigned long long *blk, void *dst,
                   unsigned long long *count);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,

@@ -105,11 +105,16 @@ struct IntroSmem {
   int wc[BLOCK / 32];
   int hmax[BLOCK / 32];
   u64 red[BLOCK / 32];
+  u64 newbase;
   int vbuf[VCAP];
 };
 
+// chunked append: a block reserves output slots kAppendChunk at a time from a global cursor
+constexpr u64 kAppendChunk = 2048;
+
 struct EmitState {
   u64 produced = 0, fresh = 0, examined = 0, cursor = 0;
+  u64 chunk_base = 0, chunk_fill = kAppendChunk;  // block-uniform
   bool full = false;
 };
 
@@ -120,15 +125,34 @@ __device__ __forceinline__ void emit(const IntroArgs &a, S &sm, EmitState &st, b
     st.produced += valid;
   } else if (MODE == 1) {
     int tot;
-    int rank = block_flag_rank<BLOCK>(valid, sm.wc, tot);
+    const int rank = block_flag_rank<BLOCK>(valid, sm.wc, tot);
+    u64 pos = 0;
+    if (a.cursor) {  // chunked append (planned capacities): one atomic per chunk
+      const u64 idx = st.chunk_fill + (u64)rank;
+      const bool spill = st.chunk_fill + (u64)tot > kAppendChunk;  // block-uniform
+      if (spill) {
+        if (threadIdx.x == 0) sm.newbase = atomicAdd(a.cursor, kAppendChunk);
+        __syncthreads();
+      }
+      const u64 nb = spill ? sm.newbase : 0;
+      pos = idx < kAppendChunk ? st.chunk_base + idx : nb + (idx - kAppendChunk);
+      if (spill) {
+        st.chunk_base = nb;
+        st.chunk_fill = st.chunk_fill + (u64)tot - kAppendChunk;
+      } else {
+        st.chunk_fill += (u64)tot;
+      }
+    } else {  // exact bases from the count pass
+      pos = st.cursor + (u64)rank;
+      st.cursor += (u64)tot;
+    }
     if (valid) {
-      u64 pos = st.cursor + (u64)rank;
+      ++st.produced;
       if (pos < a.out.cap)
         store_slot(reinterpret_cast<Slot<K> *>(a.out.slots), pos,
                    a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
       else st.full = true;
     }
-    st.cursor += (u64)tot;
   } else if (valid) {
     ++st.produced;
     int r = hash_add(reinterpret_cast<Slot<K> *>(a.out.slots), a.out.cap,
@@ -331,6 +355,12 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
       plain_tile<K, MODE, BLOCK>(a, sm, st);
     __syncthreads();  // the next tile overwrites the shared arrays
   }
+  if (MODE == 1 && a.cursor && st.chunk_fill < kAppendChunk) {
+    // the unused tail of this block's last chunk becomes holes
+    Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+    for (u64 j = st.chunk_fill + threadIdx.x; j < kAppendChunk; j += BLOCK)
+      if (st.chunk_base + j < a.out.cap) store_slot(out, st.chunk_base + j, (K)0, 0ull);
+  }
   if (st.full) atomicOr(a.err, kErrOverflow);
   if (MODE == 0) {
     u64 s = block_sum<BLOCK>(st.produced, sm.red);
@@ -339,7 +369,20 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
       blk_count[blockIdx.x] = s;
       if (x) atomicAdd(a.cand, x);
     }
+  } else if (MODE == 1) {
+    if (a.valid) {
+      u64 s = block_sum<BLOCK>(st.produced, sm.red);
+      if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
+    }
+    if (a.cand) {
+      u64 x = block_sum<BLOCK>(st.examined, sm.red);
+      if (threadIdx.x == 0 && x) atomicAdd(a.cand, x);
+    }
   } else if (MODE == 2) {
+    if (a.cand) {
+      u64 x = block_sum<BLOCK>(st.examined, sm.red);
+      if (threadIdx.x == 0 && x) atomicAdd(a.cand, x);
+    }
     u64 s = block_sum<BLOCK>(st.produced, sm.red);
     if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
     u64 f = block_sum<BLOCK>(st.fresh, sm.red);

@@ -25,8 +25,10 @@ namespace {
 using namespace dev;
 
 template <typename K, typename SK, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) sort_hist_kernel(SortSpec sp, const void *src, u64 n,
-                                                          int shift, u64 *hist) {
+__global__ void __launch_bounds__(BLOCK) sort_hist_kernel(SortSpec sp, const void *src,
+                                                          const u64 *n_ptr, u64 n_cap, int shift,
+                                                          u64 *hist) {
+  const u64 n = min(*n_ptr, n_cap);
   __shared__ unsigned s_h[256];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   for (int d = threadIdx.x; d < 256; d += BLOCK) s_h[d] = 0;
@@ -92,9 +94,11 @@ __global__ void __launch_bounds__(256) digit_base_kernel(u64 *hist, int G) {
 }
 
 template <typename K, typename SK, int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const void *src, u64 n,
+__global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const void *src,
+                                                             const u64 *n_ptr, u64 n_cap,
                                                              int shift, const u64 *off,
                                                              void *dst, u64 dst_cap) {
+  const u64 n = min(*n_ptr, n_cap);
   static_assert(BLOCK == 256, "one thread per digit");
   constexpr int W = BLOCK / 32, TILE = BLOCK * ITEMS;
   __shared__ Slot<K> s_stage[TILE];
@@ -182,7 +186,9 @@ __global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const 
 
 // ---- reduce by key: equal keys are adjacent; one record per run with the summed count ------
 template <typename K, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, u64 n, u64 *blk) {
+__global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, const u64 *n_ptr,
+                                                             u64 *blk) {
+  const u64 n = *n_ptr;
   __shared__ u64 s_red[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   const u64 G = gridDim.x, chunk = (n + G - 1) / G;
@@ -212,8 +218,10 @@ __global__ void blk_scan_kernel(u64 *blk, int G) {
 }
 
 template <typename K, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, u64 n, const u64 *blk,
-                                                             void *dst, u64 *count) {
+__global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, const u64 *n_ptr,
+                                                             const u64 *blk, void *dst,
+                                                             u64 *count) {
+  const u64 n = *n_ptr;
   __shared__ int s_wc[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
@@ -250,21 +258,24 @@ __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, u6
 int grid256(const DevInfo &d) { return d.sms * d.blocks_per_sm; }
 
 template <typename K, typename SK, int ITEMS>
-int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *src, u64 n_src,
-              u64 n, void *buf_a, void *buf_b, u64 *hist, int *which) {
+int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *src,
+              const u64 *n_src, u64 src_cap, const u64 *n, u64 buf_cap, void *buf_a, void *buf_b,
+              u64 *hist, int *which) {
   const int G = grid256(d);
   const void *in = src;
-  u64 n_in = n_src;
+  const u64 *n_in = n_src;
+  u64 in_cap = src_cap;
   void *bufs[2] = {buf_a, buf_b};
   int cur = 0;
   for (int shift = 0; shift < sp.bits; shift += 8) {
-    sort_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist);
+    sort_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, in, n_in, in_cap, shift, hist);
     row_scan_kernel<<<256, 256, 0, s>>>(hist, G);
     digit_base_kernel<<<1, 256, 0, s>>>(hist, G);
-    sort_scatter_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(sp, in, n_in, shift, hist, bufs[cur],
-                                                             n);
+    sort_scatter_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(sp, in, n_in, in_cap, shift, hist,
+                                                             bufs[cur], buf_cap);
     in = bufs[cur];
     n_in = n;
+    in_cap = buf_cap;
     cur ^= 1;
   }
   *which = cur ^ 1;
@@ -278,23 +289,30 @@ int sort_grid(const DevInfo &d) { return grid256(d); }
 int sort_passes(const SortSpec &sp) { return (sp.bits + 7) / 8; }
 
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
-                        const void *src, unsigned long long n_src, unsigned long long n,
-                        void *buf_a, void *buf_b, unsigned long long *hist, int *which) {
+                        const void *src, const unsigned long long *n_src,
+                        unsigned long long src_cap, const unsigned long long *n,
+                        unsigned long long buf_cap, void *buf_a, void *buf_b,
+                        unsigned long long *hist, int *which) {
   *which = -1;
-  if (n == 0 || sp.bits == 0) return 0;
+  if (sp.bits == 0) return 0;
   if (kw == 1) {
-    return sp.bits <= 64 ? sort_impl<u64, u64, 8>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
-                         : sort_impl<u64, u128, 8>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
+    return sp.bits <= 64
+               ? sort_impl<u64, u64, 8>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
+                                        hist, which)
+               : sort_impl<u64, u128, 8>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
+                                         hist, which);
   }
-  return sp.bits <= 64 ? sort_impl<u128, u64, 4>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which)
-                       : sort_impl<u128, u128, 4>(s, d, sp, src, n_src, n, buf_a, buf_b, hist, which);
+  return sp.bits <= 64
+             ? sort_impl<u128, u64, 4>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
+                                       hist, which)
+             : sort_impl<u128, u128, 4>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
+                                        hist, which);
 }
 
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
-                  unsigned long long n, unsigned long long *blk, void *dst,
+                  const unsigned long long *n, unsigned long long *blk, void *dst,
                   unsigned long long *count) {
   const int G = grid256(d);
-  if (n == 0) return (int)cudaMemsetAsync(count, 0, sizeof(u64), s);
   if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk);
   else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk);
   blk_scan_kernel<<<1, 32, 0, s>>>(blk, G);

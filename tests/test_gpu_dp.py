@@ -295,3 +295,38 @@ def test_workload_ba20k_grid2x4_sampled(ctx):
     r1 = gpu_dp(ctx, g, pat, colours=z[[5, 40]], k=8)
     assert int(r1["count"][0]) == int(counts[5]) and int(r1["count"][1]) == int(counts[40])
     release(ctx, r1)
+
+
+def test_planned_runs_match_exact(ctx):
+    """A second run of the same pattern, graph, trials and colours uses the capacities planned
+    by the first (no count passes): results and table sizes are unchanged."""
+    g = synth.barabasi_albert(3000, 4, 7)
+    for pat in (synth.grid_pattern(2, 3), synth.pattern_B(), synth.random_partial_ktree(8, 2, 9)):
+        nF = pat[0]
+        ref = None
+        for rep in range(3):
+            colours = oracle.colors(3000, 4, nF, seed=40 + (rep % 2))
+            for fuse in (0, 1, 2):
+                r = gpu_dp(ctx, g, pat, colours=colours, k=nF, fuse=fuse)
+                want = oracle.run_dp(g, pat, colours, nF) if fuse == 0 else want
+                assert np.array_equal(r["count"], want.count)
+                assert np.array_equal(r["sizes"], want.node_sizes.sum(axis=0))
+                release(ctx, r)
+
+
+def test_planned_overflow_falls_back(ctx):
+    """Capacities planned on a colouring with tiny tables are too small for a random one; the
+    run notices, plans again exactly and still returns the oracle's results."""
+    g = synth.barabasi_albert(3000, 4, 8)
+    pat = synth.grid_pattern(2, 3)
+    mono = np.zeros((4, 3000), np.uint8)  # one colour: no colourful edge at all
+    r = gpu_dp(ctx, g, pat, colours=mono, k=6)
+    assert int(r["count"].sum()) == 0
+    release(ctx, r)
+    colours = oracle.colors(3000, 4, 6, seed=9)
+    for fuse in (1, 2, 0):
+        r = gpu_dp(ctx, g, pat, colours=colours, k=6, fuse=fuse)
+        ref = oracle.run_dp(g, pat, colours, 6)
+        assert np.array_equal(r["count"], ref.count)
+        assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+        release(ctx, r)
