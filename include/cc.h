@@ -142,10 +142,12 @@ typedef struct {
   int32_t profile;       /* 1: time every kernel launch with CUDA events (cc_run_timings)     */
   int32_t group;         /* 1: an introduce whose vertex has >= 2 bag neighbours first sorts   */
                          /*    its child by their images and shares candidate lists per run    */
+  int32_t sort_sweep;    /* 1: radix sorts take all digit counts in one read and one kernel   */
+                         /*    per pass (decoupled look-back); 0: histogram+scan+scatter passes */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
- * 0.5, block 256, profile 0, group 1). */
+ * 0.5, block 256, profile 0, group 1, sort_sweep 1). */
 void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in

@@ -649,18 +649,32 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     void *ba = c->arena.alloc(std::max<u64>(1, cap) * rb);
     void *bb = c->arena.alloc(std::max<u64>(1, cap) * rb);
     u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev) + 512);
-    if (!ba || !bb || !hist) {
+    // one-sweep scratch: tiles of the largest pass input (the scanned source or the buffers)
+    cc::SweepScratch sw{};
+    sw.max_tiles = std::max(src_cap, cap) / cc::sweep_tile(R->kw) + 2;
+    sw.ghist = arena_alloc<u64>(c, 256 * 16);
+    sw.tile_ctr = arena_alloc<unsigned>(c, 16);
+    sw.status = arena_alloc<u64>(c, 256 * sw.max_tiles);
+    sw.err = c->d_err;
+    if (!ba || !bb || !hist || !sw.ghist || !sw.tile_ctr || !sw.status) {
       c->arena.release(ba);
       c->arena.release(bb);
       c->arena.release(hist);
+      c->arena.release(sw.ghist);
+      c->arena.release(sw.tile_ctr);
+      c->arena.release(sw.status);
       return CC_ENOMEM;
     }
     int which = 0;
-    int r = timed(node, CC_K_SORT, 4 * cc::sort_passes(sp), [&] {
+    const bool sweep = R->opts.sort_sweep != 0;
+    int r = timed(node, CC_K_SORT, sweep ? 2 + cc::sort_passes(sp) : 4 * cc::sort_passes(sp), [&] {
       return cc::launch_sort_records(c->stream, c->dev, R->kw, sp, src, n_src, src_cap, nn, cap,
-                                     ba, bb, hist, &which);
+                                     ba, bb, hist, &which, sweep ? &sw : nullptr);
     });
     c->arena.release(hist);
+    c->arena.release(sw.ghist);
+    c->arena.release(sw.tile_ctr);
+    c->arena.release(sw.status);
     c->arena.release(which ? ba : bb);
     *out = which ? bb : ba;
     return r;
@@ -1147,7 +1161,8 @@ int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **ou
   R->retained = R->opts.retain != 0;
   const std::vector<long long> key = {pid, c->graph_version, col.trials, col.k,
                                       R->opts.degree_filter, R->opts.fuse, R->opts.group,
-                                      R->opts.block, (long long)(R->opts.load_factor * 1000)};
+                                      R->opts.block, (long long)(R->opts.load_factor * 1000),
+                                      R->opts.sort_sweep};
   auto reset = [&]() -> int {
     for (auto &t : R->tables)
       if (t.slots) c->arena.release(t.slots);
@@ -1222,6 +1237,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->profile = 0;
   o->group = 1;
   o->fuse = 2;
+  o->sort_sweep = 1;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {

@@ -137,13 +137,23 @@ struct SortSpec {
 // needs 256 * sort_grid(d) + 512 words.
 int sort_grid(const DevInfo &d);
 int sort_passes(const SortSpec &sp);
+// Scratch of a one-sweep sort: 256 digit counts per pass, a tile counter per pass, and 256
+// look-back words per tile of the largest pass (max_tiles >= records / sweep_tile(kw) + 1).
+struct SweepScratch {
+  unsigned long long *ghist;
+  unsigned *tile_ctr;
+  unsigned long long *status;
+  unsigned long long max_tiles;
+  int *err;
+};
+int sweep_tile(int kw);
 // The record counts live on the device: the first pass scans min(*n_src, src_cap) slots of
 // src (holes skipped), later passes *n records.  buf_a / buf_b hold buf_cap records.
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
                         const void *src, const unsigned long long *n_src,
                         unsigned long long src_cap, const unsigned long long *n,
                         unsigned long long buf_cap, void *buf_a, void *buf_b,
-                        unsigned long long *hist, int *which);
+                        unsigned long long *hist, int *which, const SweepScratch *sw);
 // One record per run of equal keys of the sorted `src` (n records) with the summed count, written
 // densely to dst; *count receives the number of runs.  blk needs 2 * sort_grid(d) + 1 words.
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,

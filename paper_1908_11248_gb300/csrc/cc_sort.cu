@@ -184,6 +184,180 @@ __global__ void __launch_bounds__(BLOCK) sort_scatter_kernel(SortSpec sp, const 
   }
 }
 
+// ---- one-sweep passes ------------------------------------------------------------------
+// All digit histograms come from one read of the input (per pass, 256 global counts turned into
+// digit bases).  Each pass is then one kernel: blocks claim tiles in increasing order, publish
+// their tile's digit counts, and find the counts of all earlier tiles by looking back through
+// the published words (decoupled look-back): an "aggregate" word carries one tile's count, an
+// "inclusive" word the sum over it and all tiles before it.  A word is (epoch << 48) |
+// (inclusive << 47) | count; words of another epoch are not yet published.  Waiting for an
+// earlier tile is bounded: after kSpinLimit polls the pass records a timeout and goes on.
+constexpr u64 kCountMask = (1ull << 47) - 1ull;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+template <typename K, typename SK, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) sweep_hist_kernel(SortSpec sp, const void *src,
+                                                           const u64 *n_ptr, u64 n_cap,
+                                                           int passes, u64 *ghist) {
+  __shared__ unsigned h[16][256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  for (int i = threadIdx.x; i < 16 * 256; i += BLOCK) h[i / 256][i % 256] = 0;
+  __syncthreads();
+  const u64 n = min(*n_ptr, n_cap);
+  for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < n; i += (u64)gridDim.x * BLOCK) {
+    K key;
+    u64 c;
+    load_slot(in, i, key, c);
+    if (key == 0) continue;
+    const SK k = sort_key<SK>(key, sp);
+    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += BLOCK)
+    if (h[i / 256][i % 256]) atomicAdd(&ghist[i], (u64)h[i / 256][i % 256]);
+}
+
+// per pass (one block each): exclusive scan of its 256 digit counts, in place
+__global__ void __launch_bounds__(256) sweep_bases_kernel(u64 *ghist) {
+  __shared__ u64 s_w[8];
+  u64 *row = ghist + (u64)blockIdx.x * 256;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u64 v = row[threadIdx.x];
+  u64 x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  u64 before = 0;
+  for (int q = 0; q < w; ++q) before += s_w[q];
+  row[threadIdx.x] = before + x - v;
+}
+
+template <typename K, typename SK, int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) sweep_pass_kernel(SortSpec sp, const void *src,
+                                                           const u64 *n_ptr, u64 n_cap, int shift,
+                                                           u64 epoch, const u64 *bases,
+                                                           u64 *status, unsigned *tile_ctr,
+                                                           void *dst, u64 dst_cap, int *err) {
+  static_assert(BLOCK == 256, "one thread per digit");
+  constexpr int W = BLOCK / 32, TILE = BLOCK * ITEMS;
+  __shared__ Slot<K> s_stage[TILE];
+  __shared__ unsigned char s_sdig[TILE];
+  __shared__ unsigned s_wc[W][256];
+  __shared__ unsigned s_thist[256], s_tstart[256], s_trun[256], s_wsum[W];
+  __shared__ u64 s_excl[256];
+  __shared__ unsigned s_tile;
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const u64 n = min(*n_ptr, n_cap);
+  const u64 tiles = (n + TILE - 1) / TILE;
+  const u64 base_d = bases[tid];
+  for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const u64 tile = s_tile;
+    if (tile >= tiles) break;
+    const u64 tb = tile * TILE;
+    K key[ITEMS];
+    u64 cnt[ITEMS];
+    int dig[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const u64 i = tb + (u64)j * BLOCK + tid;
+      key[j] = 0;
+      cnt[j] = 0;
+      if (i < n) load_slot(in, i, key[j], cnt[j]);
+      dig[j] = key[j] != 0 ? (int)((unsigned)(sort_key<SK>(key[j], sp) >> shift) & 255u) : -1;
+    }
+    s_thist[tid] = 0;
+    s_trun[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+      if (dig[j] >= 0) atomicAdd(&s_thist[dig[j]], 1u);
+    __syncthreads();
+    {  // publish this tile's count of digit tid, then look back for the tiles before it
+      const u64 mine = s_thist[tid];
+      u64 *word = status + tile * 256 + tid;
+      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | mine);
+      u64 excl = 0;
+      if (tile > 0) {
+        long long j = (long long)tile - 1;
+        unsigned spins = 0;
+        while (j >= 0) {
+          const u64 v = __ldcv(status + (u64)j * 256 + tid);
+          if ((v >> 48) != epoch) {
+            if (++spins > kSpinLimit) {
+              atomicOr(err, kErrTimeout);
+              break;
+            }
+            continue;
+          }
+          excl += v & kCountMask;
+          if (v >> 47 & 1ull) break;
+          --j;
+        }
+        atomicExch(word, (epoch << 48) | (1ull << 47) | (excl + mine));
+      }
+      s_excl[tid] = excl;
+    }
+    {  // exclusive scan of the tile histogram, thread d owns digit d
+      unsigned v = s_thist[tid], x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[w] = x;
+      __syncthreads();
+      unsigned before = 0;
+      for (int q = 0; q < w; ++q) before += s_wsum[q];
+      s_tstart[tid] = before + x - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int d = dig[j];
+      const unsigned peers = __match_any_sync(0xffffffffu, d >= 0 ? d : 256 + lane);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      if (d >= 0 && lane == __ffs(peers) - 1) s_wc[w][d] = __popc(peers);
+      __syncthreads();
+      {
+        unsigned acc = s_trun[tid];
+        for (int x = 0; x < W; ++x) {
+          unsigned c = s_wc[x][tid];
+          s_wc[x][tid] = acc;
+          acc += c;
+        }
+        s_trun[tid] = acc;
+      }
+      __syncthreads();
+      if (d >= 0) {
+        const unsigned local = s_tstart[d] + s_wc[w][d] + rank;
+        s_stage[local].key = key[j];
+        s_stage[local].cnt = cnt[j];
+        s_sdig[local] = (unsigned char)d;
+      }
+      __syncthreads();
+      for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+      __syncthreads();
+    }
+    // s_excl holds, per digit, the records of that digit in all earlier tiles
+    s_excl[tid] += base_d;
+    __syncthreads();
+    const unsigned tcount = s_tstart[255] + s_thist[255];
+    for (unsigned i = tid; i < tcount; i += BLOCK) {
+      const int d = s_sdig[i];
+      const u64 pos = s_excl[d] + (i - s_tstart[d]);
+      if (pos < dst_cap) store_slot(out, pos, s_stage[i].key, s_stage[i].cnt);
+    }
+    __syncthreads();
+  }
+}
+
 // ---- reduce by key: equal keys are adjacent; one record per run with the summed count ------
 template <typename K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, const u64 *n_ptr,
@@ -260,13 +434,32 @@ int grid256(const DevInfo &d) { return d.sms * d.blocks_per_sm; }
 template <typename K, typename SK, int ITEMS>
 int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *src,
               const u64 *n_src, u64 src_cap, const u64 *n, u64 buf_cap, void *buf_a, void *buf_b,
-              u64 *hist, int *which) {
+              u64 *hist, int *which, const SweepScratch *sw) {
   const int G = grid256(d);
   const void *in = src;
   const u64 *n_in = n_src;
   u64 in_cap = src_cap;
   void *bufs[2] = {buf_a, buf_b};
   int cur = 0;
+  const int passes = (sp.bits + 7) / 8;
+  if (sw) {  // one-sweep: histograms once, then one kernel per pass
+    cudaMemsetAsync(sw->ghist, 0, sizeof(u64) * 256 * passes, s);
+    cudaMemsetAsync(sw->tile_ctr, 0, sizeof(unsigned) * passes, s);
+    cudaMemsetAsync(sw->status, 0, sizeof(u64) * 256 * sw->max_tiles, s);
+    sweep_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, src, n_src, src_cap, passes, sw->ghist);
+    sweep_bases_kernel<<<passes, 256, 0, s>>>(sw->ghist);
+    for (int p = 0; p < passes; ++p) {
+      sweep_pass_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(
+          sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,
+          sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);
+      in = bufs[cur];
+      n_in = n;
+      in_cap = buf_cap;
+      cur ^= 1;
+    }
+    *which = cur ^ 1;
+    return (int)cudaGetLastError();
+  }
   for (int shift = 0; shift < sp.bits; shift += 8) {
     sort_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, in, n_in, in_cap, shift, hist);
     row_scan_kernel<<<256, 256, 0, s>>>(hist, G);
@@ -288,25 +481,27 @@ int sort_grid(const DevInfo &d) { return grid256(d); }
 
 int sort_passes(const SortSpec &sp) { return (sp.bits + 7) / 8; }
 
+int sweep_tile(int kw) { return kw == 1 ? 256 * 8 : 256 * 4; }
+
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
                         const void *src, const unsigned long long *n_src,
                         unsigned long long src_cap, const unsigned long long *n,
                         unsigned long long buf_cap, void *buf_a, void *buf_b,
-                        unsigned long long *hist, int *which) {
+                        unsigned long long *hist, int *which, const SweepScratch *sw) {
   *which = -1;
   if (sp.bits == 0) return 0;
   if (kw == 1) {
     return sp.bits <= 64
                ? sort_impl<u64, u64, 8>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
-                                        hist, which)
+                                        hist, which, sw)
                : sort_impl<u64, u128, 8>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
-                                         hist, which);
+                                         hist, which, sw);
   }
   return sp.bits <= 64
              ? sort_impl<u128, u64, 4>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
-                                       hist, which)
+                                       hist, which, sw)
              : sort_impl<u128, u128, 4>(s, d, sp, src, n_src, src_cap, n, buf_cap, buf_a, buf_b,
-                                        hist, which);
+                                        hist, which, sw);
 }
 
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
