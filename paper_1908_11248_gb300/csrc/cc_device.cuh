@@ -270,5 +270,25 @@ __device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
   return s;
 }
 
+// Inverse of a full sort key (sp.full == 1): the packed key it was made from.
+template <typename K>
+__device__ __forceinline__ K unsort_key(K s, const SortSpec &sp) {
+  const KeyLayout &L = sp.L;
+  K key = s & (K)((1ull << L.k) - 1ull);
+  s >>= L.k;
+  if (L.tb) {
+    key |= (s & (K)((1ull << L.tb) - 1ull)) << L.tpos;
+    s >>= L.tb;
+  }
+  const K vmask = (K)((1ull << L.nb) - 1ull);
+#pragma unroll
+  for (int j = kMaxBag - 1; j >= 0; --j)
+    if (j < sp.b) {
+      key |= (s & vmask) << (L.k + sp.order[j] * L.nb);
+      s >>= L.nb;
+    }
+  return key;
+}
+
 }  // namespace dev
 }  // namespace cc

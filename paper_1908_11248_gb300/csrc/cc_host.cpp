@@ -808,7 +808,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         }
         rc = timed(f, CC_K_REDUCE, 3, [&] {
           return cc::launch_reduce(c->stream, c->dev, R->kw, srt, R->d_counters + x, blk, out,
-                                   R->d_counters + f);
+                                   R->d_counters + f, R->opts.sort_sweep ? &sp : nullptr);
         });
         c->arena.release(srt);
         if (rc) return rc;

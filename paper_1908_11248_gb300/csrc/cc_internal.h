@@ -156,9 +156,11 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
                         unsigned long long *hist, int *which, const SweepScratch *sw);
 // One record per run of equal keys of the sorted `src` (n records) with the summed count, written
 // densely to dst; *count receives the number of runs.  blk needs 2 * sort_grid(d) + 1 words.
+// With from_s non-null the records carry full sort keys of that order (a one-sweep sort leaves
+// them so) and are written back as packed keys.
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
                   const unsigned long long *n, unsigned long long *blk, void *dst,
-                  unsigned long long *count);
+                  unsigned long long *count, const SortSpec *from_s);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
                 const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write

@@ -235,55 +235,63 @@ __global__ void __launch_bounds__(256) sweep_bases_kernel(u64 *ghist) {
   row[threadIdx.x] = before + x - v;
 }
 
-template <typename K, typename SK, int BLOCK, int ITEMS>
+// One pass.  Warp w of the block owns elements [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, read
+// in ITEMS coalesced rounds; stable ranks come from the warp's own sequential rounds (match on
+// the digit, one leader per digit) on top of per-(warp, digit) bases, so a tile needs five
+// block barriers.  With STORE_S the records leave carrying their sort key in place of the packed
+// key (a full sort key is a bijection of the key): later passes read digits off it directly,
+// and reduce-by-key turns it back.
+template <typename K, typename SK, int BLOCK, int ITEMS, bool FROM_KEY, bool STORE_S>
 __global__ void __launch_bounds__(BLOCK) sweep_pass_kernel(SortSpec sp, const void *src,
                                                            const u64 *n_ptr, u64 n_cap, int shift,
                                                            u64 epoch, const u64 *bases,
                                                            u64 *status, unsigned *tile_ctr,
                                                            void *dst, u64 dst_cap, int *err) {
   static_assert(BLOCK == 256, "one thread per digit");
-  constexpr int W = BLOCK / 32, TILE = BLOCK * ITEMS;
+  constexpr int W = BLOCK / 32, TILE = BLOCK * ITEMS, PER_WARP = 32 * ITEMS;
   __shared__ Slot<K> s_stage[TILE];
   __shared__ unsigned char s_sdig[TILE];
   __shared__ unsigned s_wc[W][256];
-  __shared__ unsigned s_thist[256], s_tstart[256], s_trun[256], s_wsum[W];
+  __shared__ unsigned s_tstart[256], s_wsum[W];
   __shared__ u64 s_excl[256];
-  __shared__ unsigned s_tile;
+  __shared__ unsigned s_tile, s_tcount;
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const u64 n = min(*n_ptr, n_cap);
   const u64 tiles = (n + TILE - 1) / TILE;
   const u64 base_d = bases[tid];
   for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
   while (true) {
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    __syncthreads();
+    __syncthreads();  // (1) also orders the previous tile's write-out before reuse
     const u64 tile = s_tile;
     if (tile >= tiles) break;
-    const u64 tb = tile * TILE;
+    const u64 wb = tile * TILE + (u64)w * PER_WARP;
     K key[ITEMS];
     u64 cnt[ITEMS];
     int dig[ITEMS];
+    unsigned peers[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      const u64 i = tb + (u64)j * BLOCK + tid;
+      const u64 i = wb + (u64)j * 32 + lane;
       key[j] = 0;
       cnt[j] = 0;
       if (i < n) load_slot(in, i, key[j], cnt[j]);
-      dig[j] = key[j] != 0 ? (int)((unsigned)(sort_key<SK>(key[j], sp) >> shift) & 255u) : -1;
+      if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
+      SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
+      dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
+      peers[j] = __match_any_sync(0xffffffffu, dig[j] >= 0 ? dig[j] : 256 + lane);
+      if (dig[j] >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][dig[j]] += __popc(peers[j]);
+      __syncwarp();
     }
-    s_thist[tid] = 0;
-    s_trun[tid] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j)
-      if (dig[j] >= 0) atomicAdd(&s_thist[dig[j]], 1u);
-    __syncthreads();
+    __syncthreads();  // (2)
+    unsigned tcount_d = 0;  // records of digit tid in this tile
+    for (int x = 0; x < W; ++x) tcount_d += s_wc[x][tid];
     {  // publish this tile's count of digit tid, then look back for the tiles before it
-      const u64 mine = s_thist[tid];
       u64 *word = status + tile * 256 + tid;
-      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | mine);
+      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | tcount_d);
       u64 excl = 0;
       if (tile > 0) {
         long long j = (long long)tile - 1;
@@ -301,60 +309,50 @@ __global__ void __launch_bounds__(BLOCK) sweep_pass_kernel(SortSpec sp, const vo
           if (v >> 47 & 1ull) break;
           --j;
         }
-        atomicExch(word, (epoch << 48) | (1ull << 47) | (excl + mine));
+        atomicExch(word, (epoch << 48) | (1ull << 47) | (excl + tcount_d));
       }
-      s_excl[tid] = excl;
+      s_excl[tid] = base_d + excl;
     }
-    {  // exclusive scan of the tile histogram, thread d owns digit d
-      unsigned v = s_thist[tid], x = v;
+    {  // tile-local start of digit tid, then each warp's base within it
+      unsigned x = tcount_d;
       for (int o = 1; o < 32; o <<= 1) {
         unsigned y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
       if (lane == 31) s_wsum[w] = x;
-      __syncthreads();
-      unsigned before = 0;
-      for (int q = 0; q < w; ++q) before += s_wsum[q];
-      s_tstart[tid] = before + x - v;
+      __syncthreads();  // (3)
+      unsigned start = x - tcount_d;
+      for (int q = 0; q < w; ++q) start += s_wsum[q];
+      s_tstart[tid] = start;
+      if (tid == 255) s_tcount = start + tcount_d;  // records in the tile
+      for (int q = 0; q < W; ++q) {
+        const unsigned c = s_wc[q][tid];
+        s_wc[q][tid] = start;
+        start += c;
+      }
     }
-    __syncthreads();
+    __syncthreads();  // (4)
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const int d = dig[j];
-      const unsigned peers = __match_any_sync(0xffffffffu, d >= 0 ? d : 256 + lane);
-      const int rank = __popc(peers & ((1u << lane) - 1u));
-      if (d >= 0 && lane == __ffs(peers) - 1) s_wc[w][d] = __popc(peers);
-      __syncthreads();
-      {
-        unsigned acc = s_trun[tid];
-        for (int x = 0; x < W; ++x) {
-          unsigned c = s_wc[x][tid];
-          s_wc[x][tid] = acc;
-          acc += c;
-        }
-        s_trun[tid] = acc;
-      }
-      __syncthreads();
       if (d >= 0) {
-        const unsigned local = s_tstart[d] + s_wc[w][d] + rank;
+        const unsigned local = s_wc[w][d] + __popc(peers[j] & lt);
         s_stage[local].key = key[j];
         s_stage[local].cnt = cnt[j];
         s_sdig[local] = (unsigned char)d;
       }
-      __syncthreads();
-      for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
-      __syncthreads();
+      __syncwarp();
+      if (d >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][d] += __popc(peers[j]);
+      __syncwarp();
     }
-    // s_excl holds, per digit, the records of that digit in all earlier tiles
-    s_excl[tid] += base_d;
-    __syncthreads();
-    const unsigned tcount = s_tstart[255] + s_thist[255];
+    __syncthreads();  // (5)
+    const unsigned tcount = s_tcount;
     for (unsigned i = tid; i < tcount; i += BLOCK) {
       const int d = s_sdig[i];
       const u64 pos = s_excl[d] + (i - s_tstart[d]);
       if (pos < dst_cap) store_slot(out, pos, s_stage[i].key, s_stage[i].cnt);
     }
-    __syncthreads();
+    for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
   }
 }
 
@@ -391,10 +389,10 @@ __global__ void blk_scan_kernel(u64 *blk, int G) {
   }
 }
 
-template <typename K, int BLOCK>
+template <typename K, int BLOCK, bool FROM_S>
 __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, const u64 *n_ptr,
                                                              const u64 *blk, void *dst,
-                                                             u64 *count) {
+                                                             u64 *count, SortSpec sp) {
   const u64 n = *n_ptr;
   __shared__ int s_wc[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
@@ -423,7 +421,7 @@ __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, co
     }
     int tot;
     const int rank = block_flag_rank<BLOCK>(head, s_wc, tot);
-    if (head) store_slot(out, cursor + rank, key, sum);
+    if (head) store_slot(out, cursor + rank, FROM_S ? unsort_key(key, sp) : key, sum);
     cursor += (u64)tot;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = blk[2 * G];
@@ -449,9 +447,14 @@ int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *
     sweep_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, src, n_src, src_cap, passes, sw->ghist);
     sweep_bases_kernel<<<passes, 256, 0, s>>>(sw->ghist);
     for (int p = 0; p < passes; ++p) {
-      sweep_pass_kernel<K, SK, 256, ITEMS><<<G, 256, 0, s>>>(
-          sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,
-          sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);
+#define CC_PASS(FK, SS)                                                                   \
+  sweep_pass_kernel<K, SK, 256, ITEMS, FK, SS><<<G, 256, 0, s>>>(                          \
+      sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,         \
+      sw->tile_ctr + p, bufs[cur], buf_cap, sw->err)
+      if (!sp.full) CC_PASS(true, false);   // partial order: recompute the tuple each pass
+      else if (p == 0) CC_PASS(true, true); // full order: records carry their sort key after
+      else CC_PASS(false, true);            // the first pass
+#undef CC_PASS
       in = bufs[cur];
       n_in = n;
       in_cap = buf_cap;
@@ -506,13 +509,19 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
 
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
                   const unsigned long long *n, unsigned long long *blk, void *dst,
-                  unsigned long long *count) {
+                  unsigned long long *count, const SortSpec *from_s) {
   const int G = grid256(d);
+  const SortSpec sp = from_s ? *from_s : SortSpec{};
   if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk);
   else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk);
   blk_scan_kernel<<<1, 32, 0, s>>>(blk, G);
-  if (kw == 1) reduce_write_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk, dst, count);
-  else reduce_write_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk, dst, count);
+  if (kw == 1) {
+    if (from_s) reduce_write_kernel<u64, 256, true><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+    else reduce_write_kernel<u64, 256, false><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+  } else {
+    if (from_s) reduce_write_kernel<u128, 256, true><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+    else reduce_write_kernel<u128, 256, false><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+  }
   return (int)cudaGetLastError();
 }
 
