@@ -274,11 +274,14 @@ __global__ void __launch_bounds__(BLOCK) sweep_pass_kernel(SortSpec sp, const vo
     int dig[ITEMS];
     unsigned peers[ITEMS];
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {  // all loads first, so that they are in flight together
       const u64 i = wb + (u64)j * 32 + lane;
       key[j] = 0;
       cnt[j] = 0;
       if (i < n) load_slot(in, i, key[j], cnt[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
       if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
       SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
       dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
