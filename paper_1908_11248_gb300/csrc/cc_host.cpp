@@ -170,6 +170,7 @@ struct Ctx {
   // graph
   int32_t n = -1;
   int32_t *d_row_ptr = nullptr, *d_col = nullptr;
+  uint8_t *d_deg8 = nullptr;  // min(degree, 255) per vertex
   std::vector<int32_t> h_row_ptr, h_col;
   int *d_err = nullptr;
   u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
@@ -551,7 +552,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   const int block = R->opts.block;
   const int df = R->opts.degree_filter;
   const bool planned = plan != nullptr;
-  cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n};
+  cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n, c->d_deg8};
   R->tables.assign(N, {});
   R->sizes.assign(N, 0);
   R->pairs.assign(N, 0);
@@ -760,8 +761,10 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.cursor = planned ? cursor + x : nullptr;
         a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
         if (planned) check(cursor + x, cap);
+        const bool warp = planned && a.nnb <= 1;  // lean warp kernel for expanding introduces
         int r = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
+          return warp ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 1, a)
+                      : cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
         });
         if (R->opts.profile && !r) R->timings.back().candidates = cand;
         return r;
@@ -775,8 +778,10 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.q = pos_in(nd.bag, P.nodes[f].vertex);
         a.valid = R->d_counters + x;
         a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
+        const bool warp = planned && a.nnb <= 1;
         rc = timed(x, CC_K_INTRO_FUSED, 1, [&] {
-          return cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a, blk);
+          return warp ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 2, a)
+                      : cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a, blk);
         });
         if (rc) return rc;
         if (R->opts.profile) R->timings.back().candidates = cand;
@@ -1024,7 +1029,7 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
     return CC_ECUDA;
   }
   cc::EnumArgs a{};
-  a.G = cc::GraphDev{c->d_row_ptr, c->d_col, col.d_colors, c->n};
+  a.G = cc::GraphDev{c->d_row_ptr, c->d_col, col.d_colors, c->n, c->d_deg8};
   a.L = R->L;
   a.nodes = d_nodes;
   a.nF = nF;
@@ -1319,9 +1324,11 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   c->colorings.clear();
   c->arena.release(c->d_row_ptr);
   c->arena.release(c->d_col);
+  c->arena.release(c->d_deg8);
   c->d_row_ptr = arena_alloc<int32_t>(c, (size_t)n + 1);
   c->d_col = arena_alloc<int32_t>(c, std::max<int64_t>(1, m2));
-  if (!c->d_row_ptr || !c->d_col) {
+  c->d_deg8 = arena_alloc<uint8_t>(c, std::max<int64_t>(1, n));
+  if (!c->d_row_ptr || !c->d_col || !c->d_deg8) {
     c->n = -1;
     return CC_ENOMEM;
   }
@@ -1330,6 +1337,8 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   if (m2 > 0)
     CUDA_OK(cudaMemcpyAsync(c->d_col, h_col, (size_t)m2 * sizeof(int32_t),
                             cudaMemcpyHostToDevice, c->stream));
+  if (cc::launch_deg8(c->stream, c->dev, c->d_row_ptr, n, c->d_deg8)) return CC_ECUDA;
+  c->launches++;
   c->graph_version++;
   c->plans.clear();
   c->h_row_ptr.assign(h_row_ptr, h_row_ptr + n + 1);

@@ -43,6 +43,7 @@ struct GraphDev {
   const int32_t *col;      // row_ptr[n]
   const uint8_t *colors;   // trials * n
   int32_t n;
+  const uint8_t *deg8;     // min(degree, 255) per vertex (pattern degrees are below 32)
 };
 
 struct LeafArgs {
@@ -161,6 +162,12 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
                   const unsigned long long *n, unsigned long long *blk, void *dst,
                   unsigned long long *count, const SortSpec *from_s);
+// Introduce of a vertex with at most one bag neighbour, warp by warp, for planned runs: mode 1
+// appends in per-warp chunks from a.cursor (holes left where chunks are not filled), mode 2
+// adds into the parent forget's hash table.
+int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a);
+int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
+                uint8_t *deg8);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
                 const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write

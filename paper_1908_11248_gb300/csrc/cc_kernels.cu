@@ -216,7 +216,7 @@ __device__ __forceinline__ void plain_tile(const IntroArgs &a, S &sm, EmitState 
       const int t = key_trial(ekey, a.L);
       const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
       valid = !((key_mask(ekey, a.L) >> cv) & 1u);
-      if (valid && a.degF) valid = a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
+      if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
       if (valid) {
         const int an = sm.anc[e];
         for (int q = 0; q < a.nnb && valid; ++q)
@@ -286,7 +286,7 @@ __device__ __forceinline__ bool grouped_tile(const IntroArgs &a, S &sm, EmitStat
     if (j < total) {
       e = owner<BLOCK>(sm.off, j);
       v = __ldg(a.G.col + sm.rs[e] + (j - sm.off[e]));
-      ok = a.degF == 0 || a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF;
+      ok = a.degF == 0 || a.G.deg8[v] >= a.degF;
       if (ok) {
         const K ekey = sm.key[e];
         const int an = sm.anc[e];
@@ -387,6 +387,137 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
     if (threadIdx.x == 0 && s) atomicAdd(a.valid, s);
     u64 f = block_sum<BLOCK>(st.fresh, sm.red);
     if (threadIdx.x == 0 && f) atomicAdd(a.out.count, f);
+  }
+}
+
+// ---- introduce, warp by warp (planned capacities, vertex with at most one bag neighbour) ------
+// Each warp takes 32 child entries at a time, scans their candidate counts with shuffles and
+// walks the concatenated candidate lists 32 at a time; a lane finds the entry owning its
+// candidate by a five-step binary search over the warp's prefix sums.  Outputs go to per-warp
+// chunks of the output (MODE 1) or into the parent forget's hash table (MODE 2).  No block
+// barrier is involved.
+constexpr u64 kWarpChunk = 256;
+
+__device__ __forceinline__ u64 shfl_key(u64 v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ u128 shfl_key(u128 v, int src) {
+  const u64 lo = __shfl_sync(0xffffffffu, (u64)v, src);
+  const u64 hi = __shfl_sync(0xffffffffu, (u64)(v >> 64), src);
+  return ((u128)hi << 64) | (u128)lo;
+}
+
+template <typename K, int MODE>
+__global__ void __launch_bounds__(256) intro_warp_kernel(IntroArgs a) {
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
+  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const u64 bound = table_bound<K>(a.in);
+  u64 cbase = 0, cfill = kWarpChunk;  // warp-uniform chunk state
+  u64 produced = 0, fresh = 0, examined = 0;
+  bool full = false;
+  for (u64 base = wid * 32; base < bound; base += warps * 32) {
+    const u64 i = base + lane;
+    K key = 0;
+    u64 c = 0;
+    if (i < bound) load_slot(in, i, key, c);
+    long long nc = 0;
+    int rs = 0;
+    if (key != 0) {
+      if (a.nnb == 0) {
+        nc = a.G.n;
+      } else {
+        const int w = key_slot(key, a.L, a.nb_slot[0]);
+        rs = a.G.row_ptr[w];
+        nc = a.G.row_ptr[w + 1] - rs;
+      }
+    }
+    long long incl = nc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) examined += (u64)total;
+    for (long long j0 = 0; j0 < total; j0 += 32) {
+      const long long j = j0 + lane;
+      bool valid = false;
+      K okey = 0;
+      u64 oc = 0;
+      // owner: smallest lane o with incl[o] > j
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const long long v = __shfl_sync(0xffffffffu, incl, mid);
+        if (v > j) hi = mid;
+        else lo = mid + 1;
+      }
+      const int o = lo;
+      const K ekey = shfl_key(key, o);
+      const u64 ec = __shfl_sync(0xffffffffu, c, o);
+      const int ers = __shfl_sync(0xffffffffu, rs, o);
+      const long long eincl = __shfl_sync(0xffffffffu, incl, o);
+      const long long enc = __shfl_sync(0xffffffffu, nc, o);
+      if (j < total) {
+        const long long r = j - (eincl - enc);
+        const int v = a.nnb ? __ldg(a.G.col + ers + r) : (int)r;
+        const int t = key_trial(ekey, a.L);
+        const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+        valid = !((key_mask(ekey, a.L) >> cv) & 1u);
+        if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+        if (valid) {
+          okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
+          oc = ec;
+        }
+      }
+      if (MODE == 1) {
+        const unsigned bal = __ballot_sync(0xffffffffu, valid);
+        const u64 tot = __popc(bal);
+        const u64 idx = cfill + __popc(bal & lt);
+        u64 nb = 0;
+        const bool spill = cfill + tot > kWarpChunk;
+        if (spill) {
+          if (lane == 0) nb = atomicAdd(a.cursor, kWarpChunk);
+          nb = __shfl_sync(0xffffffffu, nb, 0);
+        }
+        if (valid) {
+          const u64 pos = idx < kWarpChunk ? cbase + idx : nb + (idx - kWarpChunk);
+          ++produced;
+          if (pos < a.out.cap)
+            store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
+          else
+            full = true;
+        }
+        if (spill) {
+          cbase = nb;
+          cfill = cfill + tot - kWarpChunk;
+        } else {
+          cfill += tot;
+        }
+      } else if (valid) {
+        ++produced;
+        const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
+        if (r > 0) ++fresh;
+        if (r < 0) full = true;
+      }
+    }
+  }
+  if (MODE == 1 && cfill < kWarpChunk)  // the unused tail of the warp's last chunk: holes
+    for (u64 j = cfill + lane; j < kWarpChunk; j += 32)
+      if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
+  if (full) atomicOr(a.err, kErrOverflow);
+  for (int o = 16; o > 0; o >>= 1) {
+    produced += __shfl_down_sync(0xffffffffu, produced, o);
+    fresh += __shfl_down_sync(0xffffffffu, fresh, o);
+  }
+  if (lane == 0) {
+    if (a.valid && produced) atomicAdd(a.valid, produced);
+    if (MODE == 2 && fresh) atomicAdd(a.out.count, fresh);
+    if (a.cand && examined) atomicAdd(a.cand, examined);
   }
 }
 
@@ -611,6 +742,31 @@ int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int gro
     r = (int)cudaGetLastError();
   }
   return r;
+}
+
+__global__ void deg8_kernel(const int32_t *row_ptr, int32_t n, uint8_t *deg8) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int d = row_ptr[v + 1] - row_ptr[v];
+    deg8[v] = (uint8_t)(d < 255 ? d : 255);
+  }
+}
+
+int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
+                uint8_t *deg8) {
+  if (n > 0) deg8_kernel<<<d.sms * 4, 256, 0, s>>>(row_ptr, n, deg8);
+  return (int)cudaGetLastError();
+}
+
+int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a) {
+  const int grid = d.sms * d.blocks_per_sm;
+  if (kw == 1) {
+    if (mode == 1) intro_warp_kernel<u64, 1><<<grid, 256, 0, s>>>(a);
+    else intro_warp_kernel<u64, 2><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (mode == 1) intro_warp_kernel<u128, 1><<<grid, 256, 0, s>>>(a);
+    else intro_warp_kernel<u128, 2><<<grid, 256, 0, s>>>(a);
+  }
+  return (int)cudaGetLastError();
 }
 
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a) {
