@@ -219,6 +219,27 @@ int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_nod
 int cc_context_stats(cc_ctx *ctx, uint64_t *kernel_launches, uint64_t *arena_used,
                      uint64_t *arena_size);
 
+/* ---- a count that allocates no device memory (the paper has no counterpart) --------------- */
+/* Size of the fixed device array cc_count_noalloc works in. */
+#define CC_NOALLOC_BYTES (64ull << 20)
+
+/* For callers that cannot allocate device memory: code running while a stream is captured into a
+ * CUDA graph (an allocation would break the capture), processes whose device memory belongs to
+ * another allocator, and hot paths that must not pay an allocation's implicit synchronisation.
+ * Returns what cc_count and cc_decide return for graph (n, h_row_ptr, h_col), pattern (n_F, m_F,
+ * h_edges, td) and cc_color(seed, trials, k) under cc_default_opts, computing everything inside
+ * one CC_NOALLOC_BYTES device array that is part of the library image (every GPU that loads the
+ * library holds it until exit); the caller passes only host inputs and the host outputs
+ * h_counts[trials] and h_exists[trials].  The first call on a device looks up the array's device
+ * address, so make it before any stream capture.  Every call shares the array and leaves its
+ * contents behind (each call clears what it needs); calls whose work overlaps on one GPU race
+ * and must be serialised by the caller.  Errors: CC_ENOMEM when the graph, the colourings or the
+ * tables do not fit the array; otherwise those of the calls it stands for. */
+int cc_count_noalloc(int device, void *cuda_stream, int32_t n, const int32_t *h_row_ptr,
+                     const int32_t *h_col, int32_t n_F, int32_t m_F, const int32_t *h_edges,
+                     const cc_td *td, uint64_t seed, int32_t trials, int32_t k,
+                     uint64_t *h_counts, uint8_t *h_exists);
+
 /* ---- serving: a resident graph, queries admitted by table memory, batched as they arrive --- */
 /* Starts a server thread that owns device work for submitted queries; mem_budget bytes of the
  * arena may hold query tables at once (0 = half the free arena). */

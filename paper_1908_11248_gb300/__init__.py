@@ -30,7 +30,7 @@ EXPORTS = [
     "cc_release_colors", "cc_default_opts", "cc_run_dp", "cc_run_batch", "cc_decide", "cc_count",
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
-    "cc_nice_decomposition", "cc_check_graph",
+    "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc",
 ]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
                 "join_build", "join_count", "join_write", "root", "sort", "reduce"]
@@ -97,6 +97,8 @@ def lib():
         "cc_context_stats": ([P, P, P, P], ctypes.c_int),
         "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_check_graph": ([i32, P, P], ctypes.c_int),
+        "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
+                             ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -313,6 +315,23 @@ def cc_context_stats(ctx):
     _check(lib().cc_context_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "cc_context_stats")
     return int(a.value), int(b.value), int(c.value)
+
+
+def cc_count_noalloc(device: int, stream: int, row_ptr, col, nF: int, edges, td, seed: int,
+                     trials: int, k: int):
+    """Counts and exists flags computed in the library's fixed device array, allocating no device
+    memory (see include/cc.h)."""
+    rp, cl = _i32(row_ptr), _i32(col)
+    e = _i32(edges).reshape(-1)
+    tdp, keep = _td_struct(td)
+    counts = np.zeros(trials, np.uint64)
+    exists = np.zeros(trials, np.uint8)
+    _check(lib().cc_count_noalloc(device, stream or None, len(rp) - 1, _p(rp),
+                                  _p(cl) if len(cl) else None, nF, len(e) // 2,
+                                  _p(e) if len(e) else None, tdp, seed, trials, k, _p(counts),
+                                  _p(exists)), "cc_count_noalloc")
+    del keep
+    return counts, exists
 
 
 def cc_serve_start(ctx, mem_budget: int = 0, max_inflight: int = 8):
