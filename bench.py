@@ -111,7 +111,11 @@ def slot_bytes(b, k):
 
 
 def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
-    """Bytes a launch must move by the method's definition (not by this implementation)."""
+    """Bytes a launch must move by the method's definition (not by this implementation): an
+    introduce reads its child's entries, one adjacency word and one colour byte per candidate
+    examined, and writes its own entries; a forget reads its child's entries and writes its own
+    (merging them by sort + reduce, or by hashing, is implementation); a join reads both
+    children and writes its entries."""
     ty, c0, c1, u, bag = nodes[node]
     S = lambda x: slot_bytes(len(nodes[x][4]), k)  # noqa: E731
     if kind == "color":
@@ -120,13 +124,18 @@ def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
         return n * T * (1 + S(node))
     if kind in ("intro_count", "intro_write", "intro_fused"):
         b = int(sizes[c0]) * S(c0) + int(cand) * 5
-        if kind == "intro_write":
+        if kind != "intro_count":  # the introduce's own table, written once
             b += int(sizes[node]) * S(node)
-        if kind == "intro_fused":
-            parent = next(i for i, nd in enumerate(nodes) if nd[1] == node)
-            b += int(sizes[parent]) * S(parent)
         return b
-    if kind == "forget":
+    if kind in ("forget", "sort", "reduce"):
+        if ty != 2:
+            return 0
+        # the sort's share of the forget is its whole read of the child's entries; the
+        # reduce writes the merged entries
+        if kind == "sort":
+            return int(sizes[c0]) * S(c0)
+        if kind == "reduce":
+            return int(sizes[node]) * S(node)
         return int(sizes[c0]) * S(c0) + int(sizes[node]) * S(node)
     if kind.startswith("join"):
         b = (int(sizes[c0]) + int(sizes[c1])) * S(node)
@@ -136,6 +145,13 @@ def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
     if kind == "root":
         return int(sizes[node]) * S(node)
     return 0
+
+
+# kernel kinds grouped by the node rule they implement (Section 3.1)
+GROUPS = {"color": "colour", "leaf": "leaf", "intro_count": "introduce",
+          "intro_write": "introduce", "intro_fused": "introduce+forget", "forget": "forget",
+          "sort": "forget", "reduce": "forget", "join_build": "join", "join_count": "join",
+          "join_write": "join", "root": "root"}
 
 
 def run_reference(args, rank):
@@ -273,20 +289,29 @@ def main():
         entries_all = float(entries)
     value = entries_all / (total_ms / 1000.0)
 
-    # roofline of the dominant kernel (largest share of device time)
-    dom = max(kern, key=lambda x: kern[x]["ms"])
-    d = kern[dom]
+    # roofline of the dominant node rule (largest share of device time); sort passes and
+    # reduce-by-key are the forget's merge, so they carry the forget's algorithmic bytes
+    grp = {}
+    for kn, v in kern.items():
+        g2 = grp.setdefault(GROUPS.get(kn, kn), {"launches": 0, "ms": 0.0, "bytes": 0})
+        for f in ("launches", "ms", "bytes"):
+            g2[f] += v[f]
+    dom = max(grp, key=lambda x: grp[x]["ms"])
+    d = grp[dom]
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
     peak, peak_kind = peaks()
+    total_kms = sum(x["ms"] for x in kern.values())
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": TRAFFIC,
             "bytes_per_launch": d["bytes"] / d["launches"],
             "ms_per_launch": d["ms"] / d["launches"],
+            "groups": {g: {"ms_per_step": v["ms"] / args.steps, "share": v["ms"] / total_kms,
+                           "gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None}
+                       for g, v in sorted(grp.items(), key=lambda x: -x[1]["ms"])},
             "kernels": {kn: {"launches": v["launches"] // args.steps,
                              "ms_per_step": v["ms"] / args.steps,
-                             "share": v["ms"] / sum(x["ms"] for x in kern.values()),
-                             "gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None}
+                             "share": v["ms"] / total_kms}
                         for kn, v in sorted(kern.items(), key=lambda x: -x[1]["ms"])}}
 
     # end to end through the C ABI: graph from pinned host memory, counts back to the host
