@@ -761,10 +761,13 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.cursor = planned ? cursor + x : nullptr;
         a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
         if (planned) check(cursor + x, cap);
-        const bool warp = planned && a.nnb <= 1;  // lean warp kernel for expanding introduces
+        // planned runs: lean warp kernels (expanding, or grouped by bag-neighbour images)
+        const bool warp = planned && a.nnb <= 1, gwarp = planned && grouped;
         int r = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-          return warp ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 1, a)
-                      : cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a, blk);
+          return warp    ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 1, a)
+                 : gwarp ? cc::launch_intro_group_warp(c->stream, c->dev, R->kw, 1, a)
+                         : cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a,
+                                                blk);
         });
         if (R->opts.profile && !r) R->timings.back().candidates = cand;
         return r;
@@ -778,10 +781,12 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.q = pos_in(nd.bag, P.nodes[f].vertex);
         a.valid = R->d_counters + x;
         a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
-        const bool warp = planned && a.nnb <= 1;
+        const bool warp = planned && a.nnb <= 1, gwarp = planned && grouped;
         rc = timed(x, CC_K_INTRO_FUSED, 1, [&] {
-          return warp ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 2, a)
-                      : cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a, blk);
+          return warp    ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 2, a)
+                 : gwarp ? cc::launch_intro_group_warp(c->stream, c->dev, R->kw, 2, a)
+                         : cc::launch_intro_blk(c->stream, c->dev, R->kw, 2, grouped, block, a,
+                                                blk);
         });
         if (rc) return rc;
         if (R->opts.profile) R->timings.back().candidates = cand;

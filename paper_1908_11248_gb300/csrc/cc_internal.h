@@ -168,6 +168,10 @@ int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
 int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a);
 int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
                 uint8_t *deg8);
+// Grouped introduce (child sorted by bag-neighbour images), warp by warp, for planned runs;
+// modes as launch_intro_warp.
+int launch_intro_group_warp(cudaStream_t s, const DevInfo &d, int kw, int mode,
+                            const IntroArgs &a);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);
 int launch_join(cudaStream_t s, const DevInfo &d, int kw, int phase, int block,
                 const JoinArgs &a);  // phase 0 build, 1 count pairs, 2 write

@@ -408,7 +408,7 @@ __device__ __forceinline__ u128 shfl_key(u128 v, int src) {
 }
 
 template <typename K, int MODE>
-__global__ void __launch_bounds__(256) intro_warp_kernel(IntroArgs a) {
+__global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
   const int lane = threadIdx.x & 31;
@@ -507,6 +507,185 @@ __global__ void __launch_bounds__(256) intro_warp_kernel(IntroArgs a) {
     }
   }
   if (MODE == 1 && cfill < kWarpChunk)  // the unused tail of the warp's last chunk: holes
+    for (u64 j = cfill + lane; j < kWarpChunk; j += 32)
+      if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
+  if (full) atomicOr(a.err, kErrOverflow);
+  for (int o = 16; o > 0; o >>= 1) {
+    produced += __shfl_down_sync(0xffffffffu, produced, o);
+    fresh += __shfl_down_sync(0xffffffffu, fresh, o);
+  }
+  if (lane == 0) {
+    if (a.valid && produced) atomicAdd(a.valid, produced);
+    if (MODE == 2 && fresh) atomicAdd(a.out.count, fresh);
+    if (a.cand && examined) atomicAdd(a.cand, examined);
+  }
+}
+
+// ---- grouped introduce, warp by warp (planned capacities) -----------------------------------
+// The child is sorted by the images of u's bag neighbours.  Each warp takes a window of 32
+// consecutive entries; the first entry of every run of equal images in the window leads: the
+// warp walks the lead's anchor list 32 candidates at a time, keeps those adjacent to every bag
+// neighbour's image (and passing the degree filter) in a small per-warp buffer, and then every
+// entry of the run tests only its own colour set against that list.  A window whose lists do not
+// fit the buffer is processed entry by entry.
+constexpr int kGroupCap = 128;  // candidate-list buffer per warp
+
+template <typename K, int MODE>
+__device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey, u64 oc,
+                                          int lane, unsigned lt, u64 &cbase, u64 &cfill,
+                                          u64 &produced, u64 &fresh, bool &full) {
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  if (MODE == 1) {
+    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+    if (!bal) return;
+    const u64 tot = __popc(bal);
+    const u64 idx = cfill + __popc(bal & lt);
+    u64 nb = 0;
+    const bool spill = cfill + tot > kWarpChunk;
+    if (spill) {
+      if (lane == 0) nb = atomicAdd(a.cursor, kWarpChunk);
+      nb = __shfl_sync(0xffffffffu, nb, 0);
+    }
+    if (valid) {
+      const u64 pos = idx < kWarpChunk ? cbase + idx : nb + (idx - kWarpChunk);
+      ++produced;
+      if (pos < a.out.cap)
+        store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
+      else
+        full = true;
+    }
+    if (spill) {
+      cbase = nb;
+      cfill = cfill + tot - kWarpChunk;
+    } else {
+      cfill += tot;
+    }
+  } else if (valid) {
+    ++produced;
+    const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
+    if (r > 0) ++fresh;
+    if (r < 0) full = true;
+  }
+}
+
+template <typename K, int MODE>
+__global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
+  __shared__ int s_buf[8][kGroupCap];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int *buf = s_buf[wib];
+  const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
+  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + wib;
+  const u64 bound = table_bound<K>(a.in);
+  u64 cbase = 0, cfill = kWarpChunk;
+  u64 produced = 0, fresh = 0, examined = 0;
+  bool full = false;
+  for (u64 base = wid * 32; base < bound; base += warps * 32) {
+    const u64 i = base + lane;
+    K key = 0;
+    u64 c = 0;
+    if (i < bound) load_slot(in, i, key, c);
+    const u64 tup = key != 0 ? nb_tuple(key, a) : ~0ull;
+    const u64 up = __shfl_up_sync(0xffffffffu, tup, 1);
+    const bool lead = key != 0 && (lane == 0 || up != tup);
+    const unsigned leads = __ballot_sync(0xffffffffu, lead);
+    // candidate lists of the window's runs, one after the other in buf
+    int lstart = 0, llen = 0;  // held by lead lanes
+    int used = 0;              // warp-uniform
+    bool overflow = false;
+    for (unsigned rest = leads; rest; rest &= rest - 1) {
+      const int l = __ffs(rest) - 1;
+      const K lkey = shfl_key(key, l);
+      int best = INT_MAX, rs = 0, anc = 0;
+      for (int j = 0; j < a.nnb; ++j) {
+        const int w = key_slot(lkey, a.L, a.nb_slot[j]);
+        const int r0 = a.G.row_ptr[w], d = a.G.row_ptr[w + 1] - r0;
+        if (d < best) {
+          best = d;
+          rs = r0;
+          anc = j;
+        }
+      }
+      if (lane == 0) examined += (u64)best;
+      const int start = used;
+      for (int j0 = 0; j0 < best; j0 += 32) {
+        const int j = j0 + lane;
+        bool ok = false;
+        int v = 0;
+        if (j < best) {
+          v = __ldg(a.G.col + rs + j);
+          ok = a.degF == 0 || a.G.deg8[v] >= a.degF;
+          for (int q = 0; q < a.nnb && ok; ++q)
+            if (q != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[q]), v);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        const int pos = used + __popc(bal & lt);
+        if (ok && pos < kGroupCap) buf[pos] = v;
+        used += __popc(bal);
+      }
+      if (used > kGroupCap) overflow = true;
+      if (lane == l) {
+        lstart = start;
+        llen = used - start;
+      }
+    }
+    __syncwarp();
+    if (!overflow) {
+      // each entry takes the list of the last lead at or before it
+      const unsigned mine = leads & (lt | (1u << lane));
+      const int from = mine ? 31 - __clz(mine) : 0;
+      const int s0 = __shfl_sync(0xffffffffu, lstart, from);
+      const int n0 = key != 0 ? __shfl_sync(0xffffffffu, llen, from) : 0;
+      int nmax = n0;
+      for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+      const int t = key != 0 ? key_trial(key, a.L) : 0;
+      for (int r = 0; r < nmax; ++r) {
+        bool valid = false;
+        K okey = 0;
+        if (r < n0) {
+          const int v = buf[s0 + r];
+          const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+          valid = !((key_mask(key, a.L) >> cv) & 1u);
+          if (valid) okey = key_insert(key, a.L, a.p, v) | ((K)1 << cv);
+        }
+        warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
+      }
+    } else {  // entry by entry, every check in full
+      int best = INT_MAX, rs = 0, anc = 0;
+      if (key != 0)
+        for (int j = 0; j < a.nnb; ++j) {
+          const int w = key_slot(key, a.L, a.nb_slot[j]);
+          const int r0 = a.G.row_ptr[w], d = a.G.row_ptr[w + 1] - r0;
+          if (d < best) {
+            best = d;
+            rs = r0;
+            anc = j;
+          }
+        }
+      const int nc = key != 0 ? best : 0;
+      int nmax = nc;
+      for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+      const int t = key != 0 ? key_trial(key, a.L) : 0;
+      for (int j = 0; j < nmax; ++j) {
+        bool valid = false;
+        K okey = 0;
+        if (j < nc) {
+          const int v = __ldg(a.G.col + rs + j);
+          const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
+          valid = !((key_mask(key, a.L) >> cv) & 1u);
+          if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+          for (int q = 0; q < a.nnb && valid; ++q)
+            if (q != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[q]), v);
+          if (valid) okey = key_insert(key, a.L, a.p, v) | ((K)1 << cv);
+        }
+        warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
+      }
+    }
+    __syncwarp();  // buf is rewritten by the next window
+  }
+  if (MODE == 1 && cfill < kWarpChunk)
     for (u64 j = cfill + lane; j < kWarpChunk; j += 32)
       if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
   if (full) atomicOr(a.err, kErrOverflow);
@@ -754,6 +933,19 @@ __global__ void deg8_kernel(const int32_t *row_ptr, int32_t n, uint8_t *deg8) {
 int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
                 uint8_t *deg8) {
   if (n > 0) deg8_kernel<<<d.sms * 4, 256, 0, s>>>(row_ptr, n, deg8);
+  return (int)cudaGetLastError();
+}
+
+int launch_intro_group_warp(cudaStream_t s, const DevInfo &d, int kw, int mode,
+                            const IntroArgs &a) {
+  const int grid = d.sms * d.blocks_per_sm;
+  if (kw == 1) {
+    if (mode == 1) intro_group_warp_kernel<u64, 1><<<grid, 256, 0, s>>>(a);
+    else intro_group_warp_kernel<u64, 2><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (mode == 1) intro_group_warp_kernel<u128, 1><<<grid, 256, 0, s>>>(a);
+    else intro_group_warp_kernel<u128, 2><<<grid, 256, 0, s>>>(a);
+  }
   return (int)cudaGetLastError();
 }
 

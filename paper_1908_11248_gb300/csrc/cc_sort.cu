@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) sweep_bases_kernel(u64 *ghist) {
 // key (a full sort key is a bijection of the key): later passes read digits off it directly,
 // and reduce-by-key turns it back.
 template <typename K, typename SK, int BLOCK, int ITEMS, bool FROM_KEY, bool STORE_S>
-__global__ void __launch_bounds__(BLOCK) sweep_pass_kernel(SortSpec sp, const void *src,
+__global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const void *src,
                                                            const u64 *n_ptr, u64 n_cap, int shift,
                                                            u64 epoch, const u64 *bases,
                                                            u64 *status, unsigned *tile_ctr,
