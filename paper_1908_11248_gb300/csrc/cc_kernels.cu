@@ -636,15 +636,17 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       // each entry takes the list of the last lead at or before it
       const unsigned mine = leads & (lt | (1u << lane));
       const int from = mine ? 31 - __clz(mine) : 0;
+      // every lane takes part in both shuffles (a full-mask shuffle in a branch is undefined)
       const int s0 = __shfl_sync(0xffffffffu, lstart, from);
-      const int n0 = key != 0 ? __shfl_sync(0xffffffffu, llen, from) : 0;
+      const int n0all = __shfl_sync(0xffffffffu, llen, from);
+      const int n0 = key != 0 ? n0all : 0;
       int nmax = n0;
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
       const int t = key != 0 ? key_trial(key, a.L) : 0;
       for (int r = 0; r < nmax; ++r) {
         bool valid = false;
         K okey = 0;
-        if (r < n0) {
+        if (r < n0 && s0 + r < kGroupCap) {
           const int v = buf[s0 + r];
           const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
           valid = !((key_mask(key, a.L) >> cv) & 1u);

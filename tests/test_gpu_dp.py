@@ -344,3 +344,19 @@ def test_sort_variants_agree(ctx, sweep):
         assert np.array_equal(r["count"], ref.count)
         assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
         release(ctx, r)
+
+
+def test_planned_at_workload_scale(ctx):
+    """Planned runs on the workload's graph (hubs of degree ~500, long candidate lists, ragged
+    last windows), against the oracle on two trials."""
+    w = synth.WORKLOADS["ba20k_grid2x4"]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    z = oracle.colors(20000, 2, 8, seed=3)
+    ref = oracle.run_dp(g, pat, z, 8)
+    for fuse in (2, 1):
+        for _ in range(2):  # exact, then planned
+            r = gpu_dp(ctx, g, pat, colours=z, k=8, fuse=fuse)
+            assert np.array_equal(r["count"], ref.count)
+            assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+            release(ctx, r)
