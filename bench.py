@@ -198,6 +198,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trials", type=int, default=0,
+                    help="colouring trials per step (default: the workload's 64); smaller values "
+                         "only for small profiling captures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -224,7 +227,7 @@ def main():
     g = synth.make_graph(w["graph"])
     nF, edges, td = synth.make_pattern(w["pattern"])
     n = len(g[0]) - 1
-    T, k = w["trials"], w["k"]
+    T, k = args.trials or w["trials"], w["k"]
     seed = w["seed"] + 1000003 * rank
     ctx = cc.Context(arena_bytes=96 << 30, device=local)
     h = ctx.h
