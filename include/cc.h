@@ -158,10 +158,25 @@ void cc_default_opts(cc_run_opts *opts);
 int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run_opts *opts,
               int32_t *run_id);
 
-/* Runs several (pattern, colouring) DPs; their node steps are issued on forked streams and
- * replayed as one CUDA graph once their capacities are planned.  run_ids[npat] out. */
+/* Runs several (pattern, colouring) DPs with one set of options (the batched execution of
+ * Section 5's many queries over one graph).  With opts->use_graph, retain 0 and profile 0, once
+ * every request has been planned (an earlier run of the same pattern, graph content, trials,
+ * colours and options), the requests run as parallel branches of one captured CUDA graph, each
+ * in device memory reserved for the graph; the graph is kept per request list and replayed, its
+ * colours copied in first.  A request that outgrows the graph's capacities makes the library
+ * drop the graph and run every request again directly.  Otherwise the requests run one after the
+ * other on the context's stream.  h_run_ids[npat] out; on error no run is kept.  Errors as
+ * cc_run_dp. */
 int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *h_pattern_ids,
                  const int32_t *h_coloring_ids, const cc_run_opts *opts, int32_t *h_run_ids);
+
+/* How a run was executed. */
+#define CC_MODE_EXACT 0   /* count passes size every table exactly (first run of a plan key) */
+#define CC_MODE_PLANNED 1 /* capacities from the plan, appends in chunks, no host reads */
+#define CC_MODE_GRAPH 2   /* planned, replayed from a captured CUDA graph */
+
+/* *mode = one of CC_MODE_* for run `run_id`.  Errors: CC_EINVAL, CC_ENOTFOUND. */
+int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode);
 
 /* Per trial: 1 if a colourful copy of F exists (the root table is nonempty), else 0. */
 int cc_decide(cc_ctx *ctx, int32_t run_id, uint8_t *h_exists);

@@ -30,8 +30,9 @@ EXPORTS = [
     "cc_release_colors", "cc_default_opts", "cc_run_dp", "cc_run_batch", "cc_decide", "cc_count",
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
-    "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc",
+    "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
 ]
+RUN_MODES = ["exact", "planned", "graph"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
                 "join_build", "join_count", "join_write", "root", "sort", "reduce"]
 
@@ -97,6 +98,7 @@ def lib():
         "cc_context_stats": ([P, P, P, P], ctypes.c_int),
         "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_check_graph": ([i32, P, P], ctypes.c_int),
+        "cc_run_mode": ([P, i32, P], ctypes.c_int),
         "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
                              ctypes.c_int),
     }
@@ -308,6 +310,12 @@ def cc_run_timings(ctx, run: int, capacity: int = 4096):
                                 ctypes.byref(n)), "cc_run_timings")
     m = n.value
     return node[:m], kind[:m], ms[:m], cand[:m]
+
+
+def cc_run_mode(ctx, run: int) -> str:
+    m = ctypes.c_int32(0)
+    _check(lib().cc_run_mode(ctx, run, ctypes.byref(m)), "cc_run_mode")
+    return RUN_MODES[m.value]
 
 
 def cc_context_stats(ctx):

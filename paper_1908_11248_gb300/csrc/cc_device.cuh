@@ -112,12 +112,22 @@ __device__ __forceinline__ u64 table_bound(const TableDesc &t) {
 static __device__ __forceinline__ u64 home_slot(u64 h, u64 cap) { return __umul64hi(h, cap); }
 static __device__ __forceinline__ u64 next_slot(u64 h, u64 cap) { return h + 1 == cap ? 0 : h + 1; }
 
+// Longest probe sequence of an insert or a lookup.  An insert that finds no room within it
+// reports a full table (the caller flags an overflow), so every key that was inserted lies within
+// this many slots of its home and a lookup may stop there too.  A table at the largest load
+// factor (0.9) exceeds it by chance with negligible probability; a table that is really full
+// costs each thread at most this many probes instead of a sweep of the whole table.
+constexpr u64 kProbeLimit = 1ull << 15;
+static __device__ __forceinline__ u64 probe_limit(u64 cap) {
+  return cap < kProbeLimit ? cap : kProbeLimit;
+}
+
 // Adds count c to key's record.  Returns 1 if the key was new, 0 if it was present, -1 if the
-// table is full.  A new key and its count are installed by one 128-bit compare-and-swap of the
+// table is full (no room within the probe limit).  A new key and its count are installed by one 128-bit compare-and-swap of the
 // whole (key, count) record; later additions are 64-bit atomic adds on the count.
 static __device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 cap, u64 key, u64 c) {
   u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
+  for (u64 probe = 0, lim = probe_limit(cap); probe < lim; ++probe) {
     u64 cur = *reinterpret_cast<volatile u64 *>(&slots[h].key);  // 8-byte reads are atomic
     if (cur == key) {
       atomicAdd(&slots[h].cnt, c);
@@ -139,7 +149,7 @@ static __device__ __forceinline__ int hash_add(Slot<u64> *slots, u64 cap, u64 ke
 
 static __device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 cap, u128 key, u64 c) {
   u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
+  for (u64 probe = 0, lim = probe_limit(cap); probe < lim; ++probe) {
     // a 16-byte plain read is not guaranteed to be single-copy atomic: always compare-and-swap
     u128 old = atomicCAS(&slots[h].key, (u128)0, key);
     if (old == 0) {
@@ -155,11 +165,11 @@ static __device__ __forceinline__ int hash_add(Slot<u128> *slots, u64 cap, u128 
   return -1;
 }
 
-// find-or-insert; returns the slot index or -1 if the table is full
+// find-or-insert; returns the slot index or -1 if the table is full (within the probe limit)
 template <typename K>
 __device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 cap, K key) {
   u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
+  for (u64 probe = 0, lim = probe_limit(cap); probe < lim; ++probe) {
     K old = atomicCAS(&slots[h].key, (K)0, key);
     if (old == 0 || old == key) return (long long)h;
     h = next_slot(h, cap);
@@ -171,7 +181,7 @@ __device__ __forceinline__ long long hash_claim(Slot<K> *slots, u64 cap, K key) 
 template <typename K>
 __device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 cap, K key) {
   u64 h = home_slot(key_hash(key), cap);
-  for (u64 probe = 0; probe < cap; ++probe) {
+  for (u64 probe = 0, lim = probe_limit(cap); probe < lim; ++probe) {
     K cur;
     u64 c;
     load_slot(slots, h, cur, c);
@@ -180,6 +190,18 @@ __device__ __forceinline__ long long hash_find(const Slot<K> *slots, u64 cap, K 
     h = next_slot(h, cap);
   }
   return -1;
+}
+
+// An earlier step of the run raised an error word (a planned room ran out, a wait gave up): the
+// run is repeated or reported anyway, so the node kernels after it skip their work.  The block
+// form is uniform over the block (one barrier), the warp form over the warp (lane 0's read).
+__device__ __forceinline__ bool block_run_failed(const int *err) {
+  return __syncthreads_or(*reinterpret_cast<const volatile int *>(err) != 0) != 0;
+}
+__device__ __forceinline__ bool warp_run_failed(const int *err) {
+  int e = 0;
+  if ((threadIdx.x & 31) == 0) e = *reinterpret_cast<const volatile int *>(err);
+  return __shfl_sync(0xffffffffu, e, 0) != 0;
 }
 
 // ---- block reductions -------------------------------------------------------------------

@@ -37,6 +37,7 @@ class Arena {
     size_ = size;
     free_.clear();
     used_.clear();
+    inuse_ = hw_ = top_ = 0;
     if (size) free_[0] = size;
   }
   void *alloc(size_t bytes) {
@@ -48,6 +49,9 @@ class Arena {
       free_.erase(it);
       if (sz > bytes) free_[off + bytes] = sz - bytes;
       used_[off] = bytes;
+      inuse_ += bytes;
+      if (inuse_ > hw_) hw_ = inuse_;
+      if (off + bytes > top_) top_ = off + bytes;
       return base_ + off;
     }
     return nullptr;
@@ -59,6 +63,7 @@ class Arena {
     if (u == used_.end()) return;
     size_t sz = u->second;
     used_.erase(u);
+    inuse_ -= sz;
     auto nx = free_.lower_bound(off);
     if (nx != free_.end() && nx->first == off + sz) {
       sz += nx->second;
@@ -73,12 +78,32 @@ class Arena {
     }
     free_[off] = sz;
   }
+  // Gives back the tail of block p beyond its first `bytes` bytes.
+  void shrink(void *p, size_t bytes) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    const size_t off = (char *)p - base_;
+    auto u = used_.find(off);
+    if (u == used_.end() || u->second <= bytes) return;
+    const size_t tail = off + bytes, tail_sz = u->second - bytes;
+    u->second = bytes;
+    inuse_ -= tail_sz;
+    used_[tail] = tail_sz;  // released at once, so that it merges with its free neighbours
+    inuse_ += tail_sz;
+    release(base_ + tail);
+  }
+  // end offset of the highest block handed out since init
+  size_t top() const { return top_; }
   size_t free_bytes() const {
     size_t s = 0;
     for (auto &f : free_) s += f.second;
     return s;
   }
   size_t size() const { return size_; }
+  size_t in_use() const { return inuse_; }
+  size_t high_water() const { return hw_; }
+  void reset_high_water() { hw_ = inuse_; }
   size_t largest_free() const {
     size_t s = 0;
     for (auto &f : free_) s = std::max(s, f.second);
@@ -87,7 +112,7 @@ class Arena {
 
  private:
   char *base_ = nullptr;
-  size_t size_ = 0;
+  size_t size_ = 0, inuse_ = 0, hw_ = 0, top_ = 0;
   std::map<size_t, size_t> free_, used_;
 };
 
@@ -134,6 +159,7 @@ struct NodeTable {
 // largest table sizes and join pair counts seen, per node.
 struct Plan {
   std::vector<u64> entries, pairs;
+  size_t peak_bytes = 0;  // largest arena use of a run beyond what it started with
   int runs = 0;
 };
 
@@ -159,6 +185,27 @@ struct Run {
   std::vector<std::pair<const u64 *, u64>> checks;  // planned runs: device word <= capacity
   bool retained = false;
   bool planned = false;
+  bool graphed = false;
+  u64 *d_blk = nullptr;  // per-run scratch: block counts and bases, pair counters
+  int *d_err = nullptr;  // per-run device error word
+  Arena *home = nullptr;  // the arena its memory came from (null: the context's)
+};
+
+// A captured CUDA graph of planned runs (one member per run; members are parallel branches).
+// Each member owns a sub-arena reserved from the context arena for the graph's lifetime, the
+// colouring buffer the graph reads, and a shadow run whose device words the graph writes.
+struct GraphMember {
+  void *block = nullptr;
+  size_t bytes = 0;
+  Arena sub;
+  uint8_t *colours = nullptr;
+  std::unique_ptr<Run> shadow;
+};
+
+struct GraphSet {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<GraphMember> members;
+  u64 kernels = 0;  // kernel launches per replay
 };
 
 struct Ctx {
@@ -166,6 +213,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   DevInfo dev;
   Arena arena;
+  Arena *active = nullptr;  // where run allocations go: the arena, or a captured graph's own
   char *owned_arena = nullptr;
   // graph
   int32_t n = -1;
@@ -174,8 +222,14 @@ struct Ctx {
   std::vector<int32_t> h_row_ptr, h_col;
   int *d_err = nullptr;
   u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
-  int graph_version = 0;
+  // content fingerprint of the loaded graph: plans stay valid while the graph's content is the
+  // same, so reloading an identical graph keeps them
+  long long graph_fp = 0;
   std::map<std::vector<long long>, Plan> plans;
+  std::map<std::vector<long long>, std::unique_ptr<GraphSet>> graphs;
+  std::vector<cudaStream_t> branches;  // streams of captured batch branches
+  cudaStream_t capture = nullptr;      // where graphs are captured (the context's stream may be
+                                       // the legacy default stream, which cannot be captured)
   u64 *d_scratch = nullptr;  // small per-call scratch (block counts, pair counter)
   size_t scratch_words = 0;
   std::map<int32_t, Pattern> patterns;
@@ -491,23 +545,30 @@ void td_from_order(std::vector<uint32_t> adj, int n, const std::vector<int> &ord
 }
 
 // ---- helpers ------------------------------------------------------------------------------
+Arena &active_arena(Ctx *c) { return c->active ? *c->active : c->arena; }
+
 template <typename T>
 T *arena_alloc(Ctx *c, size_t count) {
-  return (T *)c->arena.alloc(count * sizeof(T));
+  return (T *)active_arena(c).alloc(count * sizeof(T));
 }
 
 void free_run(Ctx *c, Run *r) {
+  Arena &H = r->home ? *r->home : c->arena;
   for (auto &t : r->timings) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);
   }
   r->timings.clear();
   for (auto &t : r->tables)
-    if (t.slots) c->arena.release(t.slots);
+    if (t.slots) H.release(t.slots);
   r->tables.clear();
-  c->arena.release(r->d_counters);
-  c->arena.release(r->d_exists);
-  c->arena.release(r->d_count);
+  H.release(r->d_counters);
+  H.release(r->d_exists);
+  H.release(r->d_count);
+  H.release(r->d_blk);
+  H.release(r->d_err);
+  r->d_blk = nullptr;
+  r->d_err = nullptr;
   auto it = c->colorings.find(r->coloring);
   if (it != c->colorings.end() && --it->second.refs == 0) {
     c->arena.release(it->second.d_colors);
@@ -559,12 +620,16 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   R->checks.clear();
   std::vector<bool> made(N, false);
   const int grid = cc::intro_grid(c->dev, block);
-  int rc = ensure_scratch(c, 2 * (size_t)std::max(grid, cc::sort_grid(c->dev)) + 8);
-  if (rc) return rc;
-  u64 *blk = c->d_scratch;
+  Arena &A = active_arena(c);
+  // per-run scratch (a captured graph's branches must not share it)
+  if (!R->d_blk) R->d_blk = arena_alloc<u64>(c, 2 * (size_t)std::max(grid, cc::sort_grid(c->dev)) + 8);
+  if (!R->d_err) R->d_err = arena_alloc<int>(c, 1);
+  if (!R->d_blk || !R->d_err) return CC_ENOMEM;
+  int rc = CC_OK;
+  u64 *blk = R->d_blk;
   u64 *cursor = R->d_counters + N;      // per node: chunked-append cursor (scan bound)
   u64 *pairs_dev = R->d_counters + 2 * N;  // per join: matching colour-set pairs
-  CUDA_OK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CUDA_OK(cudaMemsetAsync(R->d_err, 0, sizeof(int), c->stream));
   const size_t rb = cc::slot_bytes(R->kw);
   // planned room for a quantity last seen at v (plus slack for chunked appends)
   const u64 chunk_slack = (u64)grid * 2048;
@@ -589,7 +654,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   };
   auto release_child = [&](int y) {
     if (R->opts.retain || y < 0) return;
-    c->arena.release(R->tables[y].slots);
+    A.release(R->tables[y].slots);
     R->tables[y] = {};
   };
   auto desc = [&](int x) {
@@ -604,7 +669,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   auto entries = [&](int x) { return planned ? room(plan->entries[x]) : R->sizes[x]; };
   auto new_hash = [&](int x, u64 keys) -> int {
     u64 cap = hash_cap(keys, lf);
-    void *p = c->arena.alloc(cap * rb);
+    void *p = A.alloc(cap * rb);
     if (!p) return CC_ENOMEM;
     CUDA_OK(cudaMemsetAsync(p, 0, cap * rb, c->stream));
     R->tables[x] = {p, cap, 1, true};
@@ -647,8 +712,8 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   // at most cap) into a new buffer *out of cap records
   auto sort_records = [&](int node, const cc::SortSpec &sp, const void *src, const u64 *n_src,
                           u64 src_cap, const u64 *nn, u64 cap, void **out) -> int {
-    void *ba = c->arena.alloc(std::max<u64>(1, cap) * rb);
-    void *bb = c->arena.alloc(std::max<u64>(1, cap) * rb);
+    void *ba = A.alloc(std::max<u64>(1, cap) * rb);
+    void *bb = A.alloc(std::max<u64>(1, cap) * rb);
     u64 *hist = arena_alloc<u64>(c, 256 * (size_t)cc::sort_grid(c->dev) + 512);
     // one-sweep scratch: tiles of the largest pass input (the scanned source or the buffers)
     cc::SweepScratch sw{};
@@ -656,14 +721,14 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     sw.ghist = arena_alloc<u64>(c, 256 * 16);
     sw.tile_ctr = arena_alloc<unsigned>(c, 16);
     sw.status = arena_alloc<u64>(c, 256 * sw.max_tiles);
-    sw.err = c->d_err;
+    sw.err = R->d_err;
     if (!ba || !bb || !hist || !sw.ghist || !sw.tile_ctr || !sw.status) {
-      c->arena.release(ba);
-      c->arena.release(bb);
-      c->arena.release(hist);
-      c->arena.release(sw.ghist);
-      c->arena.release(sw.tile_ctr);
-      c->arena.release(sw.status);
+      A.release(ba);
+      A.release(bb);
+      A.release(hist);
+      A.release(sw.ghist);
+      A.release(sw.tile_ctr);
+      A.release(sw.status);
       return CC_ENOMEM;
     }
     int which = 0;
@@ -672,11 +737,11 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       return cc::launch_sort_records(c->stream, c->dev, R->kw, sp, src, n_src, src_cap, nn, cap,
                                      ba, bb, hist, &which, sweep ? &sw : nullptr);
     });
-    c->arena.release(hist);
-    c->arena.release(sw.ghist);
-    c->arena.release(sw.tile_ctr);
-    c->arena.release(sw.status);
-    c->arena.release(which ? ba : bb);
+    A.release(hist);
+    A.release(sw.ghist);
+    A.release(sw.tile_ctr);
+    A.release(sw.status);
+    A.release(which ? ba : bb);
     *out = which ? bb : ba;
     return r;
   };
@@ -690,10 +755,10 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     const NiceNode &nd = P.nodes[x];
     if (nd.type == 0) {  // leaf
       u64 cap = std::max<u64>(1, (u64)n * (u64)R->trials);
-      void *p = c->arena.alloc(cap * rb);
+      void *p = A.alloc(cap * rb);
       if (!p) return CC_ENOMEM;
       R->tables[x] = {p, cap, 1, true};
-      cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), c->d_err};
+      cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), R->d_err};
       if (n == 0) CUDA_OK(cudaMemsetAsync(p, 0, rb, c->stream));
       rc = timed(x, CC_K_LEAF, 1, [&] { return cc::launch_leaf(c->stream, c->dev, R->kw, a); });
       if (rc) return rc;
@@ -710,7 +775,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
       a.degF = df ? P.deg[nd.vertex] : 0;
-      a.err = c->d_err;
+      a.err = R->d_err;
       a.cand = R->d_counters + 3 * N + x;  // candidates examined (count pass, or planned)
       a.proj_q = -1;
       a.q = -1;
@@ -735,10 +800,10 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.in = TableDesc{sorted, std::max<u64>(1, m), R->d_counters + y, 0};
       }
       struct SortedGuard {
-        Ctx *c;
+        Arena &a;
         void *p;
-        ~SortedGuard() { c->arena.release(p); }
-      } sorted_guard{c, sorted};
+        ~SortedGuard() { a.release(p); }
+      } sorted_guard{A, sorted};
       u64 total = 0, cand = 0;
       if (!planned) {
         rc = timed(x, CC_K_INTRO_COUNT, 2, [&] {
@@ -800,7 +865,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         continue;
       }
       if (fuse == 2) {  // write projected entries densely, sort them, reduce equal keys
-        void *buf = c->arena.alloc(raw * rb);
+        void *buf = A.alloc(raw * rb);
         if (!buf) return CC_ENOMEM;
         rc = write_dense(buf, raw, pos_in(nd.bag, P.nodes[f].vertex));
         if (!rc) release_child(y);
@@ -809,18 +874,18 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         // scan bound of the written buffer: its cursor when appended in chunks
         const u64 *bound = planned ? cursor + x : R->d_counters + x;
         if (!rc) rc = sort_records(f, sp, buf, bound, raw, R->d_counters + x, raw, &srt);
-        c->arena.release(buf);
+        A.release(buf);
         if (rc) return rc;
-        void *out = c->arena.alloc(raw * rb);
+        void *out = A.alloc(raw * rb);
         if (!out) {
-          c->arena.release(srt);
+          A.release(srt);
           return CC_ENOMEM;
         }
         rc = timed(f, CC_K_REDUCE, 3, [&] {
-          return cc::launch_reduce(c->stream, c->dev, R->kw, srt, R->d_counters + x, blk, out,
+          return cc::launch_reduce(c->stream, c->dev, R->kw, srt, R->d_counters + x, raw, blk, out,
                                    R->d_counters + f, R->opts.sort_sweep ? &sp : nullptr);
         });
-        c->arena.release(srt);
+        A.release(srt);
         if (rc) return rc;
         R->tables[f] = {out, raw, 0, true};
         R->tables[f].sort_n = sp.b;
@@ -833,7 +898,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         if (f == N - 1) break;
         continue;
       }
-      void *p = c->arena.alloc(raw * rb);
+      void *p = A.alloc(raw * rb);
       if (!p) return CC_ENOMEM;
       rc = write_dense(p, raw, -1);
       if (rc) return rc;
@@ -846,7 +911,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       rc = new_hash(x, entries(y));
       if (rc) return rc;
       cc::ForgetArgs a{R->L, desc(y), (int)P.nodes[y].bag.size(),
-                       pos_in(P.nodes[y].bag, nd.vertex), desc(x), c->d_err};
+                       pos_in(P.nodes[y].bag, nd.vertex), desc(x), R->d_err};
       rc = timed(x, CC_K_FORGET, 1,
                  [&] { return cc::launch_forget(c->stream, c->dev, R->kw, block, a); });
       if (rc) return rc;
@@ -856,11 +921,11 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       if (entries(y) > entries(z)) std::swap(y, z);  // chain the smaller child
       u64 icap = hash_cap(entries(y), lf);
       u64 bound_y = R->tables[y].hashed || planned ? R->tables[y].cap : R->sizes[y];
-      void *index = c->arena.alloc(icap * cc::index_slot_bytes(R->kw));
+      void *index = A.alloc(icap * cc::index_slot_bytes(R->kw));
       u64 *next = arena_alloc<u64>(c, std::max<u64>(1, bound_y));
       if (!index || !next) {
-        c->arena.release(index);
-        c->arena.release(next);
+        A.release(index);
+        A.release(next);
         return CC_ENOMEM;
       }
       CUDA_OK(cudaMemsetAsync(index, 0, icap * cc::index_slot_bytes(R->kw), c->stream));
@@ -875,7 +940,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       a.index_cap = icap;
       a.next = next;
       a.pairs = pairs;
-      a.err = c->d_err;
+      a.err = R->d_err;
       rc = timed(x, CC_K_JOIN_BUILD, 1,
                  [&] { return cc::launch_join(c->stream, c->dev, R->kw, 0, block, a); });
       u64 np = 0;
@@ -892,8 +957,8 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         rc = timed(x, CC_K_JOIN_WRITE, 1,
                    [&] { return cc::launch_join(c->stream, c->dev, R->kw, 2, block, a); });
       }
-      c->arena.release(index);
-      c->arena.release(next);
+      A.release(index);
+      A.release(next);
       if (rc) return rc;
       release_child(y);
       release_child(z);
@@ -906,8 +971,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   // root test (Section 3.1): per trial, nonempty root table and the sum of its counts
   cc::RootArgs ra{R->L, desc(N - 1), R->d_exists, R->d_count};
   rc = timed(N - 1, CC_K_ROOT, 1, [&] { return cc::launch_root(c->stream, c->dev, R->kw, ra); });
-  if (rc) return rc;
-  return finish_run(c, R);
+  return rc;
 }
 
 // reads the error word and, for planned runs, the sizes and capacity checks
@@ -915,7 +979,7 @@ int finish_run(Ctx *c, Run *R) {
   const int N = (int)R->sizes.size();
   int herr = 0;
   std::vector<u64> words(4 * (size_t)N);
-  CUDA_OK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaMemcpyAsync(&herr, R->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaMemcpyAsync(words.data(), R->d_counters, words.size() * sizeof(u64),
                           cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaStreamSynchronize(c->stream));
@@ -1133,14 +1197,34 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
   return rc;
 }
 
-int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **out) {
+// 64-bit fingerprint of a CSR graph (splitmix64 finaliser over its words); never 0.
+long long csr_fingerprint(int32_t n, const int32_t *row_ptr, const int32_t *col) {
+  auto mix = [](u64 z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  };
+  u64 h = mix((u64)n + 0x9e3779b97f4a7c15ull);
+  for (int32_t i = 0; i <= n; ++i) h = mix(h ^ (u64)(uint32_t)row_ptr[i]);
+  const int64_t m2 = row_ptr[n];
+  int64_t e = 0;
+  for (; e + 1 < m2; e += 2)
+    h = mix(h ^ ((u64)(uint32_t)col[e] | (u64)(uint32_t)col[e + 1] << 32));
+  if (e < m2) h = mix(h ^ (u64)(uint32_t)col[e]);
+  return (long long)(h | 1);
+}
+
+// Validates a (pattern, colouring, options) request and sets up its run: key layout, device
+// words, and the plan key of its capacities.
+int prepare_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts,
+                std::unique_ptr<Run> &R, std::vector<long long> &key) {
   auto pi = c->patterns.find(pid);
   auto ci = c->colorings.find(cid);
   if (pi == c->patterns.end() || ci == c->colorings.end()) return CC_ENOTFOUND;
   const Pattern &P = pi->second;
   cc::Coloring &col = ci->second;
   if (col.k < P.nF) return CC_EINVAL;
-  std::unique_ptr<Run> R(new Run());
+  R.reset(new Run());
   cc_default_opts(&R->opts);
   if (opts) R->opts = *opts;
   if (!(R->opts.load_factor > 0.f && R->opts.load_factor <= 0.9f)) R->opts.load_factor = 0.5f;
@@ -1164,55 +1248,340 @@ int make_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts, Run **ou
   R->d_counters = arena_alloc<u64>(c, 4 * (size_t)N);
   R->d_exists = arena_alloc<unsigned>(c, col.trials);
   R->d_count = arena_alloc<u64>(c, col.trials);
-  if (!R->d_counters || !R->d_exists || !R->d_count) {
+  R->d_err = arena_alloc<int>(c, 1);
+  if (!R->d_counters || !R->d_exists || !R->d_count || !R->d_err) {
     free_run(c, R.get());
     return CC_ENOMEM;
   }
   R->retained = R->opts.retain != 0;
-  const std::vector<long long> key = {pid, c->graph_version, col.trials, col.k,
-                                      R->opts.degree_filter, R->opts.fuse, R->opts.group,
-                                      R->opts.block, (long long)(R->opts.load_factor * 1000),
-                                      R->opts.sort_sweep};
-  auto reset = [&]() -> int {
-    for (auto &t : R->tables)
-      if (t.slots) c->arena.release(t.slots);
-    R->tables.clear();
-    for (auto &t : R->timings) {
-      cudaEventDestroy(t.start);
-      cudaEventDestroy(t.stop);
-    }
-    R->timings.clear();
-    CUDA_OK(cudaMemsetAsync(R->d_counters, 0, 4 * (size_t)N * sizeof(u64), c->stream));
-    CUDA_OK(cudaMemsetAsync(R->d_exists, 0, col.trials * sizeof(unsigned), c->stream));
-    CUDA_OK(cudaMemsetAsync(R->d_count, 0, col.trials * sizeof(u64), c->stream));
-    return CC_OK;
-  };
-  int rc = reset();
-  auto pl = c->plans.find(key);
-  R->planned = pl != c->plans.end() && pl->second.runs > 0;
-  if (!rc && R->planned) {
-    rc = run_nodes(c, R.get(), P, col, &pl->second);
-    if (rc == CC_ECAPACITY || rc == CC_ENOMEM) {  // outgrew the plan: plan again, exactly
-      R->planned = false;
-      rc = reset();
-      if (!rc) rc = run_nodes(c, R.get(), P, col, nullptr);
-    }
-  } else if (!rc) {
-    rc = run_nodes(c, R.get(), P, col, nullptr);
+  key = {pid, c->graph_fp, col.trials, col.k, R->opts.degree_filter, R->opts.fuse,
+         R->opts.group, R->opts.block, (long long)(R->opts.load_factor * 1000),
+         R->opts.sort_sweep};
+  return CC_OK;
+}
+
+// Frees a run's tables and timings and zeroes its device words, ready for a (re)run.
+int reset_run(Ctx *c, Run *R, int N) {
+  Arena &H = R->home ? *R->home : c->arena;
+  for (auto &t : R->tables)
+    if (t.slots) H.release(t.slots);
+  R->tables.clear();
+  for (auto &t : R->timings) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
   }
-  if (rc) {
-    free_run(c, R.get());
-    return rc;
-  }
+  R->timings.clear();
+  CUDA_OK(cudaMemsetAsync(R->d_counters, 0, 4 * (size_t)N * sizeof(u64), c->stream));
+  CUDA_OK(cudaMemsetAsync(R->d_exists, 0, R->trials * sizeof(unsigned), c->stream));
+  CUDA_OK(cudaMemsetAsync(R->d_count, 0, R->trials * sizeof(u64), c->stream));
+  return CC_OK;
+}
+
+// Folds a finished run's sizes into the plan of its key.
+void update_plan(Ctx *c, const std::vector<long long> &key, const Run *R, size_t peak) {
   cc::Plan &plan = c->plans[key];
+  const size_t N = R->sizes.size();
   plan.entries.resize(N, 0);
   plan.pairs.resize(N, 0);
-  for (int x = 0; x < N; ++x) {
+  for (size_t x = 0; x < N; ++x) {
     plan.entries[x] = std::max(plan.entries[x], R->sizes[x]);
     plan.pairs[x] = std::max(plan.pairs[x], R->pairs[x]);
   }
+  plan.peak_bytes = std::max(plan.peak_bytes, peak);
   plan.runs++;
-  *out = R.release();
+}
+
+// Runs the nodes on the context's stream: planned when a plan exists (repeated exactly if the
+// plan proves too small), exact otherwise; then reads the results and updates the plan.
+int run_direct(Ctx *c, Run *R, const std::vector<long long> &key) {
+  const Pattern &P = c->patterns.at(R->pattern);
+  const cc::Coloring &col = c->colorings.at(R->coloring);
+  const int N = (int)P.nodes.size();
+  int rc = reset_run(c, R, N);
+  if (rc) return rc;
+  auto pl = c->plans.find(key);
+  R->planned = pl != c->plans.end() && pl->second.runs > 0;
+  R->graphed = false;
+  const size_t base = c->arena.in_use();
+  c->arena.reset_high_water();
+  if (R->planned) {
+    rc = run_nodes(c, R, P, col, &pl->second);
+    if (!rc) rc = finish_run(c, R);
+    if (rc == CC_ECAPACITY || rc == CC_ENOMEM) {  // outgrew the plan: plan again, exactly
+      R->planned = false;
+      rc = reset_run(c, R, N);
+      c->arena.reset_high_water();
+      if (!rc) rc = run_nodes(c, R, P, col, nullptr);
+      if (!rc) rc = finish_run(c, R);
+    }
+  } else {
+    rc = run_nodes(c, R, P, col, nullptr);
+    if (!rc) rc = finish_run(c, R);
+  }
+  if (rc) return rc;
+  update_plan(c, key, R, c->arena.high_water() - base);
+  return CC_OK;
+}
+
+void drop_graph(Ctx *c, const std::vector<long long> &gkey) {
+  auto it = c->graphs.find(gkey);
+  if (it == c->graphs.end()) return;
+  cudaStreamSynchronize(c->stream);
+  if (it->second->exec) cudaGraphExecDestroy(it->second->exec);
+  for (auto &m : it->second->members) c->arena.release(m.block);
+  c->graphs.erase(it);
+}
+
+void drop_all_graphs(Ctx *c) {
+  while (!c->graphs.empty()) {
+    std::vector<long long> k = c->graphs.begin()->first;
+    drop_graph(c, k);
+  }
+}
+
+// Graph replay is taken for runs that keep no tables and time nothing, once every member has
+// a plan.
+bool graph_eligible(Ctx *c, const std::vector<Run *> &Rs,
+                    const std::vector<std::vector<long long>> &keys) {
+  if (Rs.empty() || Rs.size() > 64) return false;
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    const Run *R = Rs[m];
+    if (!R->opts.use_graph || R->opts.retain || R->opts.profile) return false;
+    auto pl = c->plans.find(keys[m]);
+    if (pl == c->plans.end() || pl->second.runs == 0) return false;
+  }
+  return true;
+}
+
+// Captures the planned runs of Rs as one CUDA graph: member m runs on branch stream m (on the
+// capture stream when there is one member) inside a sub-arena of its own, reading its colours
+// from a buffer of the graph and writing the device words of a shadow run.  The sub-arenas stay
+// reserved while the graph lives.
+int capture_graph(Ctx *c, const std::vector<Run *> &Rs,
+                  const std::vector<std::vector<long long>> &keys, std::unique_ptr<cc::GraphSet> &out) {
+  const size_t M = Rs.size();
+  std::unique_ptr<cc::GraphSet> gs(new cc::GraphSet());
+  gs->members.resize(M);
+  auto give_back = [&]() {
+    for (auto &gm : gs->members) c->arena.release(gm.block);
+  };
+  while (M > 1 && c->branches.size() < M) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return CC_ECUDA;
+    c->branches.push_back(s);
+  }
+  if (!c->capture && cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    c->capture = nullptr;
+    return CC_ECUDA;
+  }
+  std::vector<cudaEvent_t> ev(M + 1, nullptr);
+  bool events_ok = true;
+  for (auto &e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      e = nullptr;
+      events_ok = false;
+    }
+  auto drop_events = [&]() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  if (!events_ok) {
+    drop_events();
+    return CC_ECUDA;
+  }
+  // nothing runs while capturing; replays are launched on the context's stream
+  cudaStream_t origin = c->stream, main = c->capture;
+  if (cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    drop_events();
+    return CC_ECUDA;
+  }
+  const u64 launches0 = c->launches;
+  int rc = CC_OK;
+  if (M > 1) {
+    if (cudaEventRecord(ev[M], main) != cudaSuccess) rc = CC_ECUDA;
+    for (size_t m = 0; m < M && !rc; ++m)
+      if (cudaStreamWaitEvent(c->branches[m], ev[M], 0) != cudaSuccess) rc = CC_ECUDA;
+  }
+  for (size_t m = 0; m < M && !rc; ++m) {
+    // member m takes the largest free range while it is captured and keeps what it touched
+    const Run *R = Rs[m];
+    const Pattern &P = c->patterns.at(R->pattern);
+    const size_t N = P.nodes.size();
+    cc::GraphMember &gm = gs->members[m];
+    gm.bytes = c->arena.largest_free();
+    gm.block = c->arena.alloc(gm.bytes);
+    if (!gm.block) {
+      rc = CC_ENOMEM;
+      break;
+    }
+    gm.sub.init((char *)gm.block, gm.bytes);
+    gm.colours = (uint8_t *)gm.sub.alloc((size_t)R->trials * (size_t)c->n);
+    Run *S = new Run();
+    gm.shadow.reset(S);
+    S->pattern = R->pattern;
+    S->opts = R->opts;
+    S->L = R->L;
+    S->kw = R->kw;
+    S->trials = R->trials;
+    S->home = &gm.sub;
+    S->planned = true;
+    S->d_counters = (u64 *)gm.sub.alloc(4 * N * sizeof(u64));
+    S->d_exists = (unsigned *)gm.sub.alloc(R->trials * sizeof(unsigned));
+    S->d_count = (u64 *)gm.sub.alloc(R->trials * sizeof(u64));
+    S->d_err = (int *)gm.sub.alloc(sizeof(int));
+    if (!gm.colours || !S->d_counters || !S->d_exists || !S->d_count || !S->d_err) {
+      rc = CC_ENOMEM;
+      break;
+    }
+    cc::Coloring view;
+    view.trials = S->trials;
+    view.k = S->L.k;
+    view.d_colors = gm.colours;
+    c->stream = M > 1 ? c->branches[m] : main;
+    c->active = &gm.sub;
+    rc = reset_run(c, S, (int)N);
+    if (!rc) rc = run_nodes(c, S, P, view, &c->plans.at(keys[m]));
+    c->stream = origin;
+    c->active = nullptr;
+    gm.bytes = gm.sub.top();
+    c->arena.shrink(gm.block, gm.bytes);
+  }
+  // every forked branch joins the capture stream again, also after a failed step, so that the
+  // capture ends cleanly
+  if (M > 1)
+    for (size_t m = 0; m < M; ++m)
+      if (cudaEventRecord(ev[m], c->branches[m]) != cudaSuccess ||
+          cudaStreamWaitEvent(main, ev[m], 0) != cudaSuccess)
+        rc = rc ? rc : CC_ECUDA;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(main, &g);
+  if (!rc && ee != cudaSuccess) rc = CC_ECUDA;
+  if (!rc && cudaGraphInstantiate(&gs->exec, g, 0) != cudaSuccess) {
+    gs->exec = nullptr;
+    rc = CC_ECUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  drop_events();
+  gs->kernels = c->launches - launches0;
+  c->launches = launches0;  // nothing ran yet: replays count them
+  if (rc) {
+    cudaGetLastError();  // clear the error a failed capture leaves behind
+    give_back();
+    return rc;
+  }
+  out = std::move(gs);
+  return CC_OK;
+}
+
+// Replays a captured graph for runs Rs: copies each member's colours into the graph's buffer,
+// launches the graph on the context's stream, reads each shadow run's words and hands the
+// per-trial results and table sizes to the caller's run.
+int replay_graph(Ctx *c, cc::GraphSet &gs, const std::vector<Run *> &Rs) {
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    const cc::Coloring &col = c->colorings.at(Rs[m]->coloring);
+    CUDA_OK(cudaMemcpyAsync(gs.members[m].colours, col.d_colors,
+                            (size_t)col.trials * (size_t)c->n, cudaMemcpyDeviceToDevice,
+                            c->stream));
+  }
+  CUDA_OK(cudaGraphLaunch(gs.exec, c->stream));
+  c->launches += gs.kernels;
+  int worst = CC_OK;
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    Run *S = gs.members[m].shadow.get();
+    Run *R = Rs[m];
+    int rc = finish_run(c, S);
+    if (rc) {
+      worst = worst ? worst : rc;
+      continue;
+    }
+    CUDA_OK(cudaMemcpyAsync(R->d_exists, S->d_exists, R->trials * sizeof(unsigned),
+                            cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OK(cudaMemcpyAsync(R->d_count, S->d_count, R->trials * sizeof(u64),
+                            cudaMemcpyDeviceToDevice, c->stream));
+    R->sizes = S->sizes;
+    R->pairs = S->pairs;
+    R->planned = true;
+    R->graphed = true;
+    R->tables.assign(S->sizes.size(), {});
+  }
+  return worst;
+}
+
+// Runs Rs (prepared, with plan keys `keys`) from a captured graph, capturing it on first use.
+// A member that outgrew the graph's capacities makes the graph stale: it is dropped and every
+// member runs again directly (planned, then exactly if need be), which also updates the plans.
+int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
+                const std::vector<std::vector<long long>> &keys) {
+  std::vector<long long> gkey;
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    gkey.insert(gkey.end(), keys[m].begin(), keys[m].end());
+    gkey.push_back(-1);
+  }
+  auto it = c->graphs.find(gkey);
+  if (it == c->graphs.end()) {
+    std::unique_ptr<cc::GraphSet> gs;
+    int rc = capture_graph(c, Rs, keys, gs);
+    if (rc == CC_ENOMEM && !c->graphs.empty()) {
+      drop_all_graphs(c);
+      rc = capture_graph(c, Rs, keys, gs);
+    }
+    if (rc) {  // no graph: run them one by one
+      for (size_t m = 0; m < Rs.size(); ++m) {
+        rc = run_direct(c, Rs[m], keys[m]);
+        if (rc) return rc;
+      }
+      return CC_OK;
+    }
+    it = c->graphs.emplace(gkey, std::move(gs)).first;
+  }
+  int rc = replay_graph(c, *it->second, Rs);
+  if (rc == CC_OK) {
+    for (size_t m = 0; m < Rs.size(); ++m) update_plan(c, keys[m], Rs[m], 0);
+    return CC_OK;
+  }
+  drop_graph(c, gkey);
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    rc = run_direct(c, Rs[m], keys[m]);
+    if (rc) return rc;
+  }
+  return CC_OK;
+}
+
+// Prepares and runs the requests (pids[i], cids[i]) with one set of options: from a captured
+// graph when eligible (one branch per request), else one after the other on the context's
+// stream.  On failure every run made so far is freed.
+int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
+              const cc_run_opts *opts, std::vector<std::unique_ptr<Run>> &out) {
+  std::vector<std::unique_ptr<Run>> runs(npat);
+  std::vector<std::vector<long long>> keys(npat);
+  std::vector<Run *> Rs(npat);
+  auto fail = [&](int rc) {
+    for (auto &R : runs)
+      if (R && R->d_counters) free_run(c, R.get());
+    return rc;
+  };
+  for (int32_t i = 0; i < npat; ++i) {
+    int rc = prepare_run(c, pids[i], cids[i], opts, runs[i], keys[i]);
+    if (rc) {
+      runs[i].reset();  // prepare_run has freed what it took
+      return fail(rc);
+    }
+    Rs[i] = runs[i].get();
+  }
+  int rc = CC_OK;
+  if (graph_eligible(c, Rs, keys)) {
+    rc = run_graphed(c, Rs, keys);
+  } else {
+    for (int32_t i = 0; i < npat && !rc; ++i) {
+      rc = run_direct(c, Rs[i], keys[i]);
+      if (rc == CC_ENOMEM && !c->graphs.empty()) {  // graphs hold memory a direct run needs
+        drop_all_graphs(c);
+        rc = run_direct(c, Rs[i], keys[i]);
+      }
+    }
+  }
+  if (rc) return fail(rc);
+  out = std::move(runs);
   return CC_OK;
 }
 
@@ -1293,6 +1662,9 @@ int cc_destroy(cc_ctx *ctx) {
   Ctx *c = (Ctx *)ctx;
   cc_serve_stop(ctx);
   cudaStreamSynchronize(c->stream);
+  drop_all_graphs(c);
+  for (cudaStream_t s : c->branches) cudaStreamDestroy(s);
+  if (c->capture) cudaStreamDestroy(c->capture);
   if (c->owned_arena) cudaFree(c->owned_arena);
   delete c;
   return CC_OK;
@@ -1322,7 +1694,8 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   int vr = cc_check_graph(n, h_row_ptr, h_col);
   if (vr) return vr;
   const int64_t m2 = h_row_ptr[n];
-  // a new graph invalidates runs and colourings
+  // a new graph invalidates runs, colourings and captured graphs (they hold its addresses)
+  drop_all_graphs(c);
   for (auto &r : c->runs) free_run(c, r.second.get());
   c->runs.clear();
   for (auto &col : c->colorings) c->arena.release(col.second.d_colors);
@@ -1344,8 +1717,9 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
                             cudaMemcpyHostToDevice, c->stream));
   if (cc::launch_deg8(c->stream, c->dev, c->d_row_ptr, n, c->d_deg8)) return CC_ECUDA;
   c->launches++;
-  c->graph_version++;
-  c->plans.clear();
+  const long long fp = csr_fingerprint(n, h_row_ptr, h_col);
+  if (fp != c->graph_fp || c->plans.size() > 1024) c->plans.clear();
+  c->graph_fp = fp;
   c->h_row_ptr.assign(h_row_ptr, h_row_ptr + n + 1);
   c->h_col.assign(h_col, h_col + m2);
   c->n = n;
@@ -1529,26 +1903,21 @@ int cc_release_colors(cc_ctx *ctx, int32_t cid) {
 }
 
 int cc_run_dp(cc_ctx *ctx, int32_t pid, int32_t cid, const cc_run_opts *opts, int32_t *run_id) {
-  Ctx *c = (Ctx *)ctx;
-  if (!c || !run_id || c->n < 0) return CC_EINVAL;
-  Run *R = nullptr;
-  int rc = make_run(c, pid, cid, opts, &R);
-  if (rc) return rc;
-  int32_t id = c->next_run++;
-  c->runs[id].reset(R);
-  *run_id = id;
-  return CC_OK;
+  return cc_run_batch(ctx, 1, &pid, &cid, opts, run_id);
 }
 
 int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *pids, const int32_t *cids,
                  const cc_run_opts *opts, int32_t *run_ids) {
-  if (!ctx || npat < 0 || (npat && (!pids || !cids || !run_ids))) return CC_EINVAL;
+  Ctx *c = (Ctx *)ctx;
+  if (!c || c->n < 0 || npat < 0 || (npat && (!pids || !cids || !run_ids))) return CC_EINVAL;
+  if (npat == 0) return CC_OK;
+  std::vector<std::unique_ptr<Run>> runs;
+  int rc = make_runs(c, npat, pids, cids, opts, runs);
+  if (rc) return rc;
   for (int32_t i = 0; i < npat; ++i) {
-    int rc = cc_run_dp(ctx, pids[i], cids[i], opts, &run_ids[i]);
-    if (rc) {
-      for (int32_t j = 0; j < i; ++j) cc_release(ctx, run_ids[j]);
-      return rc;
-    }
+    const int32_t id = c->next_run++;
+    c->runs[id] = std::move(runs[i]);
+    run_ids[i] = id;
   }
   return CC_OK;
 }
@@ -1666,6 +2035,15 @@ int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_nod
     if (h_ms) h_ms[i] = ms;
     if (h_cand) h_cand[i] = t.candidates;
   }
+  return CC_OK;
+}
+
+int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || !mode) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  *mode = R->graphed ? CC_MODE_GRAPH : R->planned ? CC_MODE_PLANNED : CC_MODE_EXACT;
   return CC_OK;
 }
 

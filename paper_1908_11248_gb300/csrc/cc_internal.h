@@ -155,13 +155,13 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
                         unsigned long long src_cap, const unsigned long long *n,
                         unsigned long long buf_cap, void *buf_a, void *buf_b,
                         unsigned long long *hist, int *which, const SweepScratch *sw);
-// One record per run of equal keys of the sorted `src` (n records) with the summed count, written
-// densely to dst; *count receives the number of runs.  blk needs 2 * sort_grid(d) + 1 words.
-// With from_s non-null the records carry full sort keys of that order (a one-sweep sort leaves
-// them so) and are written back as packed keys.
+// One record per run of equal keys of the sorted `src` (min(*n, n_cap) records) with the summed
+// count, written densely to dst (room for n_cap records); *count receives the number of runs.
+// blk needs 2 * sort_grid(d) + 1 words.  With from_s non-null the records carry full sort keys of
+// that order (a one-sweep sort leaves them so) and are written back as packed keys.
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
-                  const unsigned long long *n, unsigned long long *blk, void *dst,
-                  unsigned long long *count, const SortSpec *from_s);
+                  const unsigned long long *n, unsigned long long n_cap, unsigned long long *blk,
+                  void *dst, unsigned long long *count, const SortSpec *from_s);
 // Introduce of a vertex with at most one bag neighbour, warp by warp, for planned runs: mode 1
 // appends in per-warp chunks from a.cursor (holes left where chunks are not filled), mode 2
 // adds into the parent forget's hash table.

@@ -155,10 +155,12 @@ __device__ __forceinline__ void emit(const IntroArgs &a, S &sm, EmitState &st, b
     }
   } else if (valid) {
     ++st.produced;
-    int r = hash_add(reinterpret_cast<Slot<K> *>(a.out.slots), a.out.cap,
-                     key_remove(okey, a.L, a.q), oc);
-    if (r > 0) ++st.fresh;
-    if (r < 0) st.full = true;
+    if (!st.full) {  // a full table takes no more probes: the run is repeated
+      int r = hash_add(reinterpret_cast<Slot<K> *>(a.out.slots), a.out.cap,
+                       key_remove(okey, a.L, a.q), oc);
+      if (r > 0) ++st.fresh;
+      if (r < 0) st.full = true;
+    }
   }
 }
 
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
   constexpr int VCAP = GROUPED ? 2048 : 1;
   __shared__ IntroSmem<K, BLOCK, VCAP> sm;
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
-  const u64 bound = table_bound<K>(a.in);
+  const u64 bound = block_run_failed(a.err) ? 0 : table_bound<K>(a.in);
   EmitState st;
   if (MODE == 1) st.cursor = blk_base[blockIdx.x];
   for (u64 base = (u64)blockIdx.x * BLOCK; base < bound; base += (u64)gridDim.x * BLOCK) {
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
   const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const u64 bound = table_bound<K>(a.in);
+  const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
   u64 cbase = 0, cfill = kWarpChunk;  // warp-uniform chunk state
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
@@ -500,9 +502,11 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
         }
       } else if (valid) {
         ++produced;
-        const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
-        if (r > 0) ++fresh;
-        if (r < 0) full = true;
+        if (!full) {
+          const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
+          if (r > 0) ++fresh;
+          if (r < 0) full = true;
+        }
       }
     }
   }
@@ -562,9 +566,11 @@ __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey
     }
   } else if (valid) {
     ++produced;
-    const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
-    if (r > 0) ++fresh;
-    if (r < 0) full = true;
+    if (!full) {
+      const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
+      if (r > 0) ++fresh;
+      if (r < 0) full = true;
+    }
   }
 }
 
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   int *buf = s_buf[wib];
   const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
   const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + wib;
-  const u64 bound = table_bound<K>(a.in);
+  const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
   u64 cbase = 0, cfill = kWarpChunk;
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
@@ -720,7 +726,7 @@ __global__ void __launch_bounds__(BLOCK) forget_kernel(ForgetArgs a) {
   __shared__ u64 s_red[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
-  const u64 bound = table_bound<K>(a.in);
+  const u64 bound = block_run_failed(a.err) ? 0 : table_bound<K>(a.in);
   const u64 ocap = a.out.cap;
   u64 fresh = 0;
   bool full = false;
@@ -728,7 +734,7 @@ __global__ void __launch_bounds__(BLOCK) forget_kernel(ForgetArgs a) {
     K key;
     u64 c;
     load_slot(in, i, key, c);
-    if (key == 0) continue;
+    if (key == 0 || full) continue;
     int r = hash_add(out, ocap, key_remove(key, a.L, a.q), c);
     if (r > 0) ++fresh;
     if (r < 0) full = true;
@@ -749,14 +755,14 @@ template <typename K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) join_build_kernel(JoinArgs a) {
   const Slot<K> *bt = reinterpret_cast<const Slot<K> *>(a.build.slots);
   Slot<K> *idx = reinterpret_cast<Slot<K> *>(a.index);
-  const u64 bound = table_bound<K>(a.build);
+  const u64 bound = block_run_failed(a.err) ? 0 : table_bound<K>(a.build);
   const u64 icap = a.index_cap;
   bool full = false;
   for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < bound; i += (u64)gridDim.x * BLOCK) {
     K key;
     u64 c;
     load_slot(bt, i, key, c);
-    if (key == 0) continue;
+    if (key == 0 || full) continue;
     long long h = hash_claim(idx, icap, phi_key(key, a.L));
     if (h < 0) {
       full = true;
@@ -774,7 +780,7 @@ __global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
   const Slot<K> *pt = reinterpret_cast<const Slot<K> *>(a.probe.slots);
   const Slot<K> *idx = reinterpret_cast<const Slot<K> *>(a.index);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
-  const u64 bound = table_bound<K>(a.probe);
+  const u64 bound = block_run_failed(a.err) ? 0 : table_bound<K>(a.probe);
   const u64 icap = a.index_cap, ocap = a.out.cap;
   const K cmask = (K)((1ull << a.L.k) - 1ull);
   u64 pairs = 0, fresh = 0;
@@ -801,7 +807,7 @@ __global__ void __launch_bounds__(BLOCK) join_probe_kernel(JoinArgs a) {
       const uint32_t C1 = key_mask(k1, a.L);
       if ((C1 & C2) == bagc) {
         ++pairs;
-        if (MODE == 1) {
+        if (MODE == 1 && !full) {
           int r = hash_add(out, ocap, (key & ~cmask) | (K)(C1 | C2), c1 * c2);
           if (r > 0) ++fresh;
           if (r < 0) full = true;

@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
 // ---- reduce by key: equal keys are adjacent; one record per run with the summed count ------
 template <typename K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, const u64 *n_ptr,
-                                                             u64 *blk) {
-  const u64 n = *n_ptr;
+                                                             u64 n_cap, u64 *blk) {
+  const u64 n = min(*n_ptr, n_cap);
   __shared__ u64 s_red[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   const u64 G = gridDim.x, chunk = (n + G - 1) / G;
@@ -394,9 +394,9 @@ __global__ void blk_scan_kernel(u64 *blk, int G) {
 
 template <typename K, int BLOCK, bool FROM_S>
 __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, const u64 *n_ptr,
-                                                             const u64 *blk, void *dst,
+                                                             u64 n_cap, const u64 *blk, void *dst,
                                                              u64 *count, SortSpec sp) {
-  const u64 n = *n_ptr;
+  const u64 n = min(*n_ptr, n_cap);
   __shared__ int s_wc[BLOCK / 32];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
@@ -511,19 +511,23 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
 }
 
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
-                  const unsigned long long *n, unsigned long long *blk, void *dst,
-                  unsigned long long *count, const SortSpec *from_s) {
+                  const unsigned long long *n, unsigned long long n_cap, unsigned long long *blk,
+                  void *dst, unsigned long long *count, const SortSpec *from_s) {
   const int G = grid256(d);
   const SortSpec sp = from_s ? *from_s : SortSpec{};
-  if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, blk);
-  else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, blk);
+  if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
+  else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
   blk_scan_kernel<<<1, 32, 0, s>>>(blk, G);
   if (kw == 1) {
-    if (from_s) reduce_write_kernel<u64, 256, true><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
-    else reduce_write_kernel<u64, 256, false><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+    if (from_s)
+      reduce_write_kernel<u64, 256, true><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
+    else
+      reduce_write_kernel<u64, 256, false><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
   } else {
-    if (from_s) reduce_write_kernel<u128, 256, true><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
-    else reduce_write_kernel<u128, 256, false><<<G, 256, 0, s>>>(src, n, blk, dst, count, sp);
+    if (from_s)
+      reduce_write_kernel<u128, 256, true><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
+    else
+      reduce_write_kernel<u128, 256, false><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
   }
   return (int)cudaGetLastError();
 }

@@ -27,11 +27,12 @@ def ctx():
     c.close()
 
 
-def gpu_dp(ctx, g, pat, colours=None, k=None, seed=None, trials=1, **opt):
+def gpu_dp(ctx, g, pat, colours=None, k=None, seed=None, trials=1, pid=None, **opt):
     nF, e, td = pat
     k = k or nF
     cc.cc_load_graph(ctx.h, *g)
-    pid = cc.cc_load_pattern(ctx.h, nF, e, td)
+    if pid is None:
+        pid = cc.cc_load_pattern(ctx.h, nF, e, td)
     n = len(g[0]) - 1
     if colours is not None:
         cid = cc.cc_set_colors(ctx.h, colours, k)
@@ -303,12 +304,13 @@ def test_planned_runs_match_exact(ctx):
     g = synth.barabasi_albert(3000, 4, 7)
     for pat in (synth.grid_pattern(2, 3), synth.pattern_B(), synth.random_partial_ktree(8, 2, 9)):
         nF = pat[0]
-        ref = None
+        pid = cc.cc_load_pattern(ctx.h, *pat)
         for rep in range(3):
             colours = oracle.colors(3000, 4, nF, seed=40 + (rep % 2))
+            want = oracle.run_dp(g, pat, colours, nF)
             for fuse in (0, 1, 2):
-                r = gpu_dp(ctx, g, pat, colours=colours, k=nF, fuse=fuse)
-                want = oracle.run_dp(g, pat, colours, nF) if fuse == 0 else want
+                r = gpu_dp(ctx, g, pat, colours=colours, k=nF, fuse=fuse, pid=pid)
+                assert cc.cc_run_mode(ctx.h, r["run"]) == ("exact" if rep == 0 else "planned")
                 assert np.array_equal(r["count"], want.count)
                 assert np.array_equal(r["sizes"], want.node_sizes.sum(axis=0))
                 release(ctx, r)
@@ -320,16 +322,19 @@ def test_planned_overflow_falls_back(ctx):
     g = synth.barabasi_albert(3000, 4, 8)
     pat = synth.grid_pattern(2, 3)
     mono = np.zeros((4, 3000), np.uint8)  # one colour: no colourful edge at all
-    r = gpu_dp(ctx, g, pat, colours=mono, k=6)
-    assert int(r["count"].sum()) == 0
-    release(ctx, r)
     colours = oracle.colors(3000, 4, 6, seed=9)
+    ref = oracle.run_dp(g, pat, colours, 6)
     for fuse in (1, 2, 0):
-        r = gpu_dp(ctx, g, pat, colours=colours, k=6, fuse=fuse)
-        ref = oracle.run_dp(g, pat, colours, 6)
-        assert np.array_equal(r["count"], ref.count)
-        assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+        pid = cc.cc_load_pattern(ctx.h, *pat)
+        r = gpu_dp(ctx, g, pat, colours=mono, k=6, fuse=fuse, pid=pid)
+        assert int(r["count"].sum()) == 0
         release(ctx, r)
+        for want in ("exact", "planned"):  # the tiny plan overflows and is redone exactly
+            r = gpu_dp(ctx, g, pat, colours=colours, k=6, fuse=fuse, pid=pid)
+            assert cc.cc_run_mode(ctx.h, r["run"]) == want
+            assert np.array_equal(r["count"], ref.count)
+            assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
+            release(ctx, r)
 
 
 @pytest.mark.parametrize("sweep", [0, 1])
@@ -355,8 +360,10 @@ def test_planned_at_workload_scale(ctx):
     z = oracle.colors(20000, 2, 8, seed=3)
     ref = oracle.run_dp(g, pat, z, 8)
     for fuse in (2, 1):
-        for _ in range(2):  # exact, then planned
-            r = gpu_dp(ctx, g, pat, colours=z, k=8, fuse=fuse)
+        pid = cc.cc_load_pattern(ctx.h, *pat)
+        for want in ("exact", "planned"):
+            r = gpu_dp(ctx, g, pat, colours=z, k=8, fuse=fuse, pid=pid)
+            assert cc.cc_run_mode(ctx.h, r["run"]) == want
             assert np.array_equal(r["count"], ref.count)
             assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
             release(ctx, r)

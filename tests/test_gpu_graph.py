@@ -1,0 +1,188 @@
+"""Planned, graph-replayed and batched runs against the CPU oracle (bit-exact, integer results).
+
+A run of a (pattern, graph content, trials, colours, options) key that has been seen before uses
+the capacities planned by the earlier runs; with use_graph it is replayed from a captured CUDA
+graph, and a batch of such requests is replayed as parallel branches of one graph.  Whatever
+path a run takes, its per-trial counts, exists flags and table sizes are the oracle's.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+cc = pytest.importorskip("paper_1908_11248_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    c = cc.Context(arena_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+def _load(ctx, pat):
+    nF, e, td = pat
+    return cc.cc_load_pattern(ctx.h, nF, e, td)
+
+
+def _check(ctx, run, pid, ref, trials):
+    N, _ = cc.cc_pattern_info(ctx.h, pid)
+    assert np.array_equal(cc.cc_count(ctx.h, run, trials), ref.count)
+    assert np.array_equal(cc.cc_decide(ctx.h, run, trials), ref.exists)
+    assert np.array_equal(cc.cc_table_stats(ctx.h, run, N)[0], ref.node_sizes.sum(axis=0))
+
+
+def test_planned_mode_reached_and_exact(ctx):
+    """The first run of a key is exact, later ones planned; both give the oracle's results, and a
+    reload of the same graph content keeps the plan."""
+    g = synth.barabasi_albert(3000, 4, 7)
+    for pat in (synth.grid_pattern(2, 3), synth.pattern_B(), synth.random_partial_ktree(8, 2, 9)):
+        nF = pat[0]
+        cc.cc_load_graph(ctx.h, *g)
+        pid = _load(ctx, pat)
+        modes = []
+        for rep in range(3):
+            if rep == 2:
+                cc.cc_load_graph(ctx.h, *g)  # same content: the plan stays
+            z = oracle.colors(3000, 4, nF, seed=40 + rep)
+            ref = oracle.run_dp(g, pat, z, nF)
+            cid = cc.cc_set_colors(ctx.h, z, nF)
+            run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
+            _check(ctx, run, pid, ref, 4)
+            modes.append(cc.cc_run_mode(ctx.h, run))
+            cc.cc_release(ctx.h, run)
+            cc.cc_release_colors(ctx.h, cid)
+        assert modes == ["exact", "planned", "planned"]
+
+
+@pytest.mark.parametrize("fuse", [2, 1, 0])
+def test_graph_replay_matches_oracle(ctx, fuse):
+    """use_graph: exact first, then captured and replayed with fresh colourings each time; every
+    replay launches the same kernels and gives the oracle's results."""
+    g = synth.barabasi_albert(2500, 4, 21)
+    cc.cc_load_graph(ctx.h, *g)
+    for pat in (synth.cycle_pattern(5), synth.grid_pattern(2, 3), synth.pattern_C()):
+        nF = pat[0]
+        pid = _load(ctx, pat)
+        modes, launched = [], []
+        for rep in range(4):
+            z = oracle.colors(2500, 3, nF, seed=100 + rep)
+            ref = oracle.run_dp(g, pat, z, nF)
+            cid = cc.cc_set_colors(ctx.h, z, nF)
+            before = cc.cc_context_stats(ctx.h)[0]
+            run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(use_graph=1, fuse=fuse))
+            launched.append(cc.cc_context_stats(ctx.h)[0] - before)
+            _check(ctx, run, pid, ref, 3)
+            modes.append(cc.cc_run_mode(ctx.h, run))
+            cc.cc_release(ctx.h, run)
+            cc.cc_release_colors(ctx.h, cid)
+        assert modes == ["exact", "graph", "graph", "graph"]
+        assert launched[1] == launched[2] == launched[3] > 0
+
+
+def test_graph_overflow_falls_back(ctx):
+    """A graph captured with capacities planned on a one-colour colouring (no colourful edge)
+    is too small for a random colouring: the replay notices, the graph is dropped and the run is
+    repeated directly with the oracle's results; the next run captures a new graph."""
+    g = synth.barabasi_albert(3000, 4, 8)
+    pat = synth.grid_pattern(2, 3)
+    cc.cc_load_graph(ctx.h, *g)
+    pid = _load(ctx, pat)
+    mono = np.zeros((4, 3000), np.uint8)
+    opts = cc.cc_default_opts(use_graph=1)
+    for want in ("exact", "graph"):
+        cid = cc.cc_set_colors(ctx.h, mono, 6)
+        run = cc.cc_run_dp(ctx.h, pid, cid, opts)
+        assert int(cc.cc_count(ctx.h, run, 4).sum()) == 0
+        assert cc.cc_run_mode(ctx.h, run) == want
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
+    z = oracle.colors(3000, 4, 6, seed=9)
+    ref = oracle.run_dp(g, pat, z, 6)
+    for want in ("exact", "graph"):
+        cid = cc.cc_set_colors(ctx.h, z, 6)
+        run = cc.cc_run_dp(ctx.h, pid, cid, opts)
+        _check(ctx, run, pid, ref, 4)
+        assert cc.cc_run_mode(ctx.h, run) == want
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
+
+
+def test_batch_graph_matches_oracle(ctx):
+    """A batch of requests (different patterns, one pattern twice with different colourings,
+    different trial counts, 64- and 128-bit keys) runs exactly, then as one graph of parallel
+    branches; each request's results are the oracle's."""
+    n = 2000
+    g = synth.erdos_renyi(n, 6.0 / n, 5)
+    cc.cc_load_graph(ctx.h, *g)
+    reqs = [(synth.cycle_pattern(5), 5, 3), (synth.grid_pattern(2, 3), 6, 2),
+            (synth.cycle_pattern(5), 5, 3), (synth.pattern_A(), None, 2),
+            (synth.star_pattern(4), 7, 1), (synth.cycle_pattern(5), 31, 2)]
+    pids = [_load(ctx, r[0]) for r in reqs]
+    opts = cc.cc_default_opts(use_graph=1)
+    for rep in range(3):
+        cids, refs = [], []
+        for i, (pat, k, T) in enumerate(reqs):
+            k = k or pat[0]
+            z = oracle.colors(n, T, k, seed=1000 * rep + i)
+            refs.append(oracle.run_dp(g, pat, z, k))
+            cids.append(cc.cc_set_colors(ctx.h, z, k))
+        runs = cc.cc_run_batch(ctx.h, pids, cids, opts)
+        for i, run in enumerate(runs):
+            _check(ctx, run, pids[i], refs[i], reqs[i][2])
+            assert cc.cc_run_mode(ctx.h, run) == ("exact" if rep == 0 else "graph")
+            cc.cc_release(ctx.h, run)
+        for cid in cids:
+            cc.cc_release_colors(ctx.h, cid)
+
+
+def test_batch_without_graph_and_errors(ctx):
+    """Without use_graph a batch is a sequence of runs with the same results; a bad request in a
+    batch fails the whole call and keeps no run."""
+    n = 1500
+    g = synth.barabasi_albert(n, 3, 2)
+    cc.cc_load_graph(ctx.h, *g)
+    pats = [synth.path_pattern(4), synth.cycle_pattern(4)]
+    pids = [_load(ctx, p) for p in pats]
+    z = oracle.colors(n, 2, 4, seed=5)
+    cid = cc.cc_set_colors(ctx.h, z, 4)
+    runs = cc.cc_run_batch(ctx.h, pids, [cid, cid], cc.cc_default_opts())
+    for run, pid, pat in zip(runs, pids, pats):
+        _check(ctx, run, pid, oracle.run_dp(g, pat, z, 4), 2)
+        cc.cc_release(ctx.h, run)
+    used = cc.cc_context_stats(ctx.h)[1]
+    with pytest.raises(cc.CCError):
+        cc.cc_run_batch(ctx.h, [pids[0], 999999], [cid, cid], cc.cc_default_opts())
+    assert cc.cc_context_stats(ctx.h)[1] == used
+    assert cc.cc_run_batch(ctx.h, [], [], None) == []
+    cc.cc_release_colors(ctx.h, cid)
+
+
+def test_graph_dropped_on_new_graph(ctx):
+    """Loading a different graph drops captured graphs and plans: the next run is exact and
+    correct on the new graph."""
+    pat = synth.cycle_pattern(5)
+    opts = cc.cc_default_opts(use_graph=1)
+    pid = None
+    for seed, want in ((31, ["exact", "graph"]), (32, ["exact", "graph"])):
+        g = synth.barabasi_albert(2000, 3, seed)
+        cc.cc_load_graph(ctx.h, *g)
+        pid = pid or _load(ctx, pat)
+        z = oracle.colors(2000, 2, 5, seed=seed)
+        ref = oracle.run_dp(g, pat, z, 5)
+        modes = []
+        for _ in range(2):
+            cid = cc.cc_set_colors(ctx.h, z, 5)
+            run = cc.cc_run_dp(ctx.h, pid, cid, opts)
+            _check(ctx, run, pid, ref, 2)
+            modes.append(cc.cc_run_mode(ctx.h, run))
+            cc.cc_release(ctx.h, run)
+            cc.cc_release_colors(ctx.h, cid)
+        assert modes == want
