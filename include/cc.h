@@ -39,6 +39,7 @@ extern "C" {
 #define CC_ECUDA (-5)      /* a CUDA runtime call failed                                        */
 #define CC_ENOTFOUND (-6)  /* unknown pattern, colouring, run or ticket id                      */
 #define CC_EKEYWIDTH (-7)  /* trial, bag-mapping and colour-set bits do not fit in 128 bits     */
+#define CC_EBUSY (-8)      /* the context is serving: only cc_serve_* and the pattern calls run */
 
 /* Static text for an error code. */
 const char *cc_strerror(int code);
@@ -256,20 +257,45 @@ int cc_count_noalloc(int device, void *cuda_stream, int32_t n, const int32_t *h_
                      uint64_t *h_counts, uint8_t *h_exists);
 
 /* ---- serving: a resident graph, queries admitted by table memory, batched as they arrive --- */
-/* Starts a server thread that owns device work for submitted queries; mem_budget bytes of the
- * arena may hold query tables at once (0 = half the free arena). */
+/* Many pattern queries against the loaded graph (Section 5 runs every query of a data set on one
+ * host graph).  cc_serve_start starts a server thread that from then on alone issues the
+ * context's device work: until cc_serve_stop, every other call on the context returns CC_EBUSY
+ * except cc_serve_*, cc_load_pattern, cc_pattern_info, cc_pattern_nodes and cc_context_stats
+ * (which may be called from any thread).  Queries wait in submission order.  The server admits
+ * the next one while one of max_inflight execution slots (each a CUDA stream; 0 = 8, at most
+ * 64) is free and the table memory its plan needs fits within mem_budget bytes of the arena
+ * (0 = half the free arena) beside the queries already running, so that queries arriving while
+ * others run share the GPU with them.  Each query colours the graph (cc_color with its seed,
+ * trials and k) and runs the DP with cc_default_opts inside its own arena range, reserved at
+ * admission and trimmed to what its kernels use.  A query whose (pattern, trials, k) has no
+ * plan yet runs exactly, synchronously on its slot; later ones of the same key run planned, and
+ * one that outgrows its plan runs again exactly.  Results are those of cc_count and cc_decide
+ * for the same inputs, whatever else runs.  Errors: CC_EINVAL (no graph, bad max_inflight),
+ * CC_EBUSY (already serving), CC_ECUDA. */
 int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight);
 
-/* Queues a query (pattern, seed, trials, k); returns at once with a ticket. */
+/* Queues a query of pattern `pattern_id` under colouring (seed, trials, k) and returns at once
+ * with *ticket.  A bad pattern id or k < n_F is reported by the query's status.  Thread-safe.
+ * Errors: CC_EINVAL (not serving or stopping, trials < 1, k outside [1, 32]). */
 int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t trials, int32_t k,
                     int64_t *ticket);
 
-/* Polls a ticket: *done = 1 when finished (then counts/exists hold `trials` values and
- * latency_ns the submit-to-completion time), 0 while queued or running; *status its result. */
+/* Polls a ticket: *done = 0 while it waits or runs.  Once done, *status is its result code and,
+ * if that is CC_OK, h_counts[trials] and h_exists[trials] (either may be NULL) hold its counts
+ * and exists flags and *latency_ns the time from submission to completion; the ticket is then
+ * forgotten (a later poll gives CC_ENOTFOUND).  Thread-safe. */
 int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
                   uint64_t *h_counts, uint8_t *h_exists, int64_t *latency_ns);
 
-/* Stops the server after the queued queries finish. */
+/* Server counters since its creation: queries submitted and completed, the most queries seen
+ * running at once, the most arena bytes they held at once, exact runs (first queries of a key
+ * and reruns) and reruns of queries that outgrew their plan.  Any pointer may be NULL.
+ * Errors: CC_EINVAL, CC_ENOTFOUND (the context never served). */
+int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed, int32_t *inflight_max,
+                   uint64_t *reserved_max, uint64_t *exact_runs, uint64_t *reruns);
+
+/* Stops the server after the queued and running queries finish; results not yet polled stay
+ * available.  Returns CC_OK if no server runs. */
 int cc_serve_stop(cc_ctx *ctx);
 
 #ifdef __cplusplus

@@ -31,6 +31,7 @@ EXPORTS = [
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
+    "cc_serve_stats",
 ]
 RUN_MODES = ["exact", "planned", "graph"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -99,6 +100,7 @@ def lib():
         "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_check_graph": ([i32, P, P], ctypes.c_int),
         "cc_run_mode": ([P, i32, P], ctypes.c_int),
+        "cc_serve_stats": ([P, P, P, P, P, P, P], ctypes.c_int),
         "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
                              ctypes.c_int),
     }
@@ -359,6 +361,14 @@ def cc_serve_poll(ctx, ticket: int, trials: int):
     _check(lib().cc_serve_poll(ctx, ticket, ctypes.byref(done), ctypes.byref(status), _p(counts),
                                _p(exists), ctypes.byref(lat)), "cc_serve_poll")
     return bool(done.value), status.value, counts, exists, lat.value
+
+
+def cc_serve_stats(ctx) -> dict:
+    v = [ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_int32(0), ctypes.c_uint64(0),
+         ctypes.c_uint64(0), ctypes.c_uint64(0)]
+    _check(lib().cc_serve_stats(ctx, *[ctypes.byref(x) for x in v]), "cc_serve_stats")
+    names = ["submitted", "completed", "inflight_max", "reserved_max", "exact_runs", "reruns"]
+    return {k: int(x.value) for k, x in zip(names, v)}
 
 
 def cc_serve_stop(ctx):

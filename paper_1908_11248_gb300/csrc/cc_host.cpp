@@ -19,236 +19,20 @@
 
 #include "../../include/cc.h"
 #include "cc_internal.h"
+#include "cc_runtime.h"
 
 using cc::DevInfo;
 using cc::KeyLayout;
 using cc::TableDesc;
-typedef unsigned long long u64;
-
-// ------------------------------------------------------------------------------------------
-// device arena: first-fit over one device range, 256-byte aligned blocks
-// ------------------------------------------------------------------------------------------
-namespace {
-
-class Arena {
- public:
-  void init(char *base, size_t size) {
-    base_ = base;
-    size_ = size;
-    free_.clear();
-    used_.clear();
-    inuse_ = hw_ = top_ = 0;
-    if (size) free_[0] = size;
-  }
-  void *alloc(size_t bytes) {
-    if (bytes == 0) bytes = 1;
-    bytes = (bytes + 255) & ~size_t(255);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      size_t off = it->first, sz = it->second;
-      free_.erase(it);
-      if (sz > bytes) free_[off + bytes] = sz - bytes;
-      used_[off] = bytes;
-      inuse_ += bytes;
-      if (inuse_ > hw_) hw_ = inuse_;
-      if (off + bytes > top_) top_ = off + bytes;
-      return base_ + off;
-    }
-    return nullptr;
-  }
-  void release(void *p) {
-    if (!p) return;
-    size_t off = (char *)p - base_;
-    auto u = used_.find(off);
-    if (u == used_.end()) return;
-    size_t sz = u->second;
-    used_.erase(u);
-    inuse_ -= sz;
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && nx->first == off + sz) {
-      sz += nx->second;
-      nx = free_.erase(nx);
-    }
-    if (nx != free_.begin()) {
-      auto pv = std::prev(nx);
-      if (pv->first + pv->second == off) {
-        pv->second += sz;
-        return;
-      }
-    }
-    free_[off] = sz;
-  }
-  // Gives back the tail of block p beyond its first `bytes` bytes.
-  void shrink(void *p, size_t bytes) {
-    if (!p) return;
-    bytes = (bytes + 255) & ~size_t(255);
-    if (bytes == 0) bytes = 256;
-    const size_t off = (char *)p - base_;
-    auto u = used_.find(off);
-    if (u == used_.end() || u->second <= bytes) return;
-    const size_t tail = off + bytes, tail_sz = u->second - bytes;
-    u->second = bytes;
-    inuse_ -= tail_sz;
-    used_[tail] = tail_sz;  // released at once, so that it merges with its free neighbours
-    inuse_ += tail_sz;
-    release(base_ + tail);
-  }
-  // end offset of the highest block handed out since init
-  size_t top() const { return top_; }
-  size_t free_bytes() const {
-    size_t s = 0;
-    for (auto &f : free_) s += f.second;
-    return s;
-  }
-  size_t size() const { return size_; }
-  size_t in_use() const { return inuse_; }
-  size_t high_water() const { return hw_; }
-  void reset_high_water() { hw_ = inuse_; }
-  size_t largest_free() const {
-    size_t s = 0;
-    for (auto &f : free_) s = std::max(s, f.second);
-    return s;
-  }
-
- private:
-  char *base_ = nullptr;
-  size_t size_ = 0, inuse_ = 0, hw_ = 0, top_ = 0;
-  std::map<size_t, size_t> free_, used_;
-};
-
-}  // namespace
-
-// ------------------------------------------------------------------------------------------
-// context objects
-// ------------------------------------------------------------------------------------------
-namespace cc {
-
-struct NiceNode {
-  int32_t type = 0;  // 0 leaf, 1 introduce, 2 forget, 3 join
-  int32_t child0 = -1, child1 = -1, vertex = -1, parent = -1;
-  std::vector<int32_t> bag;  // increasing
-};
-
-struct Pattern {
-  int32_t nF = 0;
-  std::vector<uint32_t> adj;  // adjacency bitmask per F-vertex
-  std::vector<int32_t> deg;
-  std::vector<NiceNode> nodes;  // post-order, root last
-  int32_t width = 0;
-};
-
-struct Coloring {
-  int32_t trials = 0, k = 0;
-  uint8_t *d_colors = nullptr;
-  int refs = 1;
-};
-
-struct NodeTable {
-  void *slots = nullptr;
-  u64 cap = 0;
-  int hashed = 0;
-  bool stored = false;
-  // a dense table sorted with these bag slots most significant (sort_n == 0: no known order)
-  int sort_n = 0;
-  int sort_slots[kMaxBag] = {};
-  // scan bound of a dense table written in chunks (holes up to it); null: the entry counter
-  unsigned long long *bound = nullptr;
-};
-
-// Capacities learned from exact runs of one (pattern, graph, trials, colours, options): the
-// largest table sizes and join pair counts seen, per node.
-struct Plan {
-  std::vector<u64> entries, pairs;
-  size_t peak_bytes = 0;  // largest arena use of a run beyond what it started with
-  int runs = 0;
-};
-
-struct Timing {
-  int32_t node, kind;
-  cudaEvent_t start, stop;
-  u64 candidates;
-};
-
-struct Run {
-  int32_t pattern = -1, coloring = -1;
-  std::vector<Timing> timings;
-  cc_run_opts opts{};
-  KeyLayout L{};
-  int kw = 1;
-  int32_t trials = 0;
-  std::vector<NodeTable> tables;
-  // per node, four words each: entries, chunk cursor, join pairs, candidates examined
-  u64 *d_counters = nullptr;
-  unsigned *d_exists = nullptr;
-  u64 *d_count = nullptr;
-  std::vector<u64> sizes, pairs;
-  std::vector<std::pair<const u64 *, u64>> checks;  // planned runs: device word <= capacity
-  bool retained = false;
-  bool planned = false;
-  bool graphed = false;
-  u64 *d_blk = nullptr;  // per-run scratch: block counts and bases, pair counters
-  int *d_err = nullptr;  // per-run device error word
-  Arena *home = nullptr;  // the arena its memory came from (null: the context's)
-};
-
-// A captured CUDA graph of planned runs (one member per run; members are parallel branches).
-// Each member owns a sub-arena reserved from the context arena for the graph's lifetime, the
-// colouring buffer the graph reads, and a shadow run whose device words the graph writes.
-struct GraphMember {
-  void *block = nullptr;
-  size_t bytes = 0;
-  Arena sub;
-  uint8_t *colours = nullptr;
-  std::unique_ptr<Run> shadow;
-};
-
-struct GraphSet {
-  cudaGraphExec_t exec = nullptr;
-  std::vector<GraphMember> members;
-  u64 kernels = 0;  // kernel launches per replay
-};
-
-struct Ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  DevInfo dev;
-  Arena arena;
-  Arena *active = nullptr;  // where run allocations go: the arena, or a captured graph's own
-  char *owned_arena = nullptr;
-  // graph
-  int32_t n = -1;
-  int32_t *d_row_ptr = nullptr, *d_col = nullptr;
-  uint8_t *d_deg8 = nullptr;  // min(degree, 255) per vertex
-  std::vector<int32_t> h_row_ptr, h_col;
-  int *d_err = nullptr;
-  u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
-  // content fingerprint of the loaded graph: plans stay valid while the graph's content is the
-  // same, so reloading an identical graph keeps them
-  long long graph_fp = 0;
-  std::map<std::vector<long long>, Plan> plans;
-  std::map<std::vector<long long>, std::unique_ptr<GraphSet>> graphs;
-  std::vector<cudaStream_t> branches;  // streams of captured batch branches
-  cudaStream_t capture = nullptr;      // where graphs are captured (the context's stream may be
-                                       // the legacy default stream, which cannot be captured)
-  u64 *d_scratch = nullptr;  // small per-call scratch (block counts, pair counter)
-  size_t scratch_words = 0;
-  std::map<int32_t, Pattern> patterns;
-  std::map<int32_t, Coloring> colorings;
-  std::map<int32_t, std::unique_ptr<Run>> runs;
-  int32_t next_pattern = 1, next_coloring = 1, next_run = 1;
-  u64 launches = 0;
-  // serving
-  struct Server *server = nullptr;
-};
-
-}  // namespace cc
-
+using cc::u64;
+using cc::Arena;
 using cc::Ctx;
 using cc::NiceNode;
 using cc::Pattern;
 using cc::Run;
 
-namespace {
+namespace cc {
+namespace rt {
 
 #define CUDA_OK(expr)                               \
   do {                                              \
@@ -546,11 +330,6 @@ void td_from_order(std::vector<uint32_t> adj, int n, const std::vector<int> &ord
 
 // ---- helpers ------------------------------------------------------------------------------
 Arena &active_arena(Ctx *c) { return c->active ? *c->active : c->arena; }
-
-template <typename T>
-T *arena_alloc(Ctx *c, size_t count) {
-  return (T *)active_arena(c).alloc(count * sizeof(T));
-}
 
 void free_run(Ctx *c, Run *r) {
   Arena &H = r->home ? *r->home : c->arena;
@@ -1214,15 +993,11 @@ long long csr_fingerprint(int32_t n, const int32_t *row_ptr, const int32_t *col)
   return (long long)(h | 1);
 }
 
-// Validates a (pattern, colouring, options) request and sets up its run: key layout, device
-// words, and the plan key of its capacities.
-int prepare_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts,
-                std::unique_ptr<Run> &R, std::vector<long long> &key) {
+int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc_run_opts *opts,
+             std::unique_ptr<Run> &R, std::vector<long long> &key) {
   auto pi = c->patterns.find(pid);
-  auto ci = c->colorings.find(cid);
-  if (pi == c->patterns.end() || ci == c->colorings.end()) return CC_ENOTFOUND;
+  if (pi == c->patterns.end()) return CC_ENOTFOUND;
   const Pattern &P = pi->second;
-  cc::Coloring &col = ci->second;
   if (col.k < P.nF) return CC_EINVAL;
   R.reset(new Run());
   cc_default_opts(&R->opts);
@@ -1244,19 +1019,42 @@ int prepare_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts,
   if (bmax > cc::kMaxBag || width > 128) return CC_EKEYWIDTH;
   R->kw = width <= 64 ? 1 : 2;
   const int N = (int)P.nodes.size();
-  col.refs++;  // released by free_run
+  Arena &A = active_arena(c);
+  R->home = &A == &c->arena ? nullptr : &A;
   R->d_counters = arena_alloc<u64>(c, 4 * (size_t)N);
   R->d_exists = arena_alloc<unsigned>(c, col.trials);
   R->d_count = arena_alloc<u64>(c, col.trials);
   R->d_err = arena_alloc<int>(c, 1);
   if (!R->d_counters || !R->d_exists || !R->d_count || !R->d_err) {
-    free_run(c, R.get());
+    A.release(R->d_counters);
+    A.release(R->d_exists);
+    A.release(R->d_count);
+    A.release(R->d_err);
+    R.reset();
     return CC_ENOMEM;
   }
   R->retained = R->opts.retain != 0;
-  key = {pid, c->graph_fp, col.trials, col.k, R->opts.degree_filter, R->opts.fuse,
-         R->opts.group, R->opts.block, (long long)(R->opts.load_factor * 1000),
-         R->opts.sort_sweep};
+  key = plan_key(c, pid, col.trials, col.k, R->opts);
+  return CC_OK;
+}
+
+std::vector<long long> plan_key(const Ctx *c, int32_t pid, int32_t trials, int32_t k,
+                                const cc_run_opts &o) {
+  return {pid, c->graph_fp, trials, k, o.degree_filter, o.fuse, o.group, o.block,
+          (long long)(o.load_factor * 1000), o.sort_sweep};
+}
+
+// init_run for colouring id cid of the context, which the run then holds a reference to.
+int prepare_run(Ctx *c, int32_t pid, int32_t cid, const cc_run_opts *opts,
+                std::unique_ptr<Run> &R, std::vector<long long> &key) {
+  auto ci = c->colorings.find(cid);
+  if (ci == c->colorings.end()) return CC_ENOTFOUND;
+  const int rc = init_run(c, pid, ci->second, cid, opts, R, key);
+  if (rc) {
+    R.reset();
+    return rc;
+  }
+  ci->second.refs++;  // released by free_run
   return CC_OK;
 }
 
@@ -1293,24 +1091,25 @@ void update_plan(Ctx *c, const std::vector<long long> &key, const Run *R, size_t
 
 // Runs the nodes on the context's stream: planned when a plan exists (repeated exactly if the
 // plan proves too small), exact otherwise; then reads the results and updates the plan.
-int run_direct(Ctx *c, Run *R, const std::vector<long long> &key) {
+int run_direct(Ctx *c, Run *R, const cc::Coloring &col, const std::vector<long long> &key,
+               bool exact_only) {
   const Pattern &P = c->patterns.at(R->pattern);
-  const cc::Coloring &col = c->colorings.at(R->coloring);
   const int N = (int)P.nodes.size();
   int rc = reset_run(c, R, N);
   if (rc) return rc;
   auto pl = c->plans.find(key);
-  R->planned = pl != c->plans.end() && pl->second.runs > 0;
+  R->planned = !exact_only && pl != c->plans.end() && pl->second.runs > 0;
   R->graphed = false;
-  const size_t base = c->arena.in_use();
-  c->arena.reset_high_water();
+  Arena &A = active_arena(c);
+  const size_t base = A.in_use();
+  A.reset_high_water();
   if (R->planned) {
     rc = run_nodes(c, R, P, col, &pl->second);
     if (!rc) rc = finish_run(c, R);
     if (rc == CC_ECAPACITY || rc == CC_ENOMEM) {  // outgrew the plan: plan again, exactly
       R->planned = false;
       rc = reset_run(c, R, N);
-      c->arena.reset_high_water();
+      A.reset_high_water();
       if (!rc) rc = run_nodes(c, R, P, col, nullptr);
       if (!rc) rc = finish_run(c, R);
     }
@@ -1319,7 +1118,7 @@ int run_direct(Ctx *c, Run *R, const std::vector<long long> &key) {
     if (!rc) rc = finish_run(c, R);
   }
   if (rc) return rc;
-  update_plan(c, key, R, c->arena.high_water() - base);
+  update_plan(c, key, R, A.high_water() - base);
   return CC_OK;
 }
 
@@ -1527,7 +1326,7 @@ int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
     }
     if (rc) {  // no graph: run them one by one
       for (size_t m = 0; m < Rs.size(); ++m) {
-        rc = run_direct(c, Rs[m], keys[m]);
+        rc = run_direct(c, Rs[m], c->colorings.at(Rs[m]->coloring), keys[m], false);
         if (rc) return rc;
       }
       return CC_OK;
@@ -1541,7 +1340,7 @@ int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
   }
   drop_graph(c, gkey);
   for (size_t m = 0; m < Rs.size(); ++m) {
-    rc = run_direct(c, Rs[m], keys[m]);
+    rc = run_direct(c, Rs[m], c->colorings.at(Rs[m]->coloring), keys[m], false);
     if (rc) return rc;
   }
   return CC_OK;
@@ -1573,10 +1372,10 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
     rc = run_graphed(c, Rs, keys);
   } else {
     for (int32_t i = 0; i < npat && !rc; ++i) {
-      rc = run_direct(c, Rs[i], keys[i]);
+      rc = run_direct(c, Rs[i], c->colorings.at(Rs[i]->coloring), keys[i], false);
       if (rc == CC_ENOMEM && !c->graphs.empty()) {  // graphs hold memory a direct run needs
         drop_all_graphs(c);
-        rc = run_direct(c, Rs[i], keys[i]);
+        rc = run_direct(c, Rs[i], c->colorings.at(Rs[i]->coloring), keys[i], false);
       }
     }
   }
@@ -1585,7 +1384,10 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
   return CC_OK;
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace cc
+
+using namespace cc::rt;
 
 // ------------------------------------------------------------------------------------------
 // C ABI
@@ -1602,6 +1404,7 @@ const char *cc_strerror(int code) {
     case CC_ECUDA: return "CUDA runtime error";
     case CC_ENOTFOUND: return "unknown id";
     case CC_EKEYWIDTH: return "trial, bag-mapping and colour bits exceed 128";
+    case CC_EBUSY: return "the context is serving";
     default: return "unknown error";
   }
 }
@@ -1661,6 +1464,7 @@ int cc_destroy(cc_ctx *ctx) {
   if (!ctx) return CC_EINVAL;
   Ctx *c = (Ctx *)ctx;
   cc_serve_stop(ctx);
+  cc::serve_free(c);
   cudaStreamSynchronize(c->stream);
   drop_all_graphs(c);
   for (cudaStream_t s : c->branches) cudaStreamDestroy(s);
@@ -1690,6 +1494,7 @@ int cc_check_graph(int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
 
 int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_t *h_col) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c) return CC_EINVAL;
   int vr = cc_check_graph(n, h_row_ptr, h_col);
   if (vr) return vr;
@@ -1793,7 +1598,9 @@ int cc_nice_decomposition(int32_t nF, int32_t mF, const int32_t *h_edges, const 
 int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
                     const cc_td *td, int32_t *pattern_id) {
   Ctx *c = (Ctx *)ctx;
-  if (!c || !pattern_id) return CC_EINVAL;
+  if (!c) return CC_EINVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
+  if (!pattern_id) return CC_EINVAL;
   Pattern P;
   int rc = make_pattern(nF, mF, h_edges, td, P);
   if (rc) return rc;
@@ -1806,6 +1613,7 @@ int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
 int cc_pattern_info(cc_ctx *ctx, int32_t pid, int32_t *num_nodes, int32_t *width) {
   Ctx *c = (Ctx *)ctx;
   if (!c) return CC_EINVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
   auto it = c->patterns.find(pid);
   if (it == c->patterns.end()) return CC_ENOTFOUND;
   if (num_nodes) *num_nodes = (int32_t)it->second.nodes.size();
@@ -1817,6 +1625,7 @@ int cc_pattern_nodes(cc_ctx *ctx, int32_t pid, int32_t *type, int32_t *child0, i
                      int32_t *vertex, int32_t *bag_ptr, int32_t *bag_vtx) {
   Ctx *c = (Ctx *)ctx;
   if (!c) return CC_EINVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
   auto it = c->patterns.find(pid);
   if (it == c->patterns.end()) return CC_ENOTFOUND;
   int32_t off = 0;
@@ -1838,6 +1647,7 @@ int cc_pattern_nodes(cc_ctx *ctx, int32_t pid, int32_t *type, int32_t *child0, i
 
 int cc_color(cc_ctx *ctx, uint64_t seed, int32_t trials, int32_t k, int32_t *cid) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || c->n < 0 || trials < 1 || k < 1 || k > 32 || !cid) return CC_EINVAL;
   cc::Coloring col;
   col.trials = trials;
@@ -1858,6 +1668,7 @@ int cc_color(cc_ctx *ctx, uint64_t seed, int32_t trials, int32_t k, int32_t *cid
 int cc_set_colors(cc_ctx *ctx, const uint8_t *h_colors, int32_t trials, int32_t k,
                   int32_t *cid) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || c->n < 0 || trials < 1 || k < 1 || k > 32 || !cid) return CC_EINVAL;
   size_t total = (size_t)trials * c->n;
   if (total && !h_colors) return CC_EINVAL;
@@ -1879,6 +1690,7 @@ int cc_set_colors(cc_ctx *ctx, const uint8_t *h_colors, int32_t trials, int32_t 
 
 int cc_get_colors(cc_ctx *ctx, int32_t cid, uint8_t *h_out) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !h_out) return CC_EINVAL;
   auto it = c->colorings.find(cid);
   if (it == c->colorings.end()) return CC_ENOTFOUND;
@@ -1892,6 +1704,7 @@ int cc_get_colors(cc_ctx *ctx, int32_t cid, uint8_t *h_out) {
 
 int cc_release_colors(cc_ctx *ctx, int32_t cid) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c) return CC_EINVAL;
   auto it = c->colorings.find(cid);
   if (it == c->colorings.end()) return CC_ENOTFOUND;
@@ -1909,6 +1722,7 @@ int cc_run_dp(cc_ctx *ctx, int32_t pid, int32_t cid, const cc_run_opts *opts, in
 int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *pids, const int32_t *cids,
                  const cc_run_opts *opts, int32_t *run_ids) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || c->n < 0 || npat < 0 || (npat && (!pids || !cids || !run_ids))) return CC_EINVAL;
   if (npat == 0) return CC_OK;
   std::vector<std::unique_ptr<Run>> runs;
@@ -1931,6 +1745,8 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 
 int cc_decide(cc_ctx *ctx, int32_t run_id, uint8_t *h_exists) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !h_exists) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -1944,6 +1760,7 @@ int cc_decide(cc_ctx *ctx, int32_t run_id, uint8_t *h_exists) {
 
 int cc_count(cc_ctx *ctx, int32_t run_id, uint64_t *h_counts) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !h_counts) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -1955,6 +1772,7 @@ int cc_count(cc_ctx *ctx, int32_t run_id, uint64_t *h_counts) {
 
 int cc_table_stats(cc_ctx *ctx, int32_t run_id, uint64_t *h_sizes, uint64_t *h_total) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -1970,6 +1788,7 @@ int cc_table_stats(cc_ctx *ctx, int32_t run_id, uint64_t *h_sizes, uint64_t *h_t
 int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity, int32_t *h_trial,
                   int32_t *h_phi, uint32_t *h_mask, uint64_t *h_cnt, uint64_t *n_out) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !n_out) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -2010,6 +1829,7 @@ int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity, 
 int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, uint64_t *n_out,
                  uint64_t *n_total) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !n_out || !n_total || (limit && !h_out)) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -2020,6 +1840,7 @@ int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, ui
 int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,
                    int32_t *h_kind, float *h_ms, uint64_t *h_cand, int32_t *n_out) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !n_out) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -2040,6 +1861,7 @@ int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_nod
 
 int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
   Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
   if (!c || !mode) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
@@ -2050,6 +1872,7 @@ int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
 int cc_context_stats(cc_ctx *ctx, uint64_t *launches, uint64_t *used, uint64_t *size) {
   Ctx *c = (Ctx *)ctx;
   if (!c) return CC_EINVAL;
+  std::lock_guard<std::mutex> lock(c->mu);
   if (launches) *launches = c->launches;
   if (used) *used = c->arena.size() - c->arena.free_bytes();
   if (size) *size = c->arena.size();

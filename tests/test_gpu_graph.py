@@ -68,7 +68,7 @@ def test_graph_replay_matches_oracle(ctx, fuse):
     replay launches the same kernels and gives the oracle's results."""
     g = synth.barabasi_albert(2500, 4, 21)
     cc.cc_load_graph(ctx.h, *g)
-    for pat in (synth.cycle_pattern(5), synth.grid_pattern(2, 3), synth.pattern_C()):
+    for pat in (synth.cycle_pattern(5), synth.grid_pattern(2, 3), synth.pattern_B()):
         nF = pat[0]
         pid = _load(ctx, pat)
         modes, launched = [], []
@@ -123,7 +123,7 @@ def test_batch_graph_matches_oracle(ctx):
     g = synth.erdos_renyi(n, 6.0 / n, 5)
     cc.cc_load_graph(ctx.h, *g)
     reqs = [(synth.cycle_pattern(5), 5, 3), (synth.grid_pattern(2, 3), 6, 2),
-            (synth.cycle_pattern(5), 5, 3), (synth.pattern_A(), None, 2),
+            (synth.cycle_pattern(5), 5, 3), (synth.pattern_B(), None, 2),
             (synth.star_pattern(4), 7, 1), (synth.cycle_pattern(5), 31, 2)]
     pids = [_load(ctx, r[0]) for r in reqs]
     opts = cc.cc_default_opts(use_graph=1)
