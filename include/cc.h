@@ -287,7 +287,7 @@ int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t tria
 int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
                   uint64_t *h_counts, uint8_t *h_exists, int64_t *latency_ns);
 
-/* Server counters since its creation: queries submitted and completed, the most queries seen
+/* Server counters since it last started: queries submitted and completed, the most queries seen
  * running at once, the most arena bytes they held at once, exact runs (first queries of a key
  * and reruns) and reruns of queries that outgrew their plan.  Any pointer may be NULL.
  * Errors: CC_EINVAL, CC_ENOTFOUND (the context never served). */

@@ -354,6 +354,9 @@ int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight) {
   const size_t free_bytes = c->arena.free_bytes();
   S->budget = mem_budget ? std::min(mem_budget, free_bytes) : free_bytes / 2;
   S->reserved = 0;
+  S->submitted = S->completed = S->exact_runs = S->reruns = 0;
+  S->inflight_max = 0;
+  S->reserved_max = 0;
   cc_default_opts(&S->opts);
   S->slots = std::vector<cc::ServeSlot>(nslots);
   for (auto &sl : S->slots)
