@@ -191,6 +191,82 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def pct(xs, q):
+    """q-th percentile (nearest rank) of a nonempty list."""
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(np.ceil(q / 100.0 * len(xs))) - 1))]
+
+
+def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
+    """Serving workload: the first `count` queries of the seeded Poisson stream over the resident
+    BA n=200000 m=5 graph, submitted at their arrival times to the library's server, then the
+    queries it completed run again one by one through the plain calls (cc_color, cc_run_dp,
+    cc_count) with the results compared bit for bit."""
+    w = synth.WORKLOADS["serve_ba200k"]
+    g = synth.make_graph(w["graph"])
+    stream = synth.serve_stream(w, count)
+    torch.cuda.empty_cache()
+    ctx = cc.Context(arena_bytes=arena_gb << 30)
+    h = ctx.h
+    cc.cc_load_graph(h, *g)
+    pids = {}
+    for q in stream:
+        if q["pattern"] not in pids:
+            pids[q["pattern"]] = cc.cc_load_pattern(h, *synth.make_pattern(q["pattern"]))
+    cc.cc_serve_start(h, budget_gb << 30, slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for q in stream:
+        dt = t0 + q["t"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(cc.cc_serve_submit(h, pids[q["pattern"]], q["seed"], q["trials"], q["k"]))
+    res = {}
+    while len(res) < len(tickets):
+        for i, t in enumerate(tickets):
+            if i not in res:
+                done, status, counts, exists, lat = cc.cc_serve_poll(h, t, stream[i]["trials"])
+                if done:
+                    res[i] = (status, counts, lat)
+        time.sleep(0.0005)
+    stats = cc.cc_serve_stats(h)
+    cc.cc_serve_stop(h)
+    ok = [i for i in range(len(stream)) if res[i][0] == 0]
+    refused = sum(1 for i in range(len(stream)) if res[i][0] == -2)
+    failed = len(stream) - len(ok) - refused
+    lat_ms = [res[i][2] / 1e6 for i in ok]
+    makespan = max(stream[i]["t"] + res[i][2] / 1e9 for i in range(len(stream)))
+    # plain path: the completed queries one after the other, no batching
+    plain_ms, same = [], True
+    for i in ok:
+        q = stream[i]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        cid = cc.cc_color(h, q["seed"], q["trials"], q["k"])
+        run = cc.cc_run_dp(h, pids[q["pattern"]], cid, cc.cc_default_opts())
+        counts = cc.cc_count(h, run, q["trials"])
+        plain_ms.append((time.perf_counter() - t1) * 1e3)
+        same = same and bool(np.array_equal(counts, res[i][1]))
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    return {
+        "workload": "serve_ba200k", "graph": "BA n=200000 m=5 seed 1",
+        "queries": len(stream), "offered_rate_qps": w["rate"],
+        "arrivals_s": stream[-1]["t"], "slots": slots, "budget_gb": budget_gb,
+        "completed": len(ok), "refused_enomem": refused, "failed": failed,
+        "served": {"qps": len(ok) / makespan, "p50_ms": pct(lat_ms, 50),
+                   "p99_ms": pct(lat_ms, 99), "makespan_s": makespan},
+        "plain": {"qps": len(ok) / (sum(plain_ms) / 1e3), "p50_ms": pct(plain_ms, 50),
+                  "p99_ms": pct(plain_ms, 99)},
+        "identical": same, "server": stats,
+        "note": "served latency runs from submission to completion and includes queueing; "
+                "plain latency is one query's call sequence alone, back to back",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +277,9 @@ def main():
     ap.add_argument("--trials", type=int, default=0,
                     help="colouring trials per step (default: the workload's 64); smaller values "
                          "only for small profiling captures")
+    ap.add_argument("--serve-queries", type=int, default=300,
+                    help="queries of the serving stream to run (0: skip the serving leg; the "
+                         "full stream has 2000)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -366,8 +445,11 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0:
+        if args.serve_queries > 0 and world == 1:
+            line["serving"] = serve_leg(cc, torch, args.serve_queries, 200, 160, 8)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -269,7 +269,8 @@ int cc_count_noalloc(int device, void *cuda_stream, int32_t n, const int32_t *h_
  * trials and k) and runs the DP with cc_default_opts inside its own arena range, reserved at
  * admission and trimmed to what its kernels use.  A query whose (pattern, trials, k) has no
  * plan yet runs exactly, synchronously on its slot; later ones of the same key run planned, and
- * one that outgrows its plan runs again exactly.  Results are those of cc_count and cc_decide
+ * one that outgrows its plan runs again exactly.  A query that runs out of memory while running
+ * alone ends with CC_ENOMEM, and later queries of its key are refused with CC_ENOMEM at once.  Results are those of cc_count and cc_decide
  * for the same inputs, whatever else runs.  Errors: CC_EINVAL (no graph, bad max_inflight),
  * CC_EBUSY (already serving), CC_ECUDA. */
 int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight);

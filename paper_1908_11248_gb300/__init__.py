@@ -389,6 +389,7 @@ class Context:
         if getattr(self, "h", None) is not None:
             cc_destroy(self.h)
             self.h = None
+        self.arena = None  # the device memory goes back to PyTorch's allocator
 
     def __enter__(self):
         return self

@@ -151,6 +151,7 @@ struct Plan {
   std::vector<u64> entries, pairs;
   size_t peak_bytes = 0;  // largest arena use of a run beyond what it started with
   int runs = 0;
+  size_t refused = 0;  // a served run of this key ran out of memory in a range this large
 };
 
 struct Timing {

@@ -168,6 +168,13 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
     publish(S, q, CC_ENOTFOUND, {}, {});
     return kDone;
   }
+  {  // a query of this key already ran out of the whole budget: refuse it without running
+    auto pl = c->plans.find(rt::plan_key(c, q.pattern, q.trials, q.k, S->opts));
+    if (pl != c->plans.end() && pl->second.refused >= S->budget) {
+      publish(S, q, CC_ENOMEM, {}, {});
+      return kDone;
+    }
+  }
   if (!reserve(S, c, sl)) {
     if (!alone) return kRetry;
     publish(S, q, CC_ENOMEM, {}, {});
@@ -217,6 +224,10 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
         S->exact_runs++;
       }
       rc = rt::run_direct(c, sl.run.get(), sl.view, sl.key, true);
+      if (rc == CC_ENOMEM && alone) {
+        size_t &r = c->plans[sl.key].refused;
+        r = std::max(r, sl.bytes);
+      }
       std::vector<u64> counts;
       std::vector<uint8_t> exists;
       if (!rc) rc = read_results(c, sl, counts, exists);

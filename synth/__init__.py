@@ -356,7 +356,44 @@ WORKLOADS = {
     # Erdos-Renyi n=100000, average degree 10 (seed 1); 3x3 grid; k=9; 32 trials
     "er100k_grid3x3": dict(graph=("er", 100000, 10.0 / 99999.0, 1), pattern=("grid", 3, 3), k=9,
                            seed=7, trials=32),
+    # serving: Barabasi-Albert n=200000, m=5 (seed 1) resident; 2000 queries, Poisson arrivals
+    # at 200/s (seed 1); families path, cycle, grid, random partial k-tree (k <= 3); n_F = k
+    # uniform in 4..10; one trial per query
+    "serve_ba200k": dict(graph=("ba", 200000, 5, 1), queries=2000, rate=200.0, seed=1,
+                         sizes=(4, 10), trials=1, ktree_pool=2),
 }
+
+GRID_SHAPES = {4: (2, 2), 6: (2, 3), 8: (2, 4), 9: (3, 3), 10: (2, 5)}
+
+
+def serve_stream(spec, count=None):
+    """The query stream of a serving workload: a list of dicts with the arrival time (s), the
+    pattern spec (as make_pattern takes it), k and the colouring seed.  Families are uniform over
+    path, cycle, grid and random partial k-tree; n_F = k is uniform in sizes; a grid family
+    drawn for a size no grid has is drawn again.  Random partial k-trees take k (their width)
+    uniform in 1..min(3, n_F - 1) and a pattern seed from a pool of `ktree_pool` per (n_F, k),
+    so that queries repeat patterns as a served population would."""
+    rng = np.random.default_rng(spec["seed"])
+    lo, hi = spec["sizes"]
+    n = spec["queries"] if count is None else min(count, spec["queries"])
+    out, t = [], 0.0
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / spec["rate"]))
+        nF = int(rng.integers(lo, hi + 1))
+        while True:
+            fam = ("path", "cycle", "grid", "ktree")[int(rng.integers(0, 4))]
+            if fam != "grid" or nF in GRID_SHAPES:
+                break
+        if fam == "grid":
+            pat = ("grid",) + GRID_SHAPES[nF]
+        elif fam == "ktree":
+            w = int(rng.integers(1, min(3, nF - 1) + 1))
+            pat = ("ktree", nF, w, 1000 * nF + 10 * w + int(rng.integers(0, spec["ktree_pool"])))
+        else:
+            pat = (fam, nF)
+        out.append(dict(t=t, pattern=pat, k=nF, seed=int(rng.integers(1, 1 << 62)),
+                        trials=spec["trials"]))
+    return out
 
 
 def make_graph(spec):
