@@ -171,6 +171,25 @@ int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run
 int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *h_pattern_ids,
                  const int32_t *h_coloring_ids, const cc_run_opts *opts, int32_t *h_run_ids);
 
+/* Autotuner: the running time depends on the decomposition supplied rather than on the
+ * treewidth of F (section on obtaining a nice tree decomposition), and beyond its width on the
+ * order of its nodes and on how the node rules are carried out.  Times the
+ * DP of pattern `pattern_id` under colouring `coloring_id` (each candidate: one run that plans,
+ * then the best wall time of `repeats` planned runs, results read back) and picks, by coordinate
+ * descent from *base (NULL: cc_default_opts; retain, profile and use_graph are cleared):
+ *   - the node schedule: the pattern's tree decomposition rooted at each of its bags in turn
+ *     (at most max_schedules distinct nice decompositions, the loaded one first; each other one
+ *     is loaded as a new pattern, which the context keeps);
+ *   - fuse (2, 1, 0), block (256, 128, 512), load_factor (0.5, 0.35, 0.7), sort_sweep (1, 0)
+ *     and group (1, 0), one option at a time.
+ * Every candidate's per-trial counts and exists flags must equal the first's (otherwise
+ * CC_ECUDA).  Out: *best_opts, *best_pattern_id (use it with the options), *best_ms (may be
+ * NULL) and *configs_tried (may be NULL).  Errors: CC_EINVAL, CC_ENOTFOUND, CC_EBUSY, and those
+ * of cc_run_dp. */
+int cc_autotune(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run_opts *base,
+                int32_t max_schedules, int32_t repeats, cc_run_opts *best_opts,
+                int32_t *best_pattern_id, float *best_ms, int32_t *configs_tried);
+
 /* How a run was executed. */
 #define CC_MODE_EXACT 0   /* count passes size every table exactly (first run of a plan key) */
 #define CC_MODE_PLANNED 1 /* capacities from the plan, appends in chunks, no host reads */

@@ -31,7 +31,7 @@ EXPORTS = [
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
-    "cc_serve_stats",
+    "cc_serve_stats", "cc_autotune",
 ]
 RUN_MODES = ["exact", "planned", "graph"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -101,6 +101,7 @@ def lib():
         "cc_check_graph": ([i32, P, P], ctypes.c_int),
         "cc_run_mode": ([P, i32, P], ctypes.c_int),
         "cc_serve_stats": ([P, P, P, P, P, P, P], ctypes.c_int),
+        "cc_autotune": ([P, i32, i32, P, i32, i32, P, P, P, P], ctypes.c_int),
         "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
                              ctypes.c_int),
     }
@@ -312,6 +313,17 @@ def cc_run_timings(ctx, run: int, capacity: int = 4096):
                                 ctypes.byref(n)), "cc_run_timings")
     m = n.value
     return node[:m], kind[:m], ms[:m], cand[:m]
+
+
+def cc_autotune(ctx, pid: int, cid: int, base: cc_run_opts | None = None,
+                max_schedules: int = 8, repeats: int = 2):
+    """(best options, best pattern id, best ms, configurations tried)."""
+    best, bp = cc_run_opts(), ctypes.c_int32(0)
+    ms, n = ctypes.c_float(0), ctypes.c_int32(0)
+    _check(lib().cc_autotune(ctx, pid, cid, ctypes.byref(base) if base is not None else None,
+                             max_schedules, repeats, ctypes.byref(best), ctypes.byref(bp),
+                             ctypes.byref(ms), ctypes.byref(n)), "cc_autotune")
+    return best, bp.value, ms.value, n.value
 
 
 def cc_run_mode(ctx, run: int) -> str:

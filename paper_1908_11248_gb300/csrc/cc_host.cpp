@@ -1384,6 +1384,19 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
   return CC_OK;
 }
 
+int nice_from_td(Pattern &P, const std::vector<std::vector<int>> &bags,
+                 const std::vector<int> &parent) {
+  int root = -1;
+  if (!valid_td(P.adj, P.nF, bags, parent, root)) return CC_EINVAL;
+  P.nodes.clear();
+  build_nice(P.adj, bags, parent, root, P.nodes);
+  P.width = 0;
+  for (auto &nd : P.nodes) P.width = std::max<int>(P.width, (int)nd.bag.size() - 1);
+  P.td_bags = bags;
+  P.td_parent = parent;
+  return CC_OK;
+}
+
 }  // namespace rt
 }  // namespace cc
 
@@ -1562,11 +1575,7 @@ static int make_pattern(int32_t nF, int32_t mF, const int32_t *h_edges, const cc
     std::vector<int> order = nF <= 20 ? exact_order(P.adj, nF) : min_fill_order(P.adj, nF);
     td_from_order(P.adj, nF, order, bags, parent);
   }
-  int root = -1;
-  if (!valid_td(P.adj, nF, bags, parent, root)) return CC_EINVAL;
-  build_nice(P.adj, bags, parent, root, P.nodes);
-  for (auto &nd : P.nodes) P.width = std::max<int>(P.width, (int)nd.bag.size() - 1);
-  return CC_OK;
+  return nice_from_td(P, bags, parent);
 }
 
 int cc_nice_decomposition(int32_t nF, int32_t mF, const int32_t *h_edges, const cc_td *td,

@@ -125,6 +125,9 @@ struct Pattern {
   std::vector<int32_t> deg;
   std::vector<NiceNode> nodes;  // post-order, root last
   int32_t width = 0;
+  // the tree decomposition the nice one was built from (given, or computed)
+  std::vector<std::vector<int>> td_bags;
+  std::vector<int> td_parent;
 };
 
 struct Coloring {
@@ -275,6 +278,13 @@ int run_direct(Ctx *c, Run *R, const Coloring &col, const std::vector<long long>
                bool exact_only);
 // Destroys every captured graph and gives back its memory.
 void drop_all_graphs(Ctx *c);
+// Checks the tree decomposition (bags, parent) of P's graph (P.nF, P.adj set) and builds P's
+// nice decomposition from it.  CC_EINVAL if it is not a tree decomposition of F.
+int nice_from_td(Pattern &P, const std::vector<std::vector<int>> &bags,
+                 const std::vector<int> &parent);
+// Runs (pattern, colouring) requests with one set of options (cc_run_batch without ids).
+int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
+              const cc_run_opts *opts, std::vector<std::unique_ptr<Run>> &out);
 
 }  // namespace rt
 }  // namespace cc
