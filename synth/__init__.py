@@ -39,6 +39,17 @@ def csr_from_edges(n: int, edges: np.ndarray):
     return row_ptr.astype(np.int32), dst.astype(np.int32)
 
 
+def plant(graph, pattern_edges, vertices):
+    """The graph with a copy of a pattern added: pattern vertex i becomes graph vertex
+    vertices[i] and every pattern edge becomes an edge (existing ones are kept once)."""
+    row_ptr, col = graph
+    n = len(row_ptr) - 1
+    v = np.asarray(vertices, dtype=np.int64)
+    pe = np.asarray(pattern_edges, dtype=np.int64).reshape(-1, 2)
+    extra = np.stack([v[pe[:, 0]], v[pe[:, 1]]], axis=1)
+    return csr_from_edges(n, np.concatenate([edges_from_csr(row_ptr, col), extra]))
+
+
 def edges_from_csr(row_ptr, col):
     """Each undirected edge once, as (u, v) with u < v, in CSR order."""
     n = len(row_ptr) - 1

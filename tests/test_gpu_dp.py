@@ -298,6 +298,68 @@ def test_workload_ba20k_grid2x4_sampled(ctx):
     release(ctx, r1)
 
 
+def test_workload_er100k_grid3x3_planted(ctx):
+    """Erdos-Renyi n=100000, average degree 10 (seed 1); 3x3 grid (treewidth 3, 128-bit keys);
+    k=9; 32 trials in one run, enumeration limited to 10^5.  A grid copy is planted on nine
+    vertices that trial 0 colours 0..8 (otherwise the expected number of colourful copies is
+    about 10^-3 and every count is 0).  Trial 0 against the oracle (count and every node's table
+    size); every count is a multiple of |Aut(G_{3,3})| = 8.  The embeddings of all trials are
+    those of the trials whose root table is nonempty, so the list (limit 10^5) comes from a run
+    that keeps the tables of those trials only (keeping all 32 trials' tables would take about
+    100 GB): it is sorted, distinct, valid, colourful in some trial and contains the oracle's
+    list of trial 0."""
+    w = synth.WORKLOADS["er100k_grid3x3"]
+    n, T, k = 100000, 32, 9
+    nF, pe, td = synth.make_pattern(w["pattern"])
+    rng = np.random.default_rng(5)
+    vs = rng.choice(n, size=nF, replace=False)
+    g = synth.plant(synth.make_graph(w["graph"]), pe, vs)
+    z = oracle.colors(n, T, k, w["seed"])
+    z[0, vs] = np.arange(nF, dtype=np.uint8)
+    big = cc.Context(arena_bytes=220 << 30)
+    try:
+        cc.cc_load_graph(big.h, *g)
+        pid = cc.cc_load_pattern(big.h, nF, pe, td)
+        N, width = cc.cc_pattern_info(big.h, pid)
+        assert width == 3
+        cid = cc.cc_set_colors(big.h, z, k)
+        run = cc.cc_run_dp(big.h, pid, cid, cc.cc_default_opts())
+        counts = cc.cc_count(big.h, run, T)
+        exists = cc.cc_decide(big.h, run, T)
+        cc.cc_release(big.h, run)
+        sel = np.nonzero(exists)[0]
+        cids = cc.cc_set_colors(big.h, z[sel], k)
+        runs = cc.cc_run_dp(big.h, pid, cids, cc.cc_default_opts(retain=1))
+        assert np.array_equal(cc.cc_count(big.h, runs, len(sel)), counts[sel])
+        lst, total = cc.cc_enumerate(big.h, runs, 100000, nF)
+        cc.cc_release(big.h, runs)
+        cid0 = cc.cc_set_colors(big.h, z[:1], k)
+        run0 = cc.cc_run_dp(big.h, pid, cid0, cc.cc_default_opts())
+        sizes0 = cc.cc_table_stats(big.h, run0, N)[0]
+        count0 = cc.cc_count(big.h, run0, 1)
+        cc.cc_release(big.h, run0)
+    finally:
+        big.close()
+    ref = oracle.run_dp(g, (nF, pe, td), z[:1], k)
+    assert int(counts[0]) == int(ref.count[0]) == int(count0[0]) and int(counts[0]) >= 8
+    assert np.array_equal(sizes0, ref.node_sizes[0])
+    assert all(int(c) % 8 == 0 for c in counts)
+    assert np.array_equal(exists, (counts > 0).astype(np.uint8))
+    # the list: sorted, distinct, valid and colourful in some trial
+    assert total == len(lst) and total >= int(counts[0])
+    rows = [tuple(int(x) for x in r) for r in lst]
+    assert rows == sorted(set(rows))
+    row_ptr, col = g
+    for phi in rows:
+        assert len(set(phi)) == nF
+        for a, b in np.asarray(pe).reshape(-1, 2):
+            u, v = phi[a], phi[b]
+            assert v in col[row_ptr[u]:row_ptr[u + 1]]
+        assert any(len(set(int(z[t, x]) for x in phi)) == nF for t in sel)
+    want = {tuple(int(x) for x in r) for r in ref.enumerate(100000)[0]}
+    assert want <= set(rows)
+
+
 def test_planned_runs_match_exact(ctx):
     """A second run of the same pattern, graph, trials and colours uses the capacities planned
     by the first (no count passes): results and table sizes are unchanged."""
