@@ -153,8 +153,11 @@ void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in
  * the same launches: the trial index is part of every table key).  Requires k >= n_F.  On
- * success *run_id names the result; per-trial results stay on the device until read.
- * Errors: CC_EINVAL, CC_ENOTFOUND, CC_ENOMEM (arena too small: nothing is kept),
+ * success *run_id names the result; per-trial results stay on the device until read.  When all
+ * trials together do not fit the arena and no tables are to be kept (retain 0), the trials run in
+ * halves, recursively, until they fit (trial streaming; cc_run_mode gives CC_MODE_STREAMED).
+ * Errors: CC_EINVAL, CC_ENOTFOUND, CC_ENOMEM (arena too small even for one trial: nothing is
+ * kept),
  * CC_EKEYWIDTH (ceil(log2 trials) + width_bags * ceil(log2 n) + k > 128), CC_ECUDA. */
 int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run_opts *opts,
               int32_t *run_id);
@@ -194,6 +197,9 @@ int cc_autotune(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_r
 #define CC_MODE_EXACT 0   /* count passes size every table exactly (first run of a plan key) */
 #define CC_MODE_PLANNED 1 /* capacities from the plan, appends in chunks, no host reads */
 #define CC_MODE_GRAPH 2   /* planned, replayed from a captured CUDA graph */
+#define CC_MODE_STREAMED 3 /* all trials together did not fit: ran in chunks of trials (halved
+                            * until they fit); counts, exists flags and table sizes as for one
+                            * run, no tables kept */
 
 /* *mode = one of CC_MODE_* for run `run_id`.  Errors: CC_EINVAL, CC_ENOTFOUND. */
 int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode);

@@ -33,7 +33,7 @@ EXPORTS = [
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
     "cc_serve_stats", "cc_autotune",
 ]
-RUN_MODES = ["exact", "planned", "graph"]
+RUN_MODES = ["exact", "planned", "graph", "streamed"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
                 "join_build", "join_count", "join_write", "root", "sort", "reduce"]
 

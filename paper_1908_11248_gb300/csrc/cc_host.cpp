@@ -1349,6 +1349,55 @@ int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
 // Prepares and runs the requests (pids[i], cids[i]) with one set of options: from a captured
 // graph when eligible (one branch per request), else one after the other on the context's
 // stream.  On failure every run made so far is freed.
+// Trials [t0, t0 + nt) of run R as a run of their own over their rows of the colouring; if
+// they do not fit either, each half in turn.  Per-trial results do not depend on the other
+// trials, so the chunk's exists flags and counts are R's, and table sizes add over chunks.
+int run_chunk(Ctx *c, Run *R, const cc::Coloring &col, int32_t t0, int32_t nt) {
+  cc::Coloring view;
+  view.trials = nt;
+  view.k = col.k;
+  view.d_colors = col.d_colors + (size_t)t0 * (size_t)c->n;
+  std::unique_ptr<Run> S;
+  std::vector<long long> key;
+  int rc = init_run(c, R->pattern, view, -1, &R->opts, S, key);
+  if (rc) return rc;
+  rc = run_direct(c, S.get(), view, key, false);
+  if (!rc) {
+    if (cudaMemcpyAsync(R->d_exists + t0, S->d_exists, nt * sizeof(unsigned),
+                        cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(R->d_count + t0, S->d_count, nt * sizeof(u64), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      rc = CC_ECUDA;
+    for (size_t x = 0; x < R->sizes.size() && !rc; ++x) {
+      R->sizes[x] += S->sizes[x];
+      R->pairs[x] = std::max(R->pairs[x], S->pairs[x]);
+    }
+  }
+  free_run(c, S.get());
+  if (rc == CC_ENOMEM && nt > 1) {
+    const int32_t h = nt / 2;
+    rc = run_chunk(c, R, col, t0, h);
+    if (!rc) rc = run_chunk(c, R, col, t0 + h, nt - h);
+  }
+  return rc;
+}
+
+// Runs R's trials in chunks after all of them together ran out of memory (trial streaming).
+int run_streamed(Ctx *c, Run *R, const cc::Coloring &col) {
+  const int N = (int)c->patterns.at(R->pattern).nodes.size();
+  int rc = reset_run(c, R, N);
+  if (rc) return rc;
+  R->sizes.assign(N, 0);
+  R->pairs.assign(N, 0);
+  R->planned = R->graphed = false;
+  R->streamed = true;
+  const int32_t h = R->trials / 2;
+  rc = run_chunk(c, R, col, 0, h);
+  if (!rc) rc = run_chunk(c, R, col, h, R->trials - h);
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CC_ECUDA;
+  return rc;
+}
+
 int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
               const cc_run_opts *opts, std::vector<std::unique_ptr<Run>> &out) {
   std::vector<std::unique_ptr<Run>> runs(npat);
@@ -1377,6 +1426,8 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
         drop_all_graphs(c);
         rc = run_direct(c, Rs[i], c->colorings.at(Rs[i]->coloring), keys[i], false);
       }
+      if (rc == CC_ENOMEM && Rs[i]->trials > 1 && !Rs[i]->retained)
+        rc = run_streamed(c, Rs[i], c->colorings.at(Rs[i]->coloring));
     }
   }
   if (rc) return fail(rc);
@@ -1874,7 +1925,10 @@ int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
   if (!c || !mode) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
-  *mode = R->graphed ? CC_MODE_GRAPH : R->planned ? CC_MODE_PLANNED : CC_MODE_EXACT;
+  *mode = R->streamed  ? CC_MODE_STREAMED
+          : R->graphed ? CC_MODE_GRAPH
+          : R->planned ? CC_MODE_PLANNED
+                       : CC_MODE_EXACT;
   return CC_OK;
 }
 

@@ -180,6 +180,7 @@ struct Run {
   bool retained = false;
   bool planned = false;
   bool graphed = false;
+  bool streamed = false;  // its trials ran in chunks (all at once did not fit)
   u64 *d_blk = nullptr;  // per-run scratch: block counts and bases, pair counters
   int *d_err = nullptr;  // per-run device error word
   Arena *home = nullptr;  // the arena its memory came from (null: the context's)

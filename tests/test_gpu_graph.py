@@ -186,3 +186,43 @@ def test_graph_dropped_on_new_graph(ctx):
             cc.cc_release(ctx.h, run)
             cc.cc_release_colors(ctx.h, cid)
         assert modes == want
+
+
+def test_trials_stream_when_memory_is_short(ctx):
+    """In an arena too small for all 16 trials at once, a run without kept tables splits the
+    trials into chunks that fit; counts, exists flags and table sizes are those of the run in a
+    large arena (and of the oracle on a sample)."""
+    g = synth.barabasi_albert(3000, 4, 13)
+    pat = synth.grid_pattern(2, 3)
+    z = oracle.colors(3000, 16, 6, seed=21)
+    cc.cc_load_graph(ctx.h, *g)
+    pid = _load(ctx, pat)
+    cid = cc.cc_set_colors(ctx.h, z, 6)
+    run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
+    N, _ = cc.cc_pattern_info(ctx.h, pid)
+    want = (cc.cc_count(ctx.h, run, 16), cc.cc_decide(ctx.h, run, 16),
+            cc.cc_table_stats(ctx.h, run, N)[0])
+    assert cc.cc_run_mode(ctx.h, run) == "exact"
+    cc.cc_release(ctx.h, run)
+    cc.cc_release_colors(ctx.h, cid)
+    small = cc.Context(arena_bytes=96 << 20)
+    try:
+        cc.cc_load_graph(small.h, *g)
+        spid = cc.cc_load_pattern(small.h, *pat)
+        scid = cc.cc_set_colors(small.h, z, 6)
+        with pytest.raises(cc.CCError) as e:  # tables kept: no streaming, nothing kept
+            cc.cc_run_dp(small.h, spid, scid, cc.cc_default_opts(retain=1))
+        assert e.value.code == -2
+        used = cc.cc_context_stats(small.h)[1]
+        for _ in range(2):
+            srun = cc.cc_run_dp(small.h, spid, scid, cc.cc_default_opts())
+            assert cc.cc_run_mode(small.h, srun) == "streamed"
+            assert np.array_equal(cc.cc_count(small.h, srun, 16), want[0])
+            assert np.array_equal(cc.cc_decide(small.h, srun, 16), want[1])
+            assert np.array_equal(cc.cc_table_stats(small.h, srun, N)[0], want[2])
+            cc.cc_release(small.h, srun)
+        assert cc.cc_context_stats(small.h)[1] == used
+    finally:
+        small.close()
+    ref = oracle.run_dp(g, pat, z[:2], 6)
+    assert np.array_equal(want[0][:2], ref.count)
