@@ -226,3 +226,50 @@ def test_trials_stream_when_memory_is_short(ctx):
         small.close()
     ref = oracle.run_dp(g, pat, z[:2], 6)
     assert np.array_equal(want[0][:2], ref.count)
+
+
+def test_batch_of_partial_3trees(ctx):
+    """The batched-patterns configuration at small scale: an erased power-law configuration
+    graph (n=2000, exponent 2.5, mean degree 8) and 16 random partial 3-trees of 10-12 vertices,
+    k = n_F, 4 trials each: single runs plan every request, then the batch is captured and
+    replayed as one CUDA graph of 16 branches.  Every request equals its own single run, and the
+    three smallest equal the oracle on trial 0."""
+    n, T = 2000, 4
+    g = synth.power_law_config(n, 8.0, 2.5, 1)
+    rng = np.random.default_rng(1)
+    pats = []
+    for i in range(16):
+        nF = int(rng.integers(10, 13))
+        pats.append(synth.random_partial_ktree(nF, 3, 7000 + i))
+    big = cc.Context(arena_bytes=64 << 30)
+    try:
+        h = big.h
+        cc.cc_load_graph(h, *g)
+        pids = [cc.cc_load_pattern(h, *p) for p in pats]
+        zs = [oracle.colors(n, T, p[0], seed=300 + i) for i, p in enumerate(pats)]
+        opts = cc.cc_default_opts(use_graph=1)
+        singles, sizes = [], []
+        for pid, z, p in zip(pids, zs, pats):
+            cid = cc.cc_set_colors(h, z, p[0])
+            run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts())
+            N, _ = cc.cc_pattern_info(h, pid)
+            singles.append(cc.cc_count(h, run, T))
+            sizes.append(cc.cc_table_stats(h, run, N)[0])
+            cc.cc_release(h, run)
+            cc.cc_release_colors(h, cid)
+        for rep in range(2):  # the single runs planned every request: graph at once
+            cids = [cc.cc_set_colors(h, z, p[0]) for z, p in zip(zs, pats)]
+            runs = cc.cc_run_batch(h, pids, cids, opts)
+            for i, run in enumerate(runs):
+                N, _ = cc.cc_pattern_info(h, pids[i])
+                assert cc.cc_run_mode(h, run) == "graph"
+                assert np.array_equal(cc.cc_count(h, run, T), singles[i]), i
+                assert np.array_equal(cc.cc_table_stats(h, run, N)[0], sizes[i]), i
+                cc.cc_release(h, run)
+            for cid in cids:
+                cc.cc_release_colors(h, cid)
+    finally:
+        big.close()
+    for i in sorted(range(16), key=lambda i: int(sizes[i].sum()))[:3]:
+        ref = oracle.run_dp(g, pats[i], zs[i][:1], pats[i][0])
+        assert int(ref.count[0]) == int(singles[i][0]), i
