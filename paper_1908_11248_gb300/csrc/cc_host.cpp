@@ -1306,49 +1306,6 @@ int replay_graph(Ctx *c, cc::GraphSet &gs, const std::vector<Run *> &Rs) {
   return worst;
 }
 
-// Runs Rs (prepared, with plan keys `keys`) from a captured graph, capturing it on first use.
-// A member that outgrew the graph's capacities makes the graph stale: it is dropped and every
-// member runs again directly (planned, then exactly if need be), which also updates the plans.
-int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
-                const std::vector<std::vector<long long>> &keys) {
-  std::vector<long long> gkey;
-  for (size_t m = 0; m < Rs.size(); ++m) {
-    gkey.insert(gkey.end(), keys[m].begin(), keys[m].end());
-    gkey.push_back(-1);
-  }
-  auto it = c->graphs.find(gkey);
-  if (it == c->graphs.end()) {
-    std::unique_ptr<cc::GraphSet> gs;
-    int rc = capture_graph(c, Rs, keys, gs);
-    if (rc == CC_ENOMEM && !c->graphs.empty()) {
-      drop_all_graphs(c);
-      rc = capture_graph(c, Rs, keys, gs);
-    }
-    if (rc) {  // no graph: run them one by one
-      for (size_t m = 0; m < Rs.size(); ++m) {
-        rc = run_direct(c, Rs[m], c->colorings.at(Rs[m]->coloring), keys[m], false);
-        if (rc) return rc;
-      }
-      return CC_OK;
-    }
-    it = c->graphs.emplace(gkey, std::move(gs)).first;
-  }
-  int rc = replay_graph(c, *it->second, Rs);
-  if (rc == CC_OK) {
-    for (size_t m = 0; m < Rs.size(); ++m) update_plan(c, keys[m], Rs[m], 0);
-    return CC_OK;
-  }
-  drop_graph(c, gkey);
-  for (size_t m = 0; m < Rs.size(); ++m) {
-    rc = run_direct(c, Rs[m], c->colorings.at(Rs[m]->coloring), keys[m], false);
-    if (rc) return rc;
-  }
-  return CC_OK;
-}
-
-// Prepares and runs the requests (pids[i], cids[i]) with one set of options: from a captured
-// graph when eligible (one branch per request), else one after the other on the context's
-// stream.  On failure every run made so far is freed.
 // Trials [t0, t0 + nt) of run R as a run of their own over their rows of the colouring; if
 // they do not fit either, each half in turn.  Per-trial results do not depend on the other
 // trials, so the chunk's exists flags and counts are R's, and table sizes add over chunks.
@@ -1398,6 +1355,71 @@ int run_streamed(Ctx *c, Run *R, const cc::Coloring &col) {
   return rc;
 }
 
+// Runs R to completion on the context's stream without a graph: planned or exact, after giving
+// back the memory of captured graphs if that is what it lacks, and in chunks of trials if all
+// trials together do not fit.
+int run_one(Ctx *c, Run *R, const std::vector<long long> &key) {
+  const cc::Coloring &col = c->colorings.at(R->coloring);
+  int rc = run_direct(c, R, col, key, false);
+  if (rc == CC_ENOMEM && !c->graphs.empty()) {
+    drop_all_graphs(c);
+    rc = run_direct(c, R, col, key, false);
+  }
+  if (rc == CC_ENOMEM && R->trials > 1 && !R->retained) rc = run_streamed(c, R, col);
+  return rc;
+}
+
+// Runs Rs (prepared, with plan keys `keys`) from a captured graph, capturing it on first use.
+// A member that outgrew the graph's capacities makes the graph stale: it is dropped and every
+// member runs again directly (planned, then exactly if need be), which also updates the plans.
+int run_graphed(Ctx *c, const std::vector<Run *> &Rs,
+                const std::vector<std::vector<long long>> &keys) {
+  std::vector<long long> gkey;
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    gkey.insert(gkey.end(), keys[m].begin(), keys[m].end());
+    gkey.push_back(-1);
+  }
+  auto it = c->graphs.find(gkey);
+  if (it == c->graphs.end()) {
+    std::unique_ptr<cc::GraphSet> gs;
+    int rc = capture_graph(c, Rs, keys, gs);
+    if (rc == CC_ENOMEM && !c->graphs.empty()) {  // older graphs hold the memory: drop them
+      drop_all_graphs(c);
+      rc = capture_graph(c, Rs, keys, gs);
+    }
+    if (rc == CC_ENOMEM && Rs.size() > 1) {  // too much at once: each half as a graph of its own
+      const size_t h = Rs.size() / 2;
+      const std::vector<Run *> R0(Rs.begin(), Rs.begin() + h), R1(Rs.begin() + h, Rs.end());
+      const std::vector<std::vector<long long>> K0(keys.begin(), keys.begin() + h),
+          K1(keys.begin() + h, keys.end());
+      rc = run_graphed(c, R0, K0);
+      return rc ? rc : run_graphed(c, R1, K1);
+    }
+    if (rc) {  // no graph: run them one by one
+      for (size_t m = 0; m < Rs.size(); ++m) {
+        rc = run_one(c, Rs[m], keys[m]);
+        if (rc) return rc;
+      }
+      return CC_OK;
+    }
+    it = c->graphs.emplace(gkey, std::move(gs)).first;
+  }
+  int rc = replay_graph(c, *it->second, Rs);
+  if (rc == CC_OK) {
+    for (size_t m = 0; m < Rs.size(); ++m) update_plan(c, keys[m], Rs[m], 0);
+    return CC_OK;
+  }
+  drop_graph(c, gkey);
+  for (size_t m = 0; m < Rs.size(); ++m) {
+    rc = run_one(c, Rs[m], keys[m]);
+    if (rc) return rc;
+  }
+  return CC_OK;
+}
+
+// Prepares and runs the requests (pids[i], cids[i]) with one set of options: from a captured
+// graph when eligible (one branch per request), else one after the other on the context's
+// stream.  On failure every run made so far is freed.
 int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
               const cc_run_opts *opts, std::vector<std::unique_ptr<Run>> &out) {
   std::vector<std::unique_ptr<Run>> runs(npat);
@@ -1420,15 +1442,7 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
   if (graph_eligible(c, Rs, keys)) {
     rc = run_graphed(c, Rs, keys);
   } else {
-    for (int32_t i = 0; i < npat && !rc; ++i) {
-      rc = run_direct(c, Rs[i], c->colorings.at(Rs[i]->coloring), keys[i], false);
-      if (rc == CC_ENOMEM && !c->graphs.empty()) {  // graphs hold memory a direct run needs
-        drop_all_graphs(c);
-        rc = run_direct(c, Rs[i], c->colorings.at(Rs[i]->coloring), keys[i], false);
-      }
-      if (rc == CC_ENOMEM && Rs[i]->trials > 1 && !Rs[i]->retained)
-        rc = run_streamed(c, Rs[i], c->colorings.at(Rs[i]->coloring));
-    }
+    for (int32_t i = 0; i < npat && !rc; ++i) rc = run_one(c, Rs[i], keys[i]);
   }
   if (rc) return fail(rc);
   out = std::move(runs);
