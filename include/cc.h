@@ -163,13 +163,14 @@ int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run
               int32_t *run_id);
 
 /* Runs several (pattern, colouring) DPs with one set of options (the batched execution of
- * Section 5's many queries over one graph).  With opts->use_graph, retain 0 and profile 0, once
- * every request has been planned (an earlier run of the same pattern, graph content, trials,
- * colours and options), the requests run as parallel branches of one captured CUDA graph, each
- * in device memory reserved for the graph; the graph is kept per request list and replayed, its
- * colours copied in first.  A request that outgrows the graph's capacities makes the library
- * drop the graph and run every request again directly.  Otherwise the requests run one after the
- * other on the context's stream.  h_run_ids[npat] out; on error no run is kept.  Errors as
+ * Section 5's many queries over one graph).  With opts->use_graph, retain 0 and profile 0, the
+ * requests that have been planned (an earlier run of the same pattern, graph content, trials,
+ * colours and options) run as parallel branches of captured CUDA graphs (up to 64 branches a
+ * graph; a set whose memory does not fit at once is split in halves), each branch in device
+ * memory reserved for its graph; a graph is kept per request list and replayed, its colours
+ * copied in first.  A request that outgrows its graph's capacities makes the library drop the
+ * graph and run its requests again directly.  The other requests run one after the other on the
+ * context's stream (which plans them).  h_run_ids[npat] out; on error no run is kept.  Errors as
  * cc_run_dp. */
 int cc_run_batch(cc_ctx *ctx, int32_t npat, const int32_t *h_pattern_ids,
                  const int32_t *h_coloring_ids, const cc_run_opts *opts, int32_t *h_run_ids);

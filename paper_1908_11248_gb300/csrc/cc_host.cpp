@@ -1138,18 +1138,11 @@ void drop_all_graphs(Ctx *c) {
   }
 }
 
-// Graph replay is taken for runs that keep no tables and time nothing, once every member has
-// a plan.
-bool graph_eligible(Ctx *c, const std::vector<Run *> &Rs,
-                    const std::vector<std::vector<long long>> &keys) {
-  if (Rs.empty() || Rs.size() > 64) return false;
-  for (size_t m = 0; m < Rs.size(); ++m) {
-    const Run *R = Rs[m];
-    if (!R->opts.use_graph || R->opts.retain || R->opts.profile) return false;
-    auto pl = c->plans.find(keys[m]);
-    if (pl == c->plans.end() || pl->second.runs == 0) return false;
-  }
-  return true;
+// Graph replay is taken for a run that keeps no tables and times nothing, once it has a plan.
+bool graph_eligible(Ctx *c, const Run *R, const std::vector<long long> &key) {
+  if (!R->opts.use_graph || R->opts.retain || R->opts.profile) return false;
+  auto pl = c->plans.find(key);
+  return pl != c->plans.end() && pl->second.runs > 0;
 }
 
 // Captures the planned runs of Rs as one CUDA graph: member m runs on branch stream m (on the
@@ -1438,12 +1431,26 @@ int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
     }
     Rs[i] = runs[i].get();
   }
+  // requests with a plan run from captured graphs (at most 64 branches a graph), the others
+  // directly, which plans them for the next call
   int rc = CC_OK;
-  if (graph_eligible(c, Rs, keys)) {
-    rc = run_graphed(c, Rs, keys);
-  } else {
-    for (int32_t i = 0; i < npat && !rc; ++i) rc = run_one(c, Rs[i], keys[i]);
+  std::vector<Run *> G;
+  std::vector<std::vector<long long>> GK;
+  auto flush = [&]() {
+    if (!rc && !G.empty()) rc = run_graphed(c, G, GK);
+    G.clear();
+    GK.clear();
+  };
+  for (int32_t i = 0; i < npat && !rc; ++i) {
+    if (graph_eligible(c, Rs[i], keys[i])) {
+      G.push_back(Rs[i]);
+      GK.push_back(keys[i]);
+      if (G.size() == 64) flush();
+    } else {
+      rc = run_one(c, Rs[i], keys[i]);
+    }
   }
+  flush();
   if (rc) return fail(rc);
   out = std::move(runs);
   return CC_OK;

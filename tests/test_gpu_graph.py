@@ -273,6 +273,17 @@ def test_batch_of_partial_3trees(ctx):
                 cc.cc_release(h, run)
             for cid in cids:
                 cc.cc_release_colors(h, cid)
+        # all 16 at once: the requests with a plan run from graphs, the large ones (whose single
+        # runs went exactly or in chunks of trials) directly, with the same results
+        cids = [cc.cc_set_colors(h, z, p[0]) for z, p in zip(zs, pats)]
+        runs = cc.cc_run_batch(h, pids, cids, opts)
+        for i, run in enumerate(runs):
+            if i in sel:
+                assert cc.cc_run_mode(h, run) == "graph"
+            assert np.array_equal(cc.cc_count(h, run, T), singles[i]), i
+            cc.cc_release(h, run)
+        for cid in cids:
+            cc.cc_release_colors(h, cid)
     finally:
         big.close()
     for i in sorted(range(16), key=lambda i: int(sizes[i].sum()))[:3]:
