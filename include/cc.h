@@ -144,7 +144,9 @@ typedef struct {
   int32_t group;         /* 1: an introduce whose vertex has >= 2 bag neighbours first sorts   */
                          /*    its child by their images and shares candidate lists per run    */
   int32_t sort_sweep;    /* 1: radix sorts take all digit counts in one read and one kernel   */
-                         /*    per pass (decoupled look-back); 0: histogram+scan+scatter passes */
+                         /*    per pass (decoupled look-back); 2: as 1, each block bringing its */
+                         /*    next tile into shared memory by bulk copy while it works on the  */
+                         /*    current one; 0: histogram+scan+scatter passes                    */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor

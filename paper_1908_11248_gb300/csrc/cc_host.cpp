@@ -501,6 +501,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     sw.tile_ctr = arena_alloc<unsigned>(c, 16);
     sw.status = arena_alloc<u64>(c, 256 * sw.max_tiles);
     sw.err = R->d_err;
+    sw.tma = R->opts.sort_sweep == 2;
     if (!ba || !bb || !hist || !sw.ghist || !sw.tile_ctr || !sw.status) {
       A.release(ba);
       A.release(bb);
@@ -1522,6 +1523,10 @@ int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t aren
     return CC_ECUDA;
   }
   c->dev.blocks_per_sm = 8;
+  if (cc::prepare_sort_kernels() != 0) {
+    delete c;
+    return CC_ECUDA;
+  }
   char *base = (char *)d_arena;
   if (!base) {
     if (cudaMalloc(&c->owned_arena, arena_bytes) != cudaSuccess) {

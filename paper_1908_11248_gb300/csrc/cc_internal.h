@@ -146,8 +146,12 @@ struct SweepScratch {
   unsigned long long *status;
   unsigned long long max_tiles;
   int *err;
+  int tma;  // 1: passes stream their next tile into shared memory by bulk copy
 };
 int sweep_tile(int kw);
+// Lets the bulk-copy sort passes use more than 48 KB of shared memory; call once per device
+// before the first sort (returns a cudaError_t as int).
+int prepare_sort_kernels();
 // The record counts live on the device: the first pass scans min(*n_src, src_cap) slots of
 // src (holes skipped), later passes *n records.  buf_a / buf_b hold buf_cap records.
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,

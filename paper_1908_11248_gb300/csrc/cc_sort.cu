@@ -359,6 +359,211 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
   }
 }
 
+// ---- one pass with the next tile's records streamed in by the tensor memory accelerator ----
+// The same ranking and look-back as sweep_pass_kernel, but a block claims its next tile as soon
+// as it starts the current one and has the bulk-copy engine (cp.async.bulk) bring that tile's
+// records into a second shared buffer meanwhile, so reads stay in flight while the block ranks,
+// waits on its predecessors and writes out.  The current tile's buffer then serves as the
+// staging area of its own scatter.  Waits on the copy barrier are bounded like the look-back.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+// thread 0: arm the barrier for `bytes` and copy them from global src to shared dst
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, u64 *bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// true once the barrier's phase `parity` has completed; false after kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned parity) {
+  for (unsigned spins = 0; spins < kSpinLimit; ++spins) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <typename K, typename SK, int ITEMS, bool FROM_KEY, bool STORE_S>
+__global__ void __launch_bounds__(256, 3) sweep_pass_tma_kernel(SortSpec sp, const void *src,
+                                                               const u64 *n_ptr, u64 n_cap,
+                                                               int shift, u64 epoch,
+                                                               const u64 *bases, u64 *status,
+                                                               unsigned *tile_ctr, void *dst,
+                                                               u64 dst_cap, int *err) {
+  constexpr int BLOCK = 256, W = BLOCK / 32, TILE = BLOCK * ITEMS, PER_WARP = 32 * ITEMS;
+  extern __shared__ __align__(128) unsigned char s_dyn[];  // two tiles of records
+  Slot<K> *const s_buf0 = reinterpret_cast<Slot<K> *>(s_dyn);
+  __shared__ __align__(8) u64 s_bar[2];
+  __shared__ unsigned char s_sdig[TILE];
+  __shared__ unsigned s_wc[W][256];
+  __shared__ unsigned s_tstart[256], s_wsum[W];
+  __shared__ u64 s_excl[256];
+  __shared__ u64 s_tile[2];
+  __shared__ unsigned s_tcount;
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const u64 n = min(*n_ptr, n_cap);
+  const u64 tiles = (n + TILE - 1) / TILE;
+  const u64 base_d = bases[tid];
+  auto tile_bytes = [&](u64 t) {
+    return (unsigned)(min((u64)TILE, n - t * TILE) * sizeof(Slot<K>));
+  };
+  for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const u64 t = atomicAdd(tile_ctr, 1u);
+    s_tile[0] = t;
+    if (t < tiles) bulk_load(s_buf0, in + t * TILE, tile_bytes(t), &s_bar[0]);
+  }
+  __syncthreads();
+  unsigned phase = 0u;    // bit b: parity of buffer b's next copy
+  unsigned pending = s_tile[0] < tiles ? 1u : 0u;  // bit b: a copy into b not yet waited for
+  int cur = 0;
+  while (true) {
+    const u64 tile = s_tile[cur];
+    if (tile >= tiles) break;
+    if (tid == 0) {  // claim the next tile and start bringing it in
+      const u64 t = atomicAdd(tile_ctr, 1u);
+      s_tile[cur ^ 1] = t;
+      if (t < tiles)
+        bulk_load(s_buf0 + (cur ^ 1) * TILE, in + t * TILE, tile_bytes(t), &s_bar[cur ^ 1]);
+    }
+    const bool got = mbar_wait(&s_bar[cur], phase >> cur & 1u);
+    if (got) {
+      phase ^= 1u << cur;
+      pending &= ~(1u << cur);
+    }
+    if (__syncthreads_or(!got)) {  // the copy never landed: give up on the pass
+      if (tid == 0) atomicOr(err, kErrTimeout);
+      break;
+    }
+    if (s_tile[cur ^ 1] < tiles) pending |= 1u << (cur ^ 1);
+    Slot<K> *buf = s_buf0 + cur * TILE;
+    const int wb = w * PER_WARP;
+    K key[ITEMS];
+    u64 cnt[ITEMS];
+    int dig[ITEMS];
+    unsigned peers[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int i = wb + j * 32 + lane;
+      key[j] = 0;
+      cnt[j] = 0;
+      if (tile * TILE + (u64)i < n) {
+        key[j] = buf[i].key;
+        cnt[j] = buf[i].cnt;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
+      SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
+      dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
+      peers[j] = __match_any_sync(0xffffffffu, dig[j] >= 0 ? dig[j] : 256 + lane);
+      if (dig[j] >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][dig[j]] += __popc(peers[j]);
+      __syncwarp();
+    }
+    __syncthreads();  // every record of buf is in registers; the counts are complete
+    unsigned tcount_d = 0;
+    for (int x = 0; x < W; ++x) tcount_d += s_wc[x][tid];
+    {
+      u64 *word = status + tile * 256 + tid;
+      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | tcount_d);
+      u64 excl = 0;
+      if (tile > 0) {
+        long long j = (long long)tile - 1;
+        unsigned spins = 0;
+        while (j >= 0) {
+          const u64 v = __ldcv(status + (u64)j * 256 + tid);
+          if ((v >> 48) != epoch) {
+            if (++spins > kSpinLimit) {
+              atomicOr(err, kErrTimeout);
+              break;
+            }
+            continue;
+          }
+          excl += v & kCountMask;
+          if (v >> 47 & 1ull) break;
+          --j;
+        }
+        atomicExch(word, (epoch << 48) | (1ull << 47) | (excl + tcount_d));
+      }
+      s_excl[tid] = base_d + excl;
+    }
+    {
+      unsigned x = tcount_d;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[w] = x;
+      __syncthreads();
+      unsigned start = x - tcount_d;
+      for (int q = 0; q < w; ++q) start += s_wsum[q];
+      s_tstart[tid] = start;
+      if (tid == 255) s_tcount = start + tcount_d;
+      for (int q = 0; q < W; ++q) {
+        const unsigned c = s_wc[q][tid];
+        s_wc[q][tid] = start;
+        start += c;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {  // stage the tile in digit order in its own buffer
+      const int d = dig[j];
+      if (d >= 0) {
+        const unsigned local = s_wc[w][d] + __popc(peers[j] & lt);
+        buf[local].key = key[j];
+        buf[local].cnt = cnt[j];
+        s_sdig[local] = (unsigned char)d;
+      }
+      __syncwarp();
+      if (d >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][d] += __popc(peers[j]);
+      __syncwarp();
+    }
+    __syncthreads();
+    const unsigned tcount = s_tcount;
+    for (unsigned i = tid; i < tcount; i += BLOCK) {
+      const int d = s_sdig[i];
+      const u64 pos = s_excl[d] + (i - s_tstart[d]);
+      if (pos < dst_cap) store_slot(out, pos, buf[i].key, buf[i].cnt);
+    }
+    for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();  // the staging is written out before the buffer receives a new tile
+    cur ^= 1;
+  }
+  // leave no copy landing in shared memory after the block has gone
+  for (int b = 0; b < 2; ++b)
+    if ((pending >> b & 1u) && !mbar_wait(&s_bar[b], phase >> b & 1u) && tid == 0)
+      atomicOr(err, kErrTimeout);
+}
+
 // ---- reduce by key: equal keys are adjacent; one record per run with the summed count ------
 template <typename K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, const u64 *n_ptr,
@@ -449,14 +654,26 @@ int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *
     cudaMemsetAsync(sw->status, 0, sizeof(u64) * 256 * sw->max_tiles, s);
     sweep_hist_kernel<K, SK, 256><<<G, 256, 0, s>>>(sp, src, n_src, src_cap, passes, sw->ghist);
     sweep_bases_kernel<<<passes, 256, 0, s>>>(sw->ghist);
+    constexpr int TI = ITEMS * 3 / 4;  // items per thread of the bulk-copy pass
+    constexpr size_t TSMEM = 2 * 256 * TI * sizeof(Slot<K>);
+    const int GT = d.sms * 3;
     for (int p = 0; p < passes; ++p) {
 #define CC_PASS(FK, SS)                                                                   \
-  sweep_pass_kernel<K, SK, 256, ITEMS, FK, SS><<<G, 256, 0, s>>>(                          \
-      sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,         \
-      sw->tile_ctr + p, bufs[cur], buf_cap, sw->err)
-      if (!sp.full) CC_PASS(true, false);   // partial order: recompute the tuple each pass
-      else if (p == 0) CC_PASS(true, true); // full order: records carry their sort key after
-      else CC_PASS(false, true);            // the first pass
+  if (sw->tma)                                                                            \
+    sweep_pass_tma_kernel<K, SK, TI, FK, SS><<<GT, 256, TSMEM, s>>>(                       \
+        sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,       \
+        sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);                                   \
+  else                                                                                    \
+    sweep_pass_kernel<K, SK, 256, ITEMS, FK, SS><<<G, 256, 0, s>>>(                        \
+        sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,       \
+        sw->tile_ctr + p, bufs[cur], buf_cap, sw->err)
+      if (!sp.full) {  // partial order: recompute the tuple each pass
+        CC_PASS(true, false);
+      } else if (p == 0) {  // full order: records carry their sort key after the first pass
+        CC_PASS(true, true);
+      } else {
+        CC_PASS(false, true);
+      }
 #undef CC_PASS
       in = bufs[cur];
       n_in = n;
@@ -487,7 +704,28 @@ int sort_grid(const DevInfo &d) { return grid256(d); }
 
 int sort_passes(const SortSpec &sp) { return (sp.bits + 7) / 8; }
 
-int sweep_tile(int kw) { return kw == 1 ? 256 * 8 : 256 * 4; }
+int sweep_tile(int kw) { return kw == 1 ? 256 * 6 : 256 * 3; }  // the smaller (bulk-copy) tile
+
+namespace {
+template <typename K, typename SK, int TI>
+int allow_tma_smem() {
+  constexpr int bytes = (int)(2 * 256 * TI * sizeof(Slot<K>));
+  int r = 0;
+  r |= (int)cudaFuncSetAttribute(sweep_pass_tma_kernel<K, SK, TI, true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  r |= (int)cudaFuncSetAttribute(sweep_pass_tma_kernel<K, SK, TI, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  r |= (int)cudaFuncSetAttribute(sweep_pass_tma_kernel<K, SK, TI, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return r;
+}
+}  // namespace
+
+int prepare_sort_kernels() {
+  int r = allow_tma_smem<u64, u64, 6>() | allow_tma_smem<u64, u128, 6>();
+  r |= allow_tma_smem<u128, u64, 3>() | allow_tma_smem<u128, u128, 3>();
+  return r;
+}
 
 int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
                         const void *src, const unsigned long long *n_src,

@@ -399,10 +399,11 @@ def test_planned_overflow_falls_back(ctx):
             release(ctx, r)
 
 
-@pytest.mark.parametrize("sweep", [0, 1])
+@pytest.mark.parametrize("sweep", [0, 1, 2])
 def test_sort_variants_agree(ctx, sweep):
-    """Both radix-sort schedules (separate histogram passes, or one-sweep with look-back) give
-    the oracle's tables, with 64- and 128-bit keys."""
+    """Every radix-sort schedule (separate histogram passes; one-sweep with look-back; one-sweep
+    with the next tile brought in by bulk copy) gives the oracle's tables, with 64- and 128-bit
+    keys."""
     g = synth.barabasi_albert(4000, 4, 12)
     for pat, k, T in ((synth.grid_pattern(2, 3), 6, 5), (synth.cycle_pattern(5), 12, 3)):
         colours = oracle.colors(4000, T, k, seed=77)
