@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--trials", type=int, default=0,
                     help="colouring trials per step (default: the workload's 64); smaller values "
                          "only for small profiling captures")
+    ap.add_argument("--arena-gb", type=int, default=96,
+                    help="device arena of the DP context (small values for profiling captures)")
     ap.add_argument("--serve-queries", type=int, default=300,
                     help="queries of the serving stream to run (0: skip the serving leg; the "
                          "full stream has 2000)")
@@ -333,7 +335,7 @@ def main():
     n = len(g[0]) - 1
     T, k = args.trials or w["trials"], w["k"]
     seed = w["seed"] + 1000003 * rank
-    ctx = cc.Context(arena_bytes=96 << 30, device=local)
+    ctx = cc.Context(arena_bytes=args.arena_gb << 30, device=local)
     h = ctx.h
     cc.cc_load_graph(h, *g)
     pid = cc.cc_load_pattern(h, nF, edges, td)

@@ -409,7 +409,8 @@ __device__ __forceinline__ u128 shfl_key(u128 v, int src) {
   return ((u128)hi << 64) | (u128)lo;
 }
 
-template <typename K, int MODE>
+// I: integer type of candidate positions within a window (int when 32 * n < 2^31).
+template <typename K, int MODE, typename I>
 __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
@@ -426,26 +427,27 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
     K key = 0;
     u64 c = 0;
     if (i < bound) load_slot(in, i, key, c);
-    long long nc = 0;
+    I nc = 0;
     int rs = 0;
     if (key != 0) {
       if (a.nnb == 0) {
-        nc = a.G.n;
+        nc = (I)a.G.n;
       } else {
         const int w = key_slot(key, a.L, a.nb_slot[0]);
         rs = a.G.row_ptr[w];
         nc = a.G.row_ptr[w + 1] - rs;
       }
     }
-    long long incl = nc;
+    I incl = nc;
     for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      const I y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const I excl = incl - nc;
+    const I total = __shfl_sync(0xffffffffu, incl, 31);
     if (lane == 0) examined += (u64)total;
-    for (long long j0 = 0; j0 < total; j0 += 32) {
-      const long long j = j0 + lane;
+    for (I j0 = 0; j0 < total; j0 += 32) {
+      const I j = j0 + lane;
       bool valid = false;
       K okey = 0;
       u64 oc = 0;
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
 #pragma unroll
       for (int step = 0; step < 5; ++step) {
         const int mid = (lo + hi) >> 1;
-        const long long v = __shfl_sync(0xffffffffu, incl, mid);
+        const I v = __shfl_sync(0xffffffffu, incl, mid);
         if (v > j) hi = mid;
         else lo = mid + 1;
       }
@@ -462,10 +464,9 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
       const K ekey = shfl_key(key, o);
       const u64 ec = __shfl_sync(0xffffffffu, c, o);
       const int ers = __shfl_sync(0xffffffffu, rs, o);
-      const long long eincl = __shfl_sync(0xffffffffu, incl, o);
-      const long long enc = __shfl_sync(0xffffffffu, nc, o);
+      const I eexcl = __shfl_sync(0xffffffffu, excl, o);
       if (j < total) {
-        const long long r = j - (eincl - enc);
+        const I r = j - eexcl;
         const int v = a.nnb ? __ldg(a.G.col + ers + r) : (int)r;
         const int t = key_trial(ekey, a.L);
         const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
@@ -959,13 +960,25 @@ int launch_intro_group_warp(cudaStream_t s, const DevInfo &d, int kw, int mode,
 
 int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a) {
   const int grid = d.sms * d.blocks_per_sm;
+  // a window's candidates number at most 32 * n (no bag neighbour: every vertex per entry)
+  const bool narrow = (long long)a.G.n * 32 < (1ll << 31);
+#define CC_IW(K, M)                                                         \
+  if (narrow) intro_warp_kernel<K, M, int><<<grid, 256, 0, s>>>(a);         \
+  else intro_warp_kernel<K, M, long long><<<grid, 256, 0, s>>>(a)
   if (kw == 1) {
-    if (mode == 1) intro_warp_kernel<u64, 1><<<grid, 256, 0, s>>>(a);
-    else intro_warp_kernel<u64, 2><<<grid, 256, 0, s>>>(a);
+    if (mode == 1) {
+      CC_IW(u64, 1);
+    } else {
+      CC_IW(u64, 2);
+    }
   } else {
-    if (mode == 1) intro_warp_kernel<u128, 1><<<grid, 256, 0, s>>>(a);
-    else intro_warp_kernel<u128, 2><<<grid, 256, 0, s>>>(a);
+    if (mode == 1) {
+      CC_IW(u128, 1);
+    } else {
+      CC_IW(u128, 2);
+    }
   }
+#undef CC_IW
   return (int)cudaGetLastError();
 }
 
