@@ -236,9 +236,10 @@ __global__ void __launch_bounds__(256) sweep_bases_kernel(u64 *ghist) {
 }
 
 // One pass.  Warp w of the block owns elements [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, read
-// in ITEMS coalesced rounds; stable ranks come from the warp's own sequential rounds (match on
-// the digit, one leader per digit) on top of per-(warp, digit) bases, so a tile needs five
-// block barriers.  With STORE_S the records leave carrying their sort key in place of the packed
+// in ITEMS coalesced rounds.  The tile's digit counts (shared-memory atomics) are published
+// first, since every later tile's look-back waits for them; stable ranks then come from the
+// warp's own sequential rounds (match on the digit, one leader per digit) on top of
+// per-(warp, digit) bases, so a tile needs six block barriers.  With STORE_S the records leave carrying their sort key in place of the packed
 // key (a full sort key is a bijection of the key): later passes read digits off it directly,
 // and reduce-by-key turns it back.
 template <typename K, typename SK, int BLOCK, int ITEMS, bool FROM_KEY, bool STORE_S>
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
   __shared__ unsigned s_wc[W][256];
   __shared__ unsigned s_tstart[256], s_wsum[W];
   __shared__ u64 s_excl[256];
-  __shared__ unsigned s_tile, s_tcount;
+  __shared__ unsigned s_tile, s_tcount, s_hist[256];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
   const u64 tiles = (n + TILE - 1) / TILE;
   const u64 base_d = bases[tid];
   for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+  s_hist[tid] = 0;
   while (true) {
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();  // (1) also orders the previous tile's write-out before reuse
@@ -281,20 +283,26 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
       if (i < n) load_slot(in, i, key[j], cnt[j]);
     }
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {  // digits, and the tile's digit counts
       if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
       SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
       dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
+      if (dig[j] >= 0) atomicAdd(&s_hist[dig[j]], 1u);
+    }
+    __syncthreads();  // (2)
+    // publish this tile's count of digit tid before ranking: every later tile's look-back
+    // waits for it
+    const unsigned tcount_d = s_hist[tid];  // records of digit tid in this tile
+    s_hist[tid] = 0;
+    u64 *word = status + tile * 256 + tid;
+    atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | tcount_d);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {  // stable ranks: per-(warp, digit) counts in input order
       peers[j] = __match_any_sync(0xffffffffu, dig[j] >= 0 ? dig[j] : 256 + lane);
       if (dig[j] >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][dig[j]] += __popc(peers[j]);
       __syncwarp();
     }
-    __syncthreads();  // (2)
-    unsigned tcount_d = 0;  // records of digit tid in this tile
-    for (int x = 0; x < W; ++x) tcount_d += s_wc[x][tid];
-    {  // publish this tile's count of digit tid, then look back for the tiles before it
-      u64 *word = status + tile * 256 + tid;
-      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | tcount_d);
+    {  // look back for the tiles before this one
       u64 excl = 0;
       if (tile > 0) {
         long long j = (long long)tile - 1;
@@ -316,6 +324,7 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
       }
       s_excl[tid] = base_d + excl;
     }
+    __syncthreads();  // the per-warp counts are complete
     {  // tile-local start of digit tid, then each warp's base within it
       unsigned x = tcount_d;
       for (int o = 1; o < 32; o <<= 1) {
