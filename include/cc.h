@@ -196,6 +196,27 @@ int cc_autotune(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_r
                 int32_t max_schedules, int32_t repeats, cc_run_opts *best_opts,
                 int32_t *best_pattern_id, float *best_ms, int32_t *configs_tried);
 
+/* ---- repetition to an error bound (Section 2.1) ------------------------------------------- */
+/* Number of colourings after which a present copy of a pattern with n_F vertices is missed with
+ * probability at most epsilon when k = n_F: ceil(e^{n_F} * ln(1/epsilon)) (clamped to INT32_MAX);
+ * -1 if n_F < 1 or epsilon is not in (0, 1).  Host only. */
+int32_t cc_solve_trials(int32_t n_F, double epsilon);
+
+/* The paper's whole solve: colours the graph again and again (trial t of the solve by Philox
+ * counter (v, t, 0, 0) under `seed`, so the solve equals one run over all its trials) in batches
+ * of `batch` trials, up to min(cc_solve_trials(n_F, epsilon), max_trials) trials, with
+ * cc_default_opts.  limit == 0 (decision, SubIso): stops after the first batch in which a trial
+ * finds a colourful copy.  limit > 0 (enumeration, SubEnum): runs every trial, keeps each batch's
+ * tables and merges its embeddings, each once: h_out[limit][n_F] receives the *n_out
+ * lexicographically smallest distinct embeddings found.  *found = 1 if any trial found a copy;
+ * *trials_run the trials run; *estimate (may be NULL) the mean count over the trials divided by
+ * (k)_{n_F}/k^{n_F}, an unbiased estimate of the number of embeddings.  Batches run with tables
+ * kept (limit > 0) must fit the arena whole.  Errors: CC_EINVAL, CC_ENOTFOUND, CC_EBUSY,
+ * CC_ENOMEM, CC_EKEYWIDTH, CC_ECUDA. */
+int cc_solve(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t k, double epsilon,
+             int32_t batch, int32_t max_trials, uint64_t limit, int32_t *h_out, uint64_t *n_out,
+             uint8_t *found, int32_t *trials_run, double *estimate);
+
 /* How a run was executed. */
 #define CC_MODE_EXACT 0   /* count passes size every table exactly (first run of a plan key) */
 #define CC_MODE_PLANNED 1 /* capacities from the plan, appends in chunks, no host reads */

@@ -31,7 +31,7 @@ EXPORTS = [
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
-    "cc_serve_stats", "cc_autotune",
+    "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -102,6 +102,9 @@ def lib():
         "cc_run_mode": ([P, i32, P], ctypes.c_int),
         "cc_serve_stats": ([P, P, P, P, P, P, P], ctypes.c_int),
         "cc_autotune": ([P, i32, i32, P, i32, i32, P, P, P, P], ctypes.c_int),
+        "cc_solve_trials": ([i32, ctypes.c_double], i32),
+        "cc_solve": ([P, i32, u64, i32, ctypes.c_double, i32, i32, u64, P, P, P, P, P],
+                     ctypes.c_int),
         "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
                              ctypes.c_int),
     }
@@ -324,6 +327,22 @@ def cc_autotune(ctx, pid: int, cid: int, base: cc_run_opts | None = None,
                              max_schedules, repeats, ctypes.byref(best), ctypes.byref(bp),
                              ctypes.byref(ms), ctypes.byref(n)), "cc_autotune")
     return best, bp.value, ms.value, n.value
+
+
+def cc_solve_trials(nF: int, epsilon: float) -> int:
+    return int(lib().cc_solve_trials(nF, epsilon))
+
+
+def cc_solve(ctx, pid: int, seed: int, k: int, epsilon: float, batch: int, max_trials: int,
+             limit: int, nF: int):
+    """(found, trials run, embeddings int32[m, nF], estimate)."""
+    out = np.zeros((max(1, limit), nF), np.int32)
+    n_out, found = ctypes.c_uint64(0), ctypes.c_uint8(0)
+    tr, est = ctypes.c_int32(0), ctypes.c_double(0)
+    _check(lib().cc_solve(ctx, pid, seed, k, epsilon, batch, max_trials, limit,
+                          _p(out) if limit else None, ctypes.byref(n_out), ctypes.byref(found),
+                          ctypes.byref(tr), ctypes.byref(est)), "cc_solve")
+    return bool(found.value), tr.value, out[:n_out.value], est.value
 
 
 def cc_run_mode(ctx, run: int) -> str:

@@ -110,8 +110,9 @@ struct DevInfo {
 };
 
 // ---- launchers (cc_kernels.cu); return a cudaError_t as int ---------------------------------
+// colours of trials t0 .. t0+trials-1 (Philox counter (v, t0 + t, 0, 0)) into out[t][v]
 int launch_color(cudaStream_t s, const DevInfo &d, uint8_t *out, int32_t n, int32_t trials,
-                 int32_t k, uint64_t seed);
+                 int32_t k, uint64_t seed, int32_t t0 = 0);
 int launch_leaf(cudaStream_t s, const DevInfo &d, int kw, const LeafArgs &a);
 // Introduce in three modes: 0 counts valid extensions per block into blk[0, grid) and writes
 // exclusive bases to blk[grid, 2*grid) and the total to blk[2*grid]; 1 writes them densely at

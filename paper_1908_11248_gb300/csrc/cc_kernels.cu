@@ -29,12 +29,12 @@ using namespace dev;
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) and the colouring of Section 2.1 -----------------
 __global__ void color_kernel(uint8_t *out, int32_t n, int32_t trials, int32_t k, uint32_t key0,
-                             uint32_t key1) {
+                             uint32_t key1, uint32_t t0) {
   u64 total = (u64)n * (u64)trials;
   for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total;
        i += (u64)gridDim.x * blockDim.x) {
     uint32_t t = (uint32_t)(i / (u64)n), v = (uint32_t)(i % (u64)n);
-    uint32_t x0 = v, x1 = t, x2 = 0u, x3 = 0u;
+    uint32_t x0 = v, x1 = t0 + t, x2 = 0u, x3 = 0u;
     uint32_t k0 = key0, k1 = key1;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -897,10 +897,10 @@ size_t index_slot_bytes(int kw) { return slot_bytes(kw); }
 int intro_grid(const DevInfo &d, int block) { return grid_for(d, block); }
 
 int launch_color(cudaStream_t s, const DevInfo &d, uint8_t *out, int32_t n, int32_t trials,
-                 int32_t k, uint64_t seed) {
+                 int32_t k, uint64_t seed, int32_t t0) {
   if ((u64)n * (u64)trials == 0) return 0;
   color_kernel<<<d.sms * 4, 256, 0, s>>>(out, n, trials, k, (uint32_t)seed,
-                                         (uint32_t)(seed >> 32));
+                                         (uint32_t)(seed >> 32), (uint32_t)t0);
   return (int)cudaGetLastError();
 }
 

@@ -97,3 +97,14 @@ def test_check_graph():
     ]
     for rp, col in bad:
         assert cc.cc_check_graph(np.array(rp, np.int32), np.array(col, np.int32)) == cc.CC_EINVAL
+
+
+def test_solve_trials_count():
+    """Repetitions for error bound epsilon: ceil(e^{n_F} ln(1/epsilon)) (Section 2.1), checked on
+    values worked out by hand; invalid arguments give -1."""
+    assert cc.cc_solve_trials(5, 0.1) == 342      # 148.413 * 2.30259 = 341.74
+    assert cc.cc_solve_trials(1, 0.5) == 2        # 2.71828 * 0.69315 = 1.884
+    assert cc.cc_solve_trials(8, 0.01) == 13728   # 2980.958 * 4.60517 = 13727.8
+    assert cc.cc_solve_trials(0, 0.1) == -1
+    assert cc.cc_solve_trials(5, 0.0) == -1
+    assert cc.cc_solve_trials(5, 1.0) == -1
