@@ -22,6 +22,9 @@
 //   * bags are ordered by increasing F-vertex id (Section 3.2, representation of mappings).
 //   * the degree filter deg_G(x) >= deg_F(y) (Section 3.2, masking unprofitable mappings) is a
 //     switch; it never changes the root result.
+//   * the extended input of that paragraph, per host vertex the set of pattern vertices that may
+//     be mapped to it, is an optional mask array (bit y of allow[x]: y may map to x); maps that
+//     break it are not counted anywhere.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -287,6 +290,7 @@ struct Run {
   NiceTD T;
   int32_t k = 0, trials = 0;
   bool degree_filter = true;
+  std::vector<uint32_t> allow;           // empty: every mapping allowed
   std::vector<uint8_t> colours;          // trials * n
   std::vector<std::vector<Table>> D;     // [trial][node]
   std::vector<uint8_t> exists;
@@ -307,6 +311,7 @@ void run_trial(Run &R, int32_t t) {
       int32_t u = nd.vertex;
       for (int32_t v = 0; v < G.n; ++v) {
         if (R.degree_filter && G.deg(v) < F.deg[u]) continue;
+        if (!R.allow.empty() && !((R.allow[v] >> u) & 1u)) continue;
         Dx[Key({v}, 1u << zeta[v])] += 1;
       }
     } else if (nd.type == INTRODUCE) {
@@ -333,6 +338,7 @@ void run_trial(Run &R, int32_t t) {
         for (int32_t v : cand) {
           if ((Cc >> zeta[v]) & 1u) continue;
           if (R.degree_filter && G.deg(v) < F.deg[u]) continue;
+          if (!R.allow.empty() && !((R.allow[v] >> u) & 1u)) continue;
           bool ok = true;
           for (int32_t s : nb_slots)
             if (!G.adjacent(phi_c[s], v)) { ok = false; break; }
@@ -557,7 +563,7 @@ int32_t or_nice_td(int32_t nF, int32_t mF, const int32_t *edges, int32_t nbags,
 void *or_dp_run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t nF, int32_t mF,
                 const int32_t *edges, int32_t nbags, const int32_t *bag_ptr,
                 const int32_t *bag_vtx, const int32_t *parent, const uint8_t *colours,
-                int32_t trials, int32_t k, int32_t degree_filter) {
+                int32_t trials, int32_t k, int32_t degree_filter, const uint32_t *allow) {
   if (nF < 1 || nF > 32 || k < nF || k > 32 || trials < 1 || n < 0) return nullptr;
   Run *R = new Run();
   R->G = make_graph(n, row_ptr, col);
@@ -569,6 +575,7 @@ void *or_dp_run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t n
   R->k = k;
   R->trials = trials;
   R->degree_filter = degree_filter != 0;
+  if (allow) R->allow.assign(allow, allow + n);
   R->colours.assign(colours, colours + (size_t)trials * n);
   R->D.resize(trials);
   R->exists.assign(trials, 0);

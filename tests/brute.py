@@ -54,13 +54,16 @@ def vstar(nodes):
     return vs
 
 
-def node_table(G, nF, edges, zeta, bag, verts, degG=None, degF=None):
+def node_table(G, nF, edges, zeta, bag, verts, degG=None, degF=None, allow=None):
     """D(x, ., .) by definition: Counter over (phi tuple in bag order, colour set) of colourful
     embeddings of F[verts].  With degG/degF given, only maps with deg_G(Phi(y)) >= deg_F(y)
-    for every y are counted (the degree filter of Section 3.2)."""
+    for every y are counted (the degree filter of Section 3.2); with allow given, only maps with
+    bit y of allow[Phi(y)] set for every y (the extended input of the same paragraph)."""
     tab = Counter()
     for m in embeddings(G, nF, edges, zeta, verts):
         if degG is not None and any(degG[m[y]] < degF[y] for y in m):
+            continue
+        if allow is not None and any(not (int(allow[m[y]]) >> y) & 1 for y in m):
             continue
         C = 0
         for v in m.values():

@@ -190,6 +190,62 @@ def test_node_tables_match_definition(ci, dfilter):
                 assert got == dict(want), (x, nd)
 
 
+@pytest.mark.parametrize("ci", range(len(TINY)))
+def test_node_tables_with_allowed_mappings(ci):
+    """Per-host-vertex masks of the pattern vertices that may map there (Section 3.2, masking
+    unprofitable mappings): every node table equals the definition restricted to allowed maps;
+    a full mask changes nothing."""
+    (nF, e, td), kind, n, p = TINY[ci]
+    g = _graph(kind, n, p, 3 + ci)
+    G = brute.adj_sets(*g)
+    nodes = oracle.nice_td(nF, e, td)
+    vs = brute.vstar(nodes)
+    rng = np.random.default_rng(50 + ci)
+    zeta = rng.integers(0, nF, size=(2, n)).astype(np.uint8)
+    allow = np.zeros(n, np.uint32)
+    for v in range(n):
+        for y in range(nF):
+            if rng.random() < 0.7:
+                allow[v] |= np.uint32(1 << y)
+    run = oracle.run_dp(g, (nF, e, td), zeta, nF, degree_filter=False, allow=allow)
+    full = oracle.run_dp(g, (nF, e, td), zeta, nF, degree_filter=False,
+                         allow=np.full(n, (1 << nF) - 1, np.uint32))
+    plain = oracle.run_dp(g, (nF, e, td), zeta, nF, degree_filter=False)
+    assert np.array_equal(full.node_sizes, plain.node_sizes)
+    assert np.array_equal(full.count, plain.count)
+    for t in range(2):
+        for x, nd in enumerate(nodes):
+            bag = nd[4]
+            want = brute.node_table(G, nF, e, zeta[t], bag, vs[x], allow=allow)
+            phi, mask, cnt = run.table(t, x, len(bag))
+            got = {(tuple(int(v) for v in phi[i]), int(mask[i])): int(cnt[i])
+                   for i in range(len(mask))}
+            assert got == dict(want), (x, nd)
+
+
+@pytest.mark.parametrize("ci", range(len(TINY)))
+def test_degree_filter_is_an_allowed_mask(ci):
+    """The degree filter is the mask {y : deg_G(x) >= deg_F(y)} (the paragraph derives it from
+    the extended input): both give the same tables."""
+    (nF, e, td), kind, n, p = TINY[ci]
+    g = _graph(kind, n, p, 3 + ci)
+    degG = np.diff(g[0])
+    degF = np.zeros(nF, int)
+    for a, b in np.asarray(e).reshape(-1, 2):
+        degF[a] += 1
+        degF[b] += 1
+    allow = np.array([sum(1 << y for y in range(nF) if degG[v] >= degF[y]) for v in range(n)],
+                     np.uint32)
+    zeta = np.random.default_rng(ci).integers(0, nF, size=(2, n)).astype(np.uint8)
+    a = oracle.run_dp(g, (nF, e, td), zeta, nF, degree_filter=True)
+    b = oracle.run_dp(g, (nF, e, td), zeta, nF, degree_filter=False, allow=allow)
+    assert np.array_equal(a.node_sizes, b.node_sizes) and np.array_equal(a.count, b.count)
+    for t in range(2):
+        for x, nd in enumerate(oracle.nice_td(nF, e, td)):
+            ta, tb = a.table(t, x, len(nd[4])), b.table(t, x, len(nd[4]))
+            assert all(np.array_equal(u, w) for u, w in zip(ta, tb))
+
+
 # ------------------------------------------------------------------------------------------
 # root counts: brute force, closed forms, sum over colourings
 # ------------------------------------------------------------------------------------------
