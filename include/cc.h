@@ -86,6 +86,17 @@ typedef struct {
 int cc_load_pattern(cc_ctx *ctx, int32_t n_F, int32_t m_F, const int32_t *h_edges,
                     const cc_td *td, int32_t *pattern_id);
 
+/* A pattern whose embeddings must also respect allowed mappings (Section 3.2, masking
+ * unprofitable mappings: the extended input names, for each vertex of the network, the pattern
+ * vertices that may be mapped to it).  h_allow[n] (n of the loaded graph): bit u of h_allow[v]
+ * lets F-vertex u be mapped to host vertex v.  Tables, counts and enumerations then count only
+ * maps that respect it (the degree filter still applies on top).  Otherwise as cc_load_pattern.
+ * The masks belong to the graph loaded now: runs of the pattern fail with CC_EINVAL once a graph
+ * of other content is loaded.  Errors: as cc_load_pattern, CC_EINVAL (no graph, h_allow NULL),
+ * CC_EBUSY, CC_ENOMEM, CC_ECUDA. */
+int cc_load_pattern_masked(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
+                           const cc_td *td, const uint32_t *h_allow, int32_t *pattern_id);
+
 /* Host-only (no context, no GPU): the nice decomposition cc_load_pattern would build for F and
  * td (td NULL: minimum width), in the layout of cc_pattern_nodes.  Arrays hold max_nodes nodes
  * (h_bag_ptr max_nodes+1, h_bag_vtx max_nodes*n_F).  *num_nodes and *width receive its size and

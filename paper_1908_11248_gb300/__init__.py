@@ -32,6 +32,7 @@ EXPORTS = [
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
     "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
+    "cc_load_pattern_masked",
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -103,6 +104,7 @@ def lib():
         "cc_serve_stats": ([P, P, P, P, P, P, P], ctypes.c_int),
         "cc_autotune": ([P, i32, i32, P, i32, i32, P, P, P, P], ctypes.c_int),
         "cc_solve_trials": ([i32, ctypes.c_double], i32),
+        "cc_load_pattern_masked": ([P, i32, i32, P, P, P, P], ctypes.c_int),
         "cc_solve": ([P, i32, u64, i32, ctypes.c_double, i32, i32, u64, P, P, P, P, P],
                      ctypes.c_int),
         "cc_count_noalloc": ([ctypes.c_int, P, i32, P, P, i32, i32, P, P, u64, i32, i32, P, P],
@@ -169,6 +171,18 @@ def cc_load_pattern(ctx, nF: int, edges, td=None) -> int:
     tdp, keep = _td_struct(td)
     _check(lib().cc_load_pattern(ctx, nF, len(e) // 2, _p(e) if len(e) else None, tdp,
                                  ctypes.byref(pid)), "cc_load_pattern")
+    del keep
+    return pid.value
+
+
+def cc_load_pattern_masked(ctx, nF: int, edges, td, allow) -> int:
+    """A pattern with allowed mappings: bit u of allow[v] (uint32[n]) lets F-vertex u map to v."""
+    e = _i32(edges).reshape(-1)
+    a = np.ascontiguousarray(np.asarray(allow, dtype=np.uint32))
+    pid = ctypes.c_int32(0)
+    tdp, keep = _td_struct(td)
+    _check(lib().cc_load_pattern_masked(ctx, nF, len(e) // 2, _p(e) if len(e) else None, tdp,
+                                        _p(a), ctypes.byref(pid)), "cc_load_pattern_masked")
     del keep
     return pid.value
 

@@ -63,6 +63,7 @@ __device__ bool member(const EnumArgs &a, int y, K key) {
       const int cv = colour_of(a.G, key_trial(key, a.L), v);
       if (!((key_mask(key, a.L) >> cv) & 1u)) return false;
       if (nd.degF && a.G.row_ptr[v + 1] - a.G.row_ptr[v] < nd.degF) return false;
+      if (a.G.allow && !((a.G.allow[v] >> nd.vertex) & 1u)) return false;
       const K k2 = key_remove(key, a.L, nd.p) & ~((K)1 << cv);
       for (int j = 0; j < nd.nnb; ++j)
         if (!adjacent(a.G, key_slot(k2, a.L, nd.nb_slot[j]), v)) return false;

@@ -392,7 +392,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   const int block = R->opts.block;
   const int df = R->opts.degree_filter;
   const bool planned = plan != nullptr;
-  cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n, c->d_deg8};
+  cc::GraphDev G{c->d_row_ptr, c->d_col, col.d_colors, n, c->d_deg8, P.d_allow};
   R->tables.assign(N, {});
   R->sizes.assign(N, 0);
   R->pairs.assign(N, 0);
@@ -538,7 +538,8 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       void *p = A.alloc(cap * rb);
       if (!p) return CC_ENOMEM;
       R->tables[x] = {p, cap, 1, true};
-      cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), R->d_err};
+      cc::LeafArgs a{G, R->L, R->trials, df ? P.deg[nd.vertex] : 0, desc(x), R->d_err,
+                     1u << nd.vertex};
       if (n == 0) CUDA_OK(cudaMemsetAsync(p, 0, rb, c->stream));
       rc = timed(x, CC_K_LEAF, 1, [&] { return cc::launch_leaf(c->stream, c->dev, R->kw, a); });
       if (rc) return rc;
@@ -555,6 +556,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
       a.degF = df ? P.deg[nd.vertex] : 0;
+      a.ubit = 1u << nd.vertex;
       a.err = R->d_err;
       a.cand = R->d_counters + 3 * N + x;  // candidates examined (count pass, or planned)
       a.proj_q = -1;
@@ -878,7 +880,8 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
     return CC_ECUDA;
   }
   cc::EnumArgs a{};
-  a.G = cc::GraphDev{c->d_row_ptr, c->d_col, col.d_colors, c->n, c->d_deg8};
+  a.G = cc::GraphDev{c->d_row_ptr, c->d_col, col.d_colors, c->n, c->d_deg8,
+                     c->patterns.at(R->pattern).d_allow};
   a.L = R->L;
   a.nodes = d_nodes;
   a.nF = nF;
@@ -1000,6 +1003,7 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
   if (pi == c->patterns.end()) return CC_ENOTFOUND;
   const Pattern &P = pi->second;
   if (col.k < P.nF) return CC_EINVAL;
+  if (P.allow_fp && P.allow_fp != c->graph_fp) return CC_EINVAL;  // masks of another graph
   R.reset(new Run());
   cc_default_opts(&R->opts);
   if (opts) R->opts = *opts;
@@ -1691,6 +1695,31 @@ int cc_load_pattern(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
   int rc = make_pattern(nF, mF, h_edges, td, P);
   if (rc) return rc;
   int32_t id = c->next_pattern++;
+  c->patterns[id] = std::move(P);
+  *pattern_id = id;
+  return CC_OK;
+}
+
+int cc_load_pattern_masked(cc_ctx *ctx, int32_t nF, int32_t mF, const int32_t *h_edges,
+                           const cc_td *td, const uint32_t *h_allow, int32_t *pattern_id) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  if (cc::serve_active(c)) return CC_EBUSY;
+  if (!pattern_id || !h_allow || c->n < 0) return CC_EINVAL;
+  Pattern P;
+  int rc = make_pattern(nF, mF, h_edges, td, P);
+  if (rc) return rc;
+  P.d_allow = arena_alloc<uint32_t>(c, std::max<size_t>(1, (size_t)c->n));
+  if (!P.d_allow) return CC_ENOMEM;
+  if (c->n > 0 && (cudaMemcpyAsync(P.d_allow, h_allow, (size_t)c->n * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                   cudaStreamSynchronize(c->stream) != cudaSuccess)) {
+    c->arena.release(P.d_allow);
+    return CC_ECUDA;
+  }
+  P.allow_fp = c->graph_fp;
+  std::lock_guard<std::mutex> lock(c->mu);
+  const int32_t id = c->next_pattern++;
   c->patterns[id] = std::move(P);
   *pattern_id = id;
   return CC_OK;

@@ -44,6 +44,7 @@ struct GraphDev {
   const uint8_t *colors;   // trials * n
   int32_t n;
   const uint8_t *deg8;     // min(degree, 255) per vertex (pattern degrees are below 32)
+  const uint32_t *allow;   // per vertex, bit u: F-vertex u may be mapped there (null: any)
 };
 
 struct LeafArgs {
@@ -53,6 +54,7 @@ struct LeafArgs {
   int degF;  // minimum host degree (degree filter), 0 = off
   TableDesc out;
   int *err;
+  uint32_t ubit;  // 1 << (the leaf's F-vertex), tested against G.allow
 };
 
 struct IntroArgs {
@@ -71,6 +73,7 @@ struct IntroArgs {
   unsigned long long *valid; // modes 1, 2: number of introduce entries produced (if non-null)
   unsigned long long *cand;  // mode 0: number of candidate vertices examined
   int *err;
+  uint32_t ubit;             // 1 << u, tested against G.allow
 };
 
 struct ForgetArgs {

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(BLOCK) leaf_kernel(LeafArgs a) {
   for (u64 i = blockIdx.x * (u64)BLOCK + threadIdx.x; i < total; i += (u64)gridDim.x * BLOCK) {
     int t = (int)(i / n), v = (int)(i % n);
     K key = 0;
-    if (a.degF == 0 || a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF) {
+    if ((a.degF == 0 || a.G.row_ptr[v + 1] - a.G.row_ptr[v] >= a.degF) &&
+        (!a.G.allow || (a.G.allow[v] & a.ubit))) {
       int c = a.G.colors[i];
       key = ((K)1 << c) | ((K)(unsigned)v << a.L.k);
       if (a.L.tb) key |= (K)(unsigned)t << a.L.tpos;
@@ -219,6 +220,7 @@ __device__ __forceinline__ void plain_tile(const IntroArgs &a, S &sm, EmitState 
       const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
       valid = !((key_mask(ekey, a.L) >> cv) & 1u);
       if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+      if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
       if (valid) {
         const int an = sm.anc[e];
         for (int q = 0; q < a.nnb && valid; ++q)
@@ -288,7 +290,8 @@ __device__ __forceinline__ bool grouped_tile(const IntroArgs &a, S &sm, EmitStat
     if (j < total) {
       e = owner<BLOCK>(sm.off, j);
       v = __ldg(a.G.col + sm.rs[e] + (j - sm.off[e]));
-      ok = a.degF == 0 || a.G.deg8[v] >= a.degF;
+      ok = (a.degF == 0 || a.G.deg8[v] >= a.degF) &&
+           (!a.G.allow || (a.G.allow[v] & a.ubit));
       if (ok) {
         const K ekey = sm.key[e];
         const int an = sm.anc[e];
@@ -472,6 +475,7 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
         const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
         valid = !((key_mask(ekey, a.L) >> cv) & 1u);
         if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+        if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
         if (valid) {
           okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
           oc = ec;
@@ -623,7 +627,8 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
         int v = 0;
         if (j < best) {
           v = __ldg(a.G.col + rs + j);
-          ok = a.degF == 0 || a.G.deg8[v] >= a.degF;
+          ok = (a.degF == 0 || a.G.deg8[v] >= a.degF) &&
+               (!a.G.allow || (a.G.allow[v] & a.ubit));
           for (int q = 0; q < a.nnb && ok; ++q)
             if (q != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[q]), v);
         }
@@ -685,6 +690,7 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
           const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
           valid = !((key_mask(key, a.L) >> cv) & 1u);
           if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+          if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
           for (int q = 0; q < a.nnb && valid; ++q)
             if (q != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[q]), v);
           if (valid) okey = key_insert(key, a.L, a.p, v) | ((K)1 << cv);

@@ -128,6 +128,10 @@ struct Pattern {
   // the tree decomposition the nice one was built from (given, or computed)
   std::vector<std::vector<int>> td_bags;
   std::vector<int> td_parent;
+  // allowed mappings (bit u of d_allow[v]: u may map to v), for the graph with fingerprint
+  // allow_fp; null / 0: every mapping allowed
+  uint32_t *d_allow = nullptr;
+  long long allow_fp = 0;
 };
 
 struct Coloring {

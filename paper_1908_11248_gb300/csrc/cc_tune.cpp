@@ -93,6 +93,8 @@ int cc_autotune(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_r
       Q.nF = base_p.nF;
       Q.adj = base_p.adj;
       Q.deg = base_p.deg;
+      Q.d_allow = base_p.d_allow;
+      Q.allow_fp = base_p.allow_fp;
       if (cc::rt::nice_from_td(Q, base_p.td_bags, cc::reroot(base_p.td_parent, r))) continue;
       bool dup = false;
       for (int32_t s : schedules) dup = dup || cc::same_nice(c->patterns.at(s), Q);

@@ -430,3 +430,46 @@ def test_planned_at_workload_scale(ctx):
             assert np.array_equal(r["count"], ref.count)
             assert np.array_equal(r["sizes"], ref.node_sizes.sum(axis=0))
             release(ctx, r)
+
+
+def test_allowed_mappings_match_oracle(ctx):
+    """Patterns with allowed-mapping masks (Section 3.2, masking unprofitable mappings): counts,
+    table sizes, planned reruns and the enumeration equal the oracle's with the same masks, for
+    every forget scheme; the masks belong to the graph they were given for."""
+    n = 1500
+    g = synth.barabasi_albert(n, 4, 17)
+    rng = np.random.default_rng(3)
+    cc.cc_load_graph(ctx.h, *g)
+    fewer = False
+    for pat in (synth.cycle_pattern(5), synth.pattern_B(), synth.grid_pattern(2, 3)):
+        nF, e, td = pat
+        bits = (rng.random((n, nF)) < 0.6).astype(np.uint32)
+        allow = (bits << np.arange(nF, dtype=np.uint32)).sum(axis=1).astype(np.uint32)
+        z = oracle.colors(n, 3, nF, seed=8)
+        ref = oracle.run_dp(g, pat, z, nF, allow=allow)
+        fewer = fewer or int(ref.count.sum()) < int(oracle.run_dp(g, pat, z, nF).count.sum())
+        want_list = ref.enumerate(100000)[0]
+        pid = cc.cc_load_pattern_masked(ctx.h, nF, e, td, allow)
+        cid = cc.cc_set_colors(ctx.h, z, nF)
+        N, _ = cc.cc_pattern_info(ctx.h, pid)
+        for fuse in (2, 1, 0):
+            for want_mode in ("exact", "planned"):
+                run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(fuse=fuse))
+                assert cc.cc_run_mode(ctx.h, run) == want_mode
+                assert np.array_equal(cc.cc_count(ctx.h, run, 3), ref.count)
+                assert np.array_equal(cc.cc_table_stats(ctx.h, run, N)[0],
+                                      ref.node_sizes.sum(axis=0))
+                cc.cc_release(ctx.h, run)
+        run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(retain=1))
+        lst, tot = cc.cc_enumerate(ctx.h, run, 100000, nF)
+        assert np.array_equal(lst, want_list)
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
+    assert fewer  # the masks removed embeddings
+    # another graph: the masked pattern no longer runs
+    cc.cc_load_graph(ctx.h, *synth.barabasi_albert(n, 3, 18))
+    cid = cc.cc_color(ctx.h, 1, 1, 6)
+    with pytest.raises(cc.CCError) as err:
+        cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
+    assert err.value.code == -1
+    cc.cc_release_colors(ctx.h, cid)
