@@ -266,6 +266,14 @@ int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity,
 int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, uint64_t *n_out,
                  uint64_t *n_total);
 
+/* As cc_enumerate, counting occurrences that differ in their vertex sets (the switch of
+ * Section 5.2: non-induced occurrences and automorphisms map the pattern onto the same vertex
+ * set in several ways): each embedding is replaced by its image set in increasing vertex order,
+ * and h_out receives the `limit` lexicographically smallest distinct sets; *n_total = distinct
+ * vertex sets.  Errors as cc_enumerate. */
+int cc_enumerate_sets(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out,
+                      uint64_t *n_out, uint64_t *n_total);
+
 /* Frees a run's tables and results. */
 int cc_release(cc_ctx *ctx, int32_t run_id);
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
     "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
-    "cc_load_pattern_masked",
+    "cc_load_pattern_masked", "cc_enumerate_sets",
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -91,6 +91,7 @@ def lib():
         "cc_table_stats": ([P, i32, P, P], ctypes.c_int),
         "cc_table_dump": ([P, i32, i32, u64, P, P, P, P, P], ctypes.c_int),
         "cc_enumerate": ([P, i32, u64, P, P, P], ctypes.c_int),
+        "cc_enumerate_sets": ([P, i32, u64, P, P, P], ctypes.c_int),
         "cc_release": ([P, i32], ctypes.c_int),
         "cc_serve_start": ([P, sz, i32], ctypes.c_int),
         "cc_serve_submit": ([P, i32, u64, i32, i32, P], ctypes.c_int),
@@ -315,6 +316,14 @@ def cc_enumerate(ctx, run: int, limit: int, nF: int):
     n_out, n_tot = ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(lib().cc_enumerate(ctx, run, limit, _p(out), ctypes.byref(n_out), ctypes.byref(n_tot)),
            "cc_enumerate")
+    return out[:n_out.value], int(n_tot.value)
+
+
+def cc_enumerate_sets(ctx, run: int, limit: int, nF: int):
+    out = np.zeros((max(1, limit), nF), np.int32)
+    n_out, n_tot = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().cc_enumerate_sets(ctx, run, limit, _p(out), ctypes.byref(n_out),
+                                   ctypes.byref(n_tot)), "cc_enumerate_sets")
     return out[:n_out.value], int(n_tot.value)
 
 

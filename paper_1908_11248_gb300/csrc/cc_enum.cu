@@ -347,6 +347,23 @@ __global__ void __launch_bounds__(256) rows_scatter_kernel(const int *rows, int 
   }
 }
 
+// each row (the images of F-vertices 0..nF-1) replaced by its vertex set in increasing order
+__global__ void rows_canon_kernel(int *rows, int nF, u64 n) {
+  for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n;
+       i += (u64)gridDim.x * blockDim.x) {
+    int *r = rows + i * (u64)nF;
+    for (int a = 1; a < nF; ++a) {  // insertion sort, n_F <= 32
+      const int v = r[a];
+      int b = a - 1;
+      while (b >= 0 && r[b] > v) {
+        r[b + 1] = r[b];
+        --b;
+      }
+      r[b + 1] = v;
+    }
+  }
+}
+
 // rows of the final states, and the identity permutation
 __global__ void rows_extract_kernel(const int *states, u64 n, int R, int D, int nF, int *rows,
                                     unsigned *perm) {
@@ -418,6 +435,12 @@ int launch_scan_u32(cudaStream_t s, const DevInfo &d, const unsigned *v, unsigne
   scan_small_kernel<<<1, 32, 0, s>>>(sums, nb, total);
   block_scan_kernel<<<nb, 1024, 0, s>>>(v, n, per, sums, off);
   cudaMemcpyAsync(off + n, total, sizeof(u64), cudaMemcpyDeviceToDevice, s);
+  return (int)cudaGetLastError();
+}
+
+int launch_rows_canon(cudaStream_t s, const DevInfo &d, int *rows, int nF,
+                      unsigned long long n) {
+  if (n) rows_canon_kernel<<<d.sms * 4, 256, 0, s>>>(rows, nF, n);
   return (int)cudaGetLastError();
 }
 

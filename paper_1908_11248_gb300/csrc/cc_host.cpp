@@ -783,7 +783,7 @@ int finish_run(Ctx *c, Run *R) {
 
 // ---- reconstruction driver (Section 4): pre-order steps over device state arrays -----------
 int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_out,
-                  uint64_t *n_total) {
+                  uint64_t *n_total, bool sets) {
   const Pattern &P = c->patterns.at(R->pattern);
   const cc::Coloring &col = c->colorings.at(R->coloring);
   const int N = (int)P.nodes.size();
@@ -956,6 +956,7 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
     } else {
       unsigned *sorted = nullptr;
       if (cc::launch_rows_extract(c->stream, c->dev, cur, n_cur, RW, D, nF, rows, perm) ||
+          (sets && cc::launch_rows_canon(c->stream, c->dev, rows, nF, n_cur)) ||
           cc::launch_rows_sort(c->stream, c->dev, rows, nF, R->L.nb, n_cur, perm, tmp, hist,
                                &sorted) ||
           cc::launch_rows_heads(c->stream, c->dev, rows, nF, sorted, n_cur, flag) ||
@@ -1949,7 +1950,18 @@ int cc_enumerate(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out, ui
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
   if (!R->retained) return CC_EINVAL;
-  return enumerate_run(c, R, limit, h_out, n_out, n_total);
+  return enumerate_run(c, R, limit, h_out, n_out, n_total, false);
+}
+
+int cc_enumerate_sets(cc_ctx *ctx, int32_t run_id, uint64_t limit, int32_t *h_out,
+                      uint64_t *n_out, uint64_t *n_total) {
+  Ctx *c = (Ctx *)ctx;
+  if (c && cc::serve_active(c)) return CC_EBUSY;
+  if (!c || !n_out || !n_total || (limit && !h_out)) return CC_EINVAL;
+  Run *R = find_run(c, run_id);
+  if (!R) return CC_ENOTFOUND;
+  if (!R->retained) return CC_EINVAL;
+  return enumerate_run(c, R, limit, h_out, n_out, n_total, true);
 }
 
 int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,

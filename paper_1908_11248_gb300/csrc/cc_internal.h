@@ -228,6 +228,9 @@ int launch_scan_u32(cudaStream_t s, const DevInfo &d, const unsigned *v, unsigne
                     unsigned long long *off, unsigned long long *scratch);
 int launch_rows_extract(cudaStream_t s, const DevInfo &d, const int *states,
                         unsigned long long n, int R, int D, int nF, int *rows, unsigned *perm);
+// every row sorted in place into increasing order (the vertex set of an embedding)
+int launch_rows_canon(cudaStream_t s, const DevInfo &d, int *rows, int nF,
+                      unsigned long long n);
 // lexicographic order of the rows (nF ints each, values < 2^nb) as a permutation; *result is
 // perm or tmp.  hist needs 256 * 2 * sms words.
 int launch_rows_sort(cudaStream_t s, const DevInfo &d, const int *rows, int nF, int nb,

@@ -127,7 +127,7 @@ int cc_solve(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t k, double e
       if (!rc && limit) {
         part.assign((size_t)limit * nF, 0);
         uint64_t m = 0, tot = 0;
-        rc = cc::rt::enumerate_run(c, R, limit, part.data(), &m, &tot);
+        rc = cc::rt::enumerate_run(c, R, limit, part.data(), &m, &tot, false);
         if (!rc) {
           part.resize((size_t)m * nF);
           cc::merge_rows(rows, part, nF, limit);

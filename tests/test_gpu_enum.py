@@ -98,3 +98,31 @@ def test_enumerate_requires_kept_tables(ctx):
     assert ex.value.code == cc.CC_EINVAL
     cc.cc_release(ctx.h, run)
     cc.cc_release_colors(ctx.h, cid)
+
+
+@pytest.mark.parametrize("name", ["C4", "C5", "G23", "K4", "B", "T2"])
+def test_enumerate_vertex_sets(ctx, name):
+    """Occurrences counted by vertex set (Section 5.2's switch): the distinct image sets of the
+    oracle's embeddings, sorted; fewer than the embeddings whenever F has automorphisms."""
+    pat = PATS[name]
+    nF, e, td = pat
+    g = synth.erdos_renyi(36, 0.3, 11)
+    colours = oracle.colors(36, 4, nF, seed=17)
+    ref = oracle.run_dp(g, pat, colours, nF)
+    emb, total, _ = ref.enumerate(10 ** 7)
+    want = sorted({tuple(sorted(int(v) for v in r)) for r in emb})
+    cc.cc_load_graph(ctx.h, *g)
+    pid = cc.cc_load_pattern(ctx.h, nF, e, td)
+    cid = cc.cc_set_colors(ctx.h, colours, nF)
+    run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(retain=1))
+    try:
+        sets, nsets = cc.cc_enumerate_sets(ctx.h, run, 10 ** 6, nF)
+        assert nsets == len(want) and [tuple(int(v) for v in r) for r in sets] == want
+        if len(want) > 3:
+            few, n2 = cc.cc_enumerate_sets(ctx.h, run, 3, nF)
+            assert n2 == len(want) and [tuple(int(v) for v in r) for r in few] == want[:3]
+        if total:
+            assert nsets < total  # every pattern here has a nontrivial automorphism
+    finally:
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
