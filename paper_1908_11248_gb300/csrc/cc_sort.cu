@@ -368,6 +368,144 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
   }
 }
 
+// ---- one pass over 4096-record tiles: 512 threads, the first 256 owning one digit each ------
+// The same steps as sweep_pass_kernel with twice the tile per block, so that each tile's
+// fixed costs (claim, barriers, look-back over 256 digit words, publication) are spread over
+// twice the records; the staging buffer lives in dynamic shared memory.
+template <typename K, typename SK, int ITEMS, bool FROM_KEY, bool STORE_S>
+__global__ void __launch_bounds__(512, 2) sweep_pass_wide_kernel(SortSpec sp, const void *src,
+                                                                const u64 *n_ptr, u64 n_cap,
+                                                                int shift, u64 epoch,
+                                                                const u64 *bases, u64 *status,
+                                                                unsigned *tile_ctr, void *dst,
+                                                                u64 dst_cap, int *err) {
+  constexpr int BLOCK = 512, W = BLOCK / 32, TILE = BLOCK * ITEMS, PER_WARP = 32 * ITEMS;
+  extern __shared__ __align__(16) unsigned char s_wdyn[];
+  Slot<K> *const s_stage = reinterpret_cast<Slot<K> *>(s_wdyn);
+  unsigned char *const s_sdig = s_wdyn + (size_t)TILE * sizeof(Slot<K>);
+  __shared__ unsigned s_wc[W][256];
+  __shared__ unsigned s_tstart[256], s_wsum[8];
+  __shared__ u64 s_excl[256];
+  __shared__ unsigned s_tile, s_tcount, s_hist[256];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const bool owner = tid < 256;  // warps 0..7: thread tid owns digit tid
+  const unsigned lt = (1u << lane) - 1u;
+  const u64 n = min(*n_ptr, n_cap);
+  const u64 tiles = (n + TILE - 1) / TILE;
+  const u64 base_d = owner ? bases[tid] : 0ull;
+  if (owner) {
+    for (int x = 0; x < W; ++x) s_wc[x][tid] = 0;
+    s_hist[tid] = 0;
+  }
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();  // also orders the previous tile's write-out before reuse
+    const u64 tile = s_tile;
+    if (tile >= tiles) break;
+    const u64 wb = tile * TILE + (u64)w * PER_WARP;
+    K key[ITEMS];
+    u64 cnt[ITEMS];
+    int dig[ITEMS];
+    unsigned peers[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const u64 i = wb + (u64)j * 32 + lane;
+      key[j] = 0;
+      cnt[j] = 0;
+      if (i < n) load_slot(in, i, key[j], cnt[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
+      SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
+      dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
+      if (dig[j] >= 0) atomicAdd(&s_hist[dig[j]], 1u);
+    }
+    __syncthreads();
+    unsigned tcount_d = 0;
+    u64 *word = status + tile * 256 + tid;
+    if (owner) {  // publish this tile's count of digit tid
+      tcount_d = s_hist[tid];
+      s_hist[tid] = 0;
+      atomicExch(word, (epoch << 48) | (tile == 0 ? (1ull << 47) : 0ull) | tcount_d);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      peers[j] = __match_any_sync(0xffffffffu, dig[j] >= 0 ? dig[j] : 256 + lane);
+      if (dig[j] >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][dig[j]] += __popc(peers[j]);
+      __syncwarp();
+    }
+    if (owner) {  // look back for the tiles before this one
+      u64 excl = 0;
+      if (tile > 0) {
+        long long j = (long long)tile - 1;
+        unsigned spins = 0;
+        while (j >= 0) {
+          const u64 v = __ldcv(status + (u64)j * 256 + tid);
+          if ((v >> 48) != epoch) {
+            if (++spins > kSpinLimit) {
+              atomicOr(err, kErrTimeout);
+              break;
+            }
+            continue;
+          }
+          excl += v & kCountMask;
+          if (v >> 47 & 1ull) break;
+          --j;
+        }
+        atomicExch(word, (epoch << 48) | (1ull << 47) | (excl + tcount_d));
+      }
+      s_excl[tid] = base_d + excl;
+    }
+    __syncthreads();  // the per-warp counts are complete
+    unsigned x = tcount_d;
+    if (owner) {
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[w] = x;
+    }
+    __syncthreads();
+    if (owner) {  // tile-local start of digit tid, then each warp's base within it
+      unsigned start = x - tcount_d;
+      for (int q = 0; q < w; ++q) start += s_wsum[q];
+      s_tstart[tid] = start;
+      if (tid == 255) s_tcount = start + tcount_d;
+      for (int q = 0; q < W; ++q) {
+        const unsigned c = s_wc[q][tid];
+        s_wc[q][tid] = start;
+        start += c;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int d = dig[j];
+      if (d >= 0) {
+        const unsigned local = s_wc[w][d] + __popc(peers[j] & lt);
+        s_stage[local].key = key[j];
+        s_stage[local].cnt = cnt[j];
+        s_sdig[local] = (unsigned char)d;
+      }
+      __syncwarp();
+      if (d >= 0 && lane == __ffs(peers[j]) - 1) s_wc[w][d] += __popc(peers[j]);
+      __syncwarp();
+    }
+    __syncthreads();
+    const unsigned tcount = s_tcount;
+    for (unsigned i = tid; i < tcount; i += BLOCK) {
+      const int d = s_sdig[i];
+      const u64 pos = s_excl[d] + (i - s_tstart[d]);
+      if (pos < dst_cap) store_slot(out, pos, s_stage[i].key, s_stage[i].cnt);
+    }
+    if (owner)
+      for (int q = 0; q < W; ++q) s_wc[q][tid] = 0;
+  }
+}
+
 // ---- one pass with the next tile's records streamed in by the tensor memory accelerator ----
 // The same ranking and look-back as sweep_pass_kernel, but a block claims its next tile as soon
 // as it starts the current one and has the bulk-copy engine (cp.async.bulk) bring that tile's
@@ -666,10 +804,18 @@ int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *
     constexpr int TI = ITEMS * 3 / 4;  // items per thread of the bulk-copy pass
     constexpr size_t TSMEM = 2 * 256 * TI * sizeof(Slot<K>);
     const int GT = d.sms * 3;
+    // 64-bit records: 512-thread passes over 4096-record tiles
+    constexpr bool WIDE = sizeof(K) == 8;
+    constexpr size_t WSMEM = (size_t)512 * ITEMS * (sizeof(Slot<K>) + 1);
+    const int GW = d.sms * 2;
     for (int p = 0; p < passes; ++p) {
 #define CC_PASS(FK, SS)                                                                   \
   if (sw->tma)                                                                            \
     sweep_pass_tma_kernel<K, SK, TI, FK, SS><<<GT, 256, TSMEM, s>>>(                       \
+        sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,       \
+        sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);                                   \
+  else if (WIDE)                                                                          \
+    sweep_pass_wide_kernel<K, SK, ITEMS, FK, SS><<<GW, 512, WSMEM, s>>>(                    \
         sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,       \
         sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);                                   \
   else                                                                                    \
@@ -730,8 +876,22 @@ int allow_tma_smem() {
 }
 }  // namespace
 
+template <typename SK>
+int allow_wide_smem() {
+  constexpr int bytes = 512 * 8 * (int)(sizeof(Slot<u64>) + 1);
+  int r = 0;
+  r |= (int)cudaFuncSetAttribute(sweep_pass_wide_kernel<u64, SK, 8, true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  r |= (int)cudaFuncSetAttribute(sweep_pass_wide_kernel<u64, SK, 8, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  r |= (int)cudaFuncSetAttribute(sweep_pass_wide_kernel<u64, SK, 8, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return r;
+}
+
 int prepare_sort_kernels() {
   int r = allow_tma_smem<u64, u64, 6>() | allow_tma_smem<u64, u128, 6>();
+  r |= allow_wide_smem<u64>() | allow_wide_smem<u128>();
   r |= allow_tma_smem<u128, u64, 3>() | allow_tma_smem<u128, u128, 3>();
   return r;
 }
