@@ -36,9 +36,11 @@ import synth  # noqa: E402
 WORKLOAD = "ba20k_grid2x4"
 METRIC = "DP entries/s"
 UNIT = "entries/s"
-# dram bytes (read + write) of the dominant kernel per launch from an ncu capture of this
-# workload, or None when no capture matches the current kernel
-TRAFFIC = None
+# DRAM bytes (read + write) per launch of each node rule's kernels, from one ncu capture of this
+# workload at full size (profiles/launches_ba20k_grid2x4.md): the timed step's sort passes,
+# digit counts, reduce-by-key and hash forgets moved 116.21 GB over the forget group's 14
+# launches.  A group missing here (or captured before a kernel change) reports null.
+TRAFFIC = {"forget": 116.211e9 / 14}
 
 
 def peaks():
@@ -412,7 +414,7 @@ def main():
     total_kms = sum(x["ms"] for x in kern.values())
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC,
+            "traffic": TRAFFIC.get(dom),
             "bytes_per_launch": d["bytes"] / d["launches"],
             "ms_per_launch": d["ms"] / d["launches"],
             "groups": {g: {"ms_per_step": v["ms"] / args.steps, "share": v["ms"] / total_kms,
