@@ -193,6 +193,23 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def rank_seed(seed, rank):
+    """Colouring seed of a replica: every rank colours its own independent trials."""
+    return seed + 1000003 * rank
+
+
+def over_ranks(dist, torch, total_ms, entries, device):
+    """Whole-job figures of the replicas: the slowest rank's time (max) and all ranks' entries
+    (sum); dist None is one process."""
+    if not dist:
+        return float(total_ms), float(entries)
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([entries], device=device, dtype=torch.float64)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
+
+
 def pct(xs, q):
     """q-th percentile (nearest rank) of a nonempty list."""
     xs = sorted(xs)
@@ -336,7 +353,7 @@ def main():
     nF, edges, td = synth.make_pattern(w["pattern"])
     n = len(g[0]) - 1
     T, k = args.trials or w["trials"], w["k"]
-    seed = w["seed"] + 1000003 * rank
+    seed = rank_seed(w["seed"], rank)
     ctx = cc.Context(arena_bytes=args.arena_gb << 30, device=local)
     h = ctx.h
     cc.cc_load_graph(h, *g)
@@ -388,16 +405,7 @@ def main():
     torch.cuda.synchronize()
     launches = cc.cc_context_stats(h)[0] - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        ent = torch.tensor([entries], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ent)
-        entries_all = float(ent.item())
-    else:
-        entries_all = float(entries)
+    total_ms, entries_all = over_ranks(dist, torch, sum(step_ms), entries, "cuda")
     value = entries_all / (total_ms / 1000.0)
 
     # roofline of the dominant node rule (largest share of device time); sort passes and
