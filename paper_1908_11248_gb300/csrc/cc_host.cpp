@@ -598,8 +598,18 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         if (R->opts.profile) R->timings.back().candidates = cand;
         R->sizes[x] = total;
       }
-      // room for this introduce's entries: exact, or planned plus chunk slack
-      const u64 raw = planned ? room(plan->entries[x]) + chunk_slack : std::max<u64>(1, total);
+      // room for this introduce's entries: exact, or planned plus the holes chunked appends
+      // may leave (one partial chunk per warp, or per block for the block kernel); a warp's
+      // chunk shrinks for small tables so that those holes stay under a quarter of the entries
+      const bool warp_path = planned && (a.nnb <= 1 || grouped);
+      a.chunk = 256;
+      u64 slack = chunk_slack;
+      if (warp_path) {
+        const u64 warps = (u64)c->dev.sms * c->dev.blocks_per_sm * 8;
+        while (a.chunk > 32 && warps * a.chunk * 4 > plan->entries[x]) a.chunk >>= 1;
+        slack = warps * a.chunk;
+      }
+      const u64 raw = planned ? room(plan->entries[x]) + slack : std::max<u64>(1, total);
       if (planned) check(R->d_counters + x, room(plan->entries[x]));
       auto write_dense = [&](void *buf, u64 cap, int proj) -> int {
         a.out = TableDesc{buf, cap, nullptr, 0};

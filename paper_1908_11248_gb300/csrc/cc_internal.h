@@ -74,6 +74,7 @@ struct IntroArgs {
   unsigned long long *cand;  // mode 0: number of candidate vertices examined
   int *err;
   uint32_t ubit;             // 1 << u, tested against G.allow
+  unsigned chunk;            // warp kernels, mode 1: slots a warp reserves at a time (32..256)
 };
 
 struct ForgetArgs {

@@ -401,7 +401,10 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
 // candidate by a five-step binary search over the warp's prefix sums.  Outputs go to per-warp
 // chunks of the output (MODE 1) or into the parent forget's hash table (MODE 2).  No block
 // barrier is involved.
-constexpr u64 kWarpChunk = 256;
+// A warp reserves a.chunk output slots at a time (a power of two in [32, 256], chosen by the
+// planner from the table's planned size so that the holes left in the warps' last chunks stay a
+// small part of the table).
+constexpr u64 kWarpChunkMax = 256;
 
 __device__ __forceinline__ u64 shfl_key(u64 v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
@@ -422,7 +425,8 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
   const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
-  u64 cbase = 0, cfill = kWarpChunk;  // warp-uniform chunk state
+  const u64 chunk = a.chunk;
+  u64 cbase = 0, cfill = chunk;  // warp-uniform chunk state
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
   for (u64 base = wid * 32; base < bound; base += warps * 32) {
@@ -486,13 +490,13 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
         const u64 tot = __popc(bal);
         const u64 idx = cfill + __popc(bal & lt);
         u64 nb = 0;
-        const bool spill = cfill + tot > kWarpChunk;
+        const bool spill = cfill + tot > chunk;
         if (spill) {
-          if (lane == 0) nb = atomicAdd(a.cursor, kWarpChunk);
+          if (lane == 0) nb = atomicAdd(a.cursor, chunk);
           nb = __shfl_sync(0xffffffffu, nb, 0);
         }
         if (valid) {
-          const u64 pos = idx < kWarpChunk ? cbase + idx : nb + (idx - kWarpChunk);
+          const u64 pos = idx < chunk ? cbase + idx : nb + (idx - chunk);
           ++produced;
           if (pos < a.out.cap)
             store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
         }
         if (spill) {
           cbase = nb;
-          cfill = cfill + tot - kWarpChunk;
+          cfill = cfill + tot - chunk;
         } else {
           cfill += tot;
         }
@@ -515,8 +519,8 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
       }
     }
   }
-  if (MODE == 1 && cfill < kWarpChunk)  // the unused tail of the warp's last chunk: holes
-    for (u64 j = cfill + lane; j < kWarpChunk; j += 32)
+  if (MODE == 1 && cfill < chunk)  // the unused tail of the warp's last chunk: holes
+    for (u64 j = cfill + lane; j < chunk; j += 32)
       if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
   if (full) atomicOr(a.err, kErrOverflow);
   for (int o = 16; o > 0; o >>= 1) {
@@ -545,18 +549,19 @@ __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey
                                           u64 &produced, u64 &fresh, bool &full) {
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
   if (MODE == 1) {
+    const u64 chunk = a.chunk;
     const unsigned bal = __ballot_sync(0xffffffffu, valid);
     if (!bal) return;
     const u64 tot = __popc(bal);
     const u64 idx = cfill + __popc(bal & lt);
     u64 nb = 0;
-    const bool spill = cfill + tot > kWarpChunk;
+    const bool spill = cfill + tot > chunk;
     if (spill) {
-      if (lane == 0) nb = atomicAdd(a.cursor, kWarpChunk);
+      if (lane == 0) nb = atomicAdd(a.cursor, chunk);
       nb = __shfl_sync(0xffffffffu, nb, 0);
     }
     if (valid) {
-      const u64 pos = idx < kWarpChunk ? cbase + idx : nb + (idx - kWarpChunk);
+      const u64 pos = idx < chunk ? cbase + idx : nb + (idx - chunk);
       ++produced;
       if (pos < a.out.cap)
         store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
@@ -565,7 +570,7 @@ __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey
     }
     if (spill) {
       cbase = nb;
-      cfill = cfill + tot - kWarpChunk;
+      cfill = cfill + tot - chunk;
     } else {
       cfill += tot;
     }
@@ -590,7 +595,8 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
   const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + wib;
   const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
-  u64 cbase = 0, cfill = kWarpChunk;
+  const u64 chunk = a.chunk;
+  u64 cbase = 0, cfill = chunk;
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
   for (u64 base = wid * 32; base < bound; base += warps * 32) {
@@ -700,8 +706,8 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
     }
     __syncwarp();  // buf is rewritten by the next window
   }
-  if (MODE == 1 && cfill < kWarpChunk)
-    for (u64 j = cfill + lane; j < kWarpChunk; j += 32)
+  if (MODE == 1 && cfill < chunk)
+    for (u64 j = cfill + lane; j < chunk; j += 32)
       if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
   if (full) atomicOr(a.err, kErrOverflow);
   for (int o = 16; o > 0; o >>= 1) {
