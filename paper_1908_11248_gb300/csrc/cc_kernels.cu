@@ -404,7 +404,6 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
 // A warp reserves a.chunk output slots at a time (a power of two in [32, 256], chosen by the
 // planner from the table's planned size so that the holes left in the warps' last chunks stay a
 // small part of the table).
-constexpr u64 kWarpChunkMax = 256;
 
 __device__ __forceinline__ u64 shfl_key(u64 v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
