@@ -299,6 +299,14 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_node,
                    int32_t *h_kind, float *h_ms, uint64_t *h_candidates, int32_t *n_out);
 
+/* Failure detection check (no counterpart in the paper): every device-side wait of the library
+ * (the sort passes' look-back, the bulk-copy barriers) polls a bounded number of times, then
+ * records CC_ETIMEOUT in the run's error word and returns, leaving the context usable.  This call
+ * makes one such wait run out on purpose: a warp polls a device word that nothing sets, `polls`
+ * times, and the error word is read back.  Returns CC_ETIMEOUT when the wait gave up as it
+ * should; CC_EINVAL (polls 0), CC_EBUSY, CC_ENOMEM, CC_ECUDA otherwise. */
+int cc_probe_bounded_wait(cc_ctx *ctx, uint32_t polls);
+
 /* Context counters: kernel launches issued since cc_create, arena bytes in use and arena size. */
 int cc_context_stats(cc_ctx *ctx, uint64_t *kernel_launches, uint64_t *arena_used,
                      uint64_t *arena_size);

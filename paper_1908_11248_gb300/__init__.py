@@ -32,7 +32,7 @@ EXPORTS = [
     "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
     "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
-    "cc_load_pattern_masked", "cc_enumerate_sets",
+    "cc_load_pattern_masked", "cc_enumerate_sets", "cc_probe_bounded_wait",
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
@@ -92,6 +92,7 @@ def lib():
         "cc_table_dump": ([P, i32, i32, u64, P, P, P, P, P], ctypes.c_int),
         "cc_enumerate": ([P, i32, u64, P, P, P], ctypes.c_int),
         "cc_enumerate_sets": ([P, i32, u64, P, P, P], ctypes.c_int),
+        "cc_probe_bounded_wait": ([P, ctypes.c_uint32], ctypes.c_int),
         "cc_release": ([P, i32], ctypes.c_int),
         "cc_serve_start": ([P, sz, i32], ctypes.c_int),
         "cc_serve_submit": ([P, i32, u64, i32, i32, P], ctypes.c_int),
@@ -372,6 +373,11 @@ def cc_run_mode(ctx, run: int) -> str:
     m = ctypes.c_int32(0)
     _check(lib().cc_run_mode(ctx, run, ctypes.byref(m)), "cc_run_mode")
     return RUN_MODES[m.value]
+
+
+def cc_probe_bounded_wait(ctx, polls: int) -> int:
+    """Return code of a bounded device wait made to run out (CC_ETIMEOUT = -4 expected)."""
+    return int(lib().cc_probe_bounded_wait(ctx, polls))
 
 
 def cc_context_stats(ctx):

@@ -1996,6 +1996,31 @@ int cc_run_timings(cc_ctx *ctx, int32_t run_id, int32_t capacity, int32_t *h_nod
   return CC_OK;
 }
 
+int cc_probe_bounded_wait(cc_ctx *ctx, uint32_t polls) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c || polls == 0) return CC_EINVAL;
+  if (cc::serve_active(c)) return CC_EBUSY;
+  u64 *flag = arena_alloc<u64>(c, 1);
+  int *err = arena_alloc<int>(c, 1);
+  int rc = CC_OK, herr = 0;
+  if (!flag || !err) {
+    rc = CC_ENOMEM;
+  } else if (cudaMemsetAsync(flag, 0, sizeof(u64), c->stream) != cudaSuccess ||
+             cudaMemsetAsync(err, 0, sizeof(int), c->stream) != cudaSuccess ||
+             cc::launch_wait_probe(c->stream, flag, polls, err) != 0 ||
+             cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    rc = CC_ECUDA;
+  } else {
+    c->launches++;
+    if (herr & cc::kErrTimeout) rc = CC_ETIMEOUT;
+  }
+  c->arena.release(flag);
+  c->arena.release(err);
+  return rc;
+}
+
 int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
   Ctx *c = (Ctx *)ctx;
   if (c && cc::serve_active(c)) return CC_EBUSY;

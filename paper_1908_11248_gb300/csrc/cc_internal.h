@@ -175,6 +175,8 @@ int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
 // appends in per-warp chunks from a.cursor (holes left where chunks are not filled), mode 2
 // adds into the parent forget's hash table.
 int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a);
+// one warp polls *flag (which nothing sets) `polls` times, then sets kErrTimeout in *err
+int launch_wait_probe(cudaStream_t s, const unsigned long long *flag, unsigned polls, int *err);
 int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
                 uint8_t *deg8);
 // Grouped introduce (child sorted by bag-neighbour images), warp by warp, for planned runs;

@@ -720,6 +720,14 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   }
 }
 
+// A wait of the kind the sort passes' look-back makes, on a word that nothing sets: each
+// thread polls it at most `polls` times, then records a timeout in the error word and returns.
+__global__ void wait_probe_kernel(const u64 *flag, unsigned polls, int *err) {
+  for (unsigned i = 0; i < polls; ++i)
+    if (__ldcv(flag) != 0) return;
+  atomicOr(err, kErrTimeout);
+}
+
 // exclusive scan of the per-block counts (one block); writes bases and the grand total
 __global__ void scan_blocks_kernel(const u64 *cnt, int nblk, u64 *base, u64 *total) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -990,6 +998,12 @@ int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const 
     }
   }
 #undef CC_IW
+  return (int)cudaGetLastError();
+}
+
+int launch_wait_probe(cudaStream_t s, const unsigned long long *flag, unsigned polls,
+                      int *err) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(flag, polls, err);
   return (int)cudaGetLastError();
 }
 

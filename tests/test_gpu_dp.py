@@ -473,3 +473,21 @@ def test_allowed_mappings_match_oracle(ctx):
         cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
     assert err.value.code == -1
     cc.cc_release_colors(ctx.h, cid)
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """Failure detection without a fault: a device wait on a word that nothing sets gives up
+    after its bound and reports CC_ETIMEOUT through the error word; the context then runs a DP
+    to the oracle's result."""
+    import time
+
+    t0 = time.time()
+    assert cc.cc_probe_bounded_wait(ctx.h, 1 << 16) == -4
+    assert time.time() - t0 < 30
+    w = synth.WORKLOADS["er200_c5"]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    r = gpu_dp(ctx, g, pat, seed=w["seed"], trials=1, k=5)
+    ref = oracle.run_dp(g, pat, oracle.colors(200, 1, 5, w["seed"]), 5)
+    assert np.array_equal(r["count"], ref.count)
+    release(ctx, r)
