@@ -53,7 +53,7 @@ def _load():
     lib.or_color.restype = None
     lib.or_nice_td.argtypes = [i32, i32, P, i32, P, P, P, i32, P, P, P, P, P, P]
     lib.or_nice_td.restype = i32
-    lib.or_dp_run.argtypes = [i32, P, P, i32, i32, P, i32, P, P, P, P, i32, i32, i32, P]
+    lib.or_dp_run.argtypes = [i32, P, P, i32, i32, P, i32, P, P, P, P, i32, i32, i32, P, i32]
     lib.or_dp_run.restype = P
     lib.or_dp_free.argtypes = [P]
     lib.or_dp_free.restype = None
@@ -162,10 +162,13 @@ class Run:
         return out[:min(limit, tot)], int(tot), int(per.value)
 
 
-def run_dp(graph, pattern, colours, k: int, degree_filter: bool = True, allow=None) -> Run:
+def run_dp(graph, pattern, colours, k: int, degree_filter: bool = True, allow=None,
+           distance_prune: bool = False) -> Run:
     """Bottom-up dynamic programme of Section 3.1 for every row of ``colours`` (uint8[T, n]).
     ``allow`` (uint32[n], optional): bit y of allow[x] lets pattern vertex y map to host vertex x
-    (Section 3.2, masking unprofitable mappings)."""
+    (Section 3.2, masking unprofitable mappings).  ``distance_prune``: an introduced vertex with
+    no bag neighbour whose nearest same-component bag vertex w is at F-distance 2 takes only the
+    host vertices within distance 2 of phi(w) (Section 3.2, mapping expansion)."""
     lib = _load()
     row_ptr, col = graph
     nF, edges, td = pattern
@@ -182,7 +185,7 @@ def run_dp(graph, pattern, colours, k: int, degree_filter: bool = True, allow=No
     h = lib.or_dp_run(len(rp) - 1, _ptr(rp), _ptr(cl), nF, len(e) // 2,
                       _ptr(e) if len(e) else None, nb, _ptr(bp), _ptr(bv), _ptr(par),
                       _ptr(colours), T, k, int(bool(degree_filter)),
-                      _ptr(am) if am is not None else None)
+                      _ptr(am) if am is not None else None, int(bool(distance_prune)))
     if not h:
         raise ValueError("oracle: invalid input")
     return Run(h, nF, T)

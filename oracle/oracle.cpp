@@ -25,6 +25,11 @@
 //   * the extended input of that paragraph, per host vertex the set of pattern vertices that may
 //     be mapped to it, is an optional mask array (bit y of allow[x]: y may map to x); maps that
 //     break it are not counted anywhere.
+//   * the distance bound of Section 3.2 (mapping expansion) is a switch: an introduced vertex u
+//     with no neighbour in the bag, whose nearest bag vertex w of its F-component is at
+//     F-distance 2, takes only the host vertices within distance 2 of phi(w); farther anchors,
+//     and vertices of another component, take every host vertex.  It never changes the root
+//     result.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -91,6 +96,18 @@ struct Pattern {
   int32_t n = 0;
   std::vector<std::vector<char>> adj;  // adjacency matrix of F
   std::vector<int32_t> deg;
+  // breadth-first distances from a in F (-1: another component)
+  std::vector<int32_t> dist(int32_t a) const {
+    std::vector<int32_t> d(n, -1), q{a};
+    d[a] = 0;
+    for (size_t h = 0; h < q.size(); ++h)
+      for (int32_t b = 0; b < n; ++b)
+        if (adj[q[h]][b] && d[b] < 0) {
+          d[b] = d[q[h]] + 1;
+          q.push_back(b);
+        }
+    return d;
+  }
 };
 
 Pattern make_pattern(int32_t nF, int32_t mF, const int32_t *edges) {
@@ -290,6 +307,7 @@ struct Run {
   NiceTD T;
   int32_t k = 0, trials = 0;
   bool degree_filter = true;
+  bool distance_prune = false;
   std::vector<uint32_t> allow;           // empty: every mapping allowed
   std::vector<uint8_t> colours;          // trials * n
   std::vector<std::vector<Table>> D;     // [trial][node]
@@ -324,6 +342,20 @@ void run_trial(Run &R, int32_t t) {
       std::vector<int32_t> nb_slots;  // slots in the child tuple of u's bag neighbours
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (F.adj[u][ch.bag[s]]) nb_slots.push_back((int32_t)s);
+      // distance bound: the bag vertex of u's component nearest to u, if it is at distance 2
+      int32_t near_slot = -1;
+      if (nb_slots.empty() && R.distance_prune) {
+        const std::vector<int32_t> du = F.dist(u);
+        int32_t best = -1;
+        for (size_t s = 0; s < ch.bag.size(); ++s) {
+          const int32_t d = du[ch.bag[s]];
+          if (d >= 0 && (best < 0 || d < best)) {
+            best = d;
+            near_slot = (int32_t)s;
+          }
+        }
+        if (best != 2) near_slot = -1;
+      }
       for (const auto &e : D[nd.child0]) {
         const std::vector<int32_t> &phi_c = e.first.first;
         uint32_t Cc = e.first.second;
@@ -331,6 +363,16 @@ void run_trial(Run &R, int32_t t) {
         if (!nb_slots.empty()) {
           int32_t a = phi_c[nb_slots[0]];
           cand.assign(G.col.begin() + G.row_ptr[a], G.col.begin() + G.row_ptr[a + 1]);
+        } else if (near_slot >= 0) {  // the host vertices within distance 2 of phi(w)
+          const int32_t a = phi_c[near_slot];
+          cand.push_back(a);
+          for (int32_t i = G.row_ptr[a]; i < G.row_ptr[a + 1]; ++i) {
+            const int32_t b = G.col[i];
+            cand.push_back(b);
+            cand.insert(cand.end(), G.col.begin() + G.row_ptr[b], G.col.begin() + G.row_ptr[b + 1]);
+          }
+          std::sort(cand.begin(), cand.end());
+          cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
         } else {
           cand.resize(G.n);
           for (int32_t v = 0; v < G.n; ++v) cand[v] = v;
@@ -563,7 +605,8 @@ int32_t or_nice_td(int32_t nF, int32_t mF, const int32_t *edges, int32_t nbags,
 void *or_dp_run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t nF, int32_t mF,
                 const int32_t *edges, int32_t nbags, const int32_t *bag_ptr,
                 const int32_t *bag_vtx, const int32_t *parent, const uint8_t *colours,
-                int32_t trials, int32_t k, int32_t degree_filter, const uint32_t *allow) {
+                int32_t trials, int32_t k, int32_t degree_filter, const uint32_t *allow,
+                int32_t distance_prune) {
   if (nF < 1 || nF > 32 || k < nF || k > 32 || trials < 1 || n < 0) return nullptr;
   Run *R = new Run();
   R->G = make_graph(n, row_ptr, col);
@@ -575,6 +618,7 @@ void *or_dp_run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t n
   R->k = k;
   R->trials = trials;
   R->degree_filter = degree_filter != 0;
+  R->distance_prune = distance_prune != 0;
   if (allow) R->allow.assign(allow, allow + n);
   R->colours.assign(colours, colours + (size_t)trials * n);
   R->D.resize(trials);

@@ -464,3 +464,71 @@ def test_reconstruction(pat):
     # truncation keeps the lexicographically smallest
     L5, tot5, _ = run.enumerate(5)
     assert tot5 == tot and np.array_equal(L5, L[:5])
+
+
+# ------------------------------------------------------------------------------------------
+# the distance bound of Section 3.2 (mapping expansion)
+# ------------------------------------------------------------------------------------------
+
+def _gdist(g, a, r):
+    """Host vertices within distance r of a (plain breadth-first search)."""
+    G = brute.adj_sets(*g)
+    seen, frontier = {a}, {a}
+    for _ in range(r):
+        frontier = {y for x in frontier for y in G[x]} - seen
+        seen |= frontier
+    return seen
+
+
+def test_distance_bound_table_by_definition():
+    """Path 0-1-2 with bags {0,2} under {0,1,2}: vertex 2 is introduced next to 0 at F-distance
+    2 with no bag neighbour, so the pruned table is the definition's table restricted to
+    phi(2) within distance 2 of phi(0); the root is unchanged."""
+    e = np.array([(0, 1), (1, 2)], np.int32)
+    td = ([[0, 2], [0, 1, 2]], [1, -1])
+    nodes = oracle.nice_td(3, e, td)
+    x = next(i for i, nd in enumerate(nodes) if nd[0] == 1 and nd[3] == 2 and len(nd[4]) == 2)
+    vs = brute.vstar(nodes)
+    for seed in range(3):
+        g = synth.erdos_renyi(12, 0.25, 40 + seed)
+        G = brute.adj_sets(*g)
+        zeta = np.random.default_rng(seed).integers(0, 3, size=(2, 12)).astype(np.uint8)
+        plain = oracle.run_dp(g, (3, e, td), zeta, 3, degree_filter=False)
+        pruned = oracle.run_dp(g, (3, e, td), zeta, 3, degree_filter=False, distance_prune=True)
+        assert np.array_equal(plain.count, pruned.count)
+        assert pruned.node_sizes[:, x].sum() < plain.node_sizes[:, x].sum()
+        for t in range(2):
+            want = brute.node_table(G, 3, e, zeta[t], nodes[x][4], vs[x])
+            want = {k: v for k, v in want.items() if k[0][1] in _gdist(g, k[0][0], 2)}
+            phi, mask, cnt = pruned.table(t, x, 2)
+            got = {(tuple(int(v) for v in phi[i]), int(mask[i])): int(cnt[i])
+                   for i in range(len(mask))}
+            assert got == want
+
+
+@pytest.mark.parametrize("pat", [synth.random_partial_ktree(7, 3, 2),
+                                 synth.random_partial_ktree(8, 2, 9),
+                                 synth.random_partial_ktree(8, 3, 4), synth.pattern_D(),
+                                 (4, np.array([(0, 1), (1, 2), (2, 3)], np.int32),
+                                  ([[0, 3], [0, 1, 3], [1, 2, 3]], [1, 2, -1]))])
+def test_distance_bound_keeps_root_and_shrinks_tables(pat):
+    """On patterns whose decompositions introduce vertices away from their bag: root counts
+    and enumerations are those without the bound, and every table is a subset (counts no
+    larger) of the unbounded one."""
+    nF = pat[0]
+    g = synth.erdos_renyi(30, 0.2, 8)
+    zeta = oracle.colors(30, 3, nF, seed=4)
+    a = oracle.run_dp(g, pat, zeta, nF)
+    b = oracle.run_dp(g, pat, zeta, nF, distance_prune=True)
+    assert np.array_equal(a.count, b.count) and np.array_equal(a.exists, b.exists)
+    assert np.array_equal(a.enumerate(10 ** 6)[0], b.enumerate(10 ** 6)[0])
+    assert (b.node_sizes <= a.node_sizes).all()
+    nodes = oracle.nice_td(*pat)
+    for t in range(3):
+        for x, nd in enumerate(nodes):
+            pa, ma, ca = a.table(t, x, len(nd[4]))
+            pb, mb, cb = b.table(t, x, len(nd[4]))
+            A = {(tuple(int(v) for v in pa[i]), int(ma[i])): int(ca[i]) for i in range(len(ma))}
+            for i in range(len(mb)):
+                k = (tuple(int(v) for v in pb[i]), int(mb[i]))
+                assert k in A and int(cb[i]) <= A[k]
