@@ -158,10 +158,14 @@ typedef struct {
                          /*    per pass (decoupled look-back); 2: as 1, each block bringing its */
                          /*    next tile into shared memory by bulk copy while it works on the  */
                          /*    current one; 0: histogram+scan+scatter passes                    */
+  int32_t distance_prune; /* 1: an introduced vertex with no bag neighbour whose nearest bag   */
+                         /*    vertex w of its F-component is at F-distance 2 takes only the   */
+                         /*    host vertices within distance 2 of phi(w) (Section 3.2, mapping  */
+                         /*    expansion); root results are unchanged, tables shrink            */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
- * 0.5, block 256, profile 0, group 1, sort_sweep 1). */
+ * 0.5, block 256, profile 0, group 1, sort_sweep 1, distance_prune 0). */
 void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in

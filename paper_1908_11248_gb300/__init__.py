@@ -55,7 +55,7 @@ class cc_run_opts(ctypes.Structure):
                 ("fuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("load_factor", ctypes.c_float), ("block", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("group", ctypes.c_int32),
-                ("sort_sweep", ctypes.c_int32)]
+                ("sort_sweep", ctypes.c_int32), ("distance_prune", ctypes.c_int32)]
 
 
 _lib = None

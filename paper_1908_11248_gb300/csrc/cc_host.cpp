@@ -375,6 +375,7 @@ int pos_in(const std::vector<int32_t> &bag, int u) {
 
 // ---- the planner: node by node in post-order, exact capacities ----------------------------
 int finish_run(Ctx *c, Run *R);
+int near_slot2(const Pattern &P, int u, const std::vector<int32_t> &child_bag);
 
 // Runs every node of the nice decomposition in post-order (Section 3.1).
 //
@@ -555,6 +556,17 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       a.nnb = 0;
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
+      if (a.nnb == 0 && R->opts.distance_prune && c->d_ball_ptr) {
+        // distance bound: candidates are the ball of radius 2 around the nearest bag vertex's
+        // image, walked like an adjacency list (no other bag neighbour is then checked)
+        const int s2 = near_slot2(P, nd.vertex, ch.bag);
+        if (s2 >= 0) {
+          a.nnb = 1;
+          a.nb_slot[0] = s2;
+          a.G.row_ptr = c->d_ball_ptr;
+          a.G.col = c->d_ball_col;
+        }
+      }
       a.degF = df ? P.deg[nd.vertex] : 0;
       a.ubit = 1u << nd.vertex;
       a.err = R->d_err;
@@ -1008,6 +1020,75 @@ long long csr_fingerprint(int32_t n, const int32_t *row_ptr, const int32_t *col)
   return (long long)(h | 1);
 }
 
+// The distance bound of Section 3.2 (mapping expansion): for a vertex u introduced with no
+// neighbour in the bag, the slot (in the child bag) of the bag vertex of u's F-component nearest
+// to u, if that vertex is at F-distance 2; else -1 (no bound: every host vertex is a candidate).
+int near_slot2(const Pattern &P, int u, const std::vector<int32_t> &child_bag) {
+  std::vector<int> d(P.nF, -1), q{u};
+  d[u] = 0;
+  for (size_t h = 0; h < q.size(); ++h)
+    for (int b = 0; b < P.nF; ++b)
+      if ((P.adj[q[h]] >> b & 1u) && d[b] < 0) {
+        d[b] = d[q[h]] + 1;
+        q.push_back(b);
+      }
+  int best = -1, slot = -1;
+  for (size_t s = 0; s < child_bag.size(); ++s) {
+    const int dd = d[child_bag[s]];
+    if (dd >= 0 && (best < 0 || dd < best)) {
+      best = dd;
+      slot = (int)s;
+    }
+  }
+  return best == 2 ? slot : -1;
+}
+
+// Builds, once per graph, the CSR of every host vertex's ball of radius 2 (itself, its
+// neighbours and theirs, each once, increasing) in the context's arena.
+int ensure_ball2(Ctx *c) {
+  if (c->d_ball_ptr) return CC_OK;
+  const int32_t n = c->n;
+  std::vector<int32_t> ptr(n + 1, 0), col, stamp(n, -1), one;
+  for (int32_t s = 0; s < n; ++s) {
+    one.clear();
+    auto add = [&](int32_t v) {
+      if (stamp[v] != s) {
+        stamp[v] = s;
+        one.push_back(v);
+      }
+    };
+    add(s);
+    for (int32_t i = c->h_row_ptr[s]; i < c->h_row_ptr[s + 1]; ++i) {
+      const int32_t b = c->h_col[i];
+      add(b);
+      for (int32_t j = c->h_row_ptr[b]; j < c->h_row_ptr[b + 1]; ++j) add(c->h_col[j]);
+    }
+    std::sort(one.begin(), one.end());
+    if (col.size() + one.size() > (size_t)INT32_MAX) return CC_ENOMEM;
+    col.insert(col.end(), one.begin(), one.end());
+    ptr[s + 1] = (int32_t)col.size();
+  }
+  int32_t *dp = (int32_t *)c->arena.alloc(((size_t)n + 1) * sizeof(int32_t));
+  int32_t *dc = (int32_t *)c->arena.alloc(std::max<size_t>(1, col.size()) * sizeof(int32_t));
+  if (!dp || !dc) {
+    c->arena.release(dp);
+    c->arena.release(dc);
+    return CC_ENOMEM;
+  }
+  if (cudaMemcpyAsync(dp, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      (!col.empty() && cudaMemcpyAsync(dc, col.data(), col.size() * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, c->stream) != cudaSuccess) ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    c->arena.release(dp);
+    c->arena.release(dc);
+    return CC_ECUDA;
+  }
+  c->d_ball_ptr = dp;
+  c->d_ball_col = dc;
+  return CC_OK;
+}
+
 int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc_run_opts *opts,
              std::unique_ptr<Run> &R, std::vector<long long> &key) {
   auto pi = c->patterns.find(pid);
@@ -1015,6 +1096,20 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
   const Pattern &P = pi->second;
   if (col.k < P.nF) return CC_EINVAL;
   if (P.allow_fp && P.allow_fp != c->graph_fp) return CC_EINVAL;  // masks of another graph
+  if (opts && opts->distance_prune) {  // the distance bound needs the graph's radius-2 balls
+    bool need = false;
+    for (const auto &nd : P.nodes)
+      if (nd.type == 1) {
+        const auto &cb = P.nodes[nd.child0].bag;
+        bool nb = false;
+        for (int32_t w : cb) nb = nb || (P.adj[nd.vertex] >> w & 1u);
+        need = need || (!nb && near_slot2(P, nd.vertex, cb) >= 0);
+      }
+    if (need) {
+      const int rc = ensure_ball2(c);
+      if (rc) return rc;
+    }
+  }
   R.reset(new Run());
   cc_default_opts(&R->opts);
   if (opts) R->opts = *opts;
@@ -1057,7 +1152,7 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
 std::vector<long long> plan_key(const Ctx *c, int32_t pid, int32_t trials, int32_t k,
                                 const cc_run_opts &o) {
   return {pid, c->graph_fp, trials, k, o.degree_filter, o.fuse, o.group, o.block,
-          (long long)(o.load_factor * 1000), o.sort_sweep};
+          (long long)(o.load_factor * 1000), o.sort_sweep, o.distance_prune};
 }
 
 // init_run for colouring id cid of the context, which the run then holds a reference to.
@@ -1513,7 +1608,6 @@ const char *cc_strerror(int code) {
 void cc_default_opts(cc_run_opts *o) {
   o->degree_filter = 1;
   o->retain = 0;
-  o->fuse = 1;
   o->use_graph = 0;
   o->load_factor = 0.5f;
   o->block = 256;
@@ -1521,6 +1615,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->group = 1;
   o->fuse = 2;
   o->sort_sweep = 1;
+  o->distance_prune = 0;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
@@ -1613,6 +1708,9 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   c->arena.release(c->d_row_ptr);
   c->arena.release(c->d_col);
   c->arena.release(c->d_deg8);
+  c->arena.release(c->d_ball_ptr);
+  c->arena.release(c->d_ball_col);
+  c->d_ball_ptr = c->d_ball_col = nullptr;
   c->d_row_ptr = arena_alloc<int32_t>(c, (size_t)n + 1);
   c->d_col = arena_alloc<int32_t>(c, std::max<int64_t>(1, m2));
   c->d_deg8 = arena_alloc<uint8_t>(c, std::max<int64_t>(1, n));

@@ -219,6 +219,8 @@ struct Ctx {
   int32_t *d_row_ptr = nullptr, *d_col = nullptr;
   uint8_t *d_deg8 = nullptr;  // min(degree, 255) per vertex
   std::vector<int32_t> h_row_ptr, h_col;
+  // per vertex the vertices within distance 2 (CSR, built on first use by the distance bound)
+  int32_t *d_ball_ptr = nullptr, *d_ball_col = nullptr;
   int *d_err = nullptr;
   u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
   // content fingerprint of the loaded graph: plans stay valid while the graph's content is the

@@ -491,3 +491,39 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     ref = oracle.run_dp(g, pat, oracle.colors(200, 1, 5, w["seed"]), 5)
     assert np.array_equal(r["count"], ref.count)
     release(ctx, r)
+
+
+@pytest.mark.parametrize("fuse", [2, 1, 0])
+def test_distance_bound_matches_oracle(ctx, fuse):
+    """distance_prune (Section 3.2, mapping expansion): an introduced vertex whose nearest
+    same-component bag vertex is two steps away takes only the radius-2 ball of that vertex's
+    image.  Counts, table sizes (exact and planned) and the enumeration equal the oracle's with
+    the same bound; the root equals the unbounded run's."""
+    n = 300
+    g = synth.erdos_renyi(n, 6.0 / n, 12)
+    pats = [(3, np.array([(0, 1), (1, 2)], np.int32), ([[0, 2], [0, 1, 2]], [1, -1])),
+            synth.random_partial_ktree(8, 3, 4), synth.random_partial_ktree(7, 3, 2)]
+    cc.cc_load_graph(ctx.h, *g)
+    shrunk = False
+    for pat in pats:
+        nF = pat[0]
+        z = oracle.colors(n, 2, nF, seed=31)
+        ref = oracle.run_dp(g, pat, z, nF, distance_prune=True)
+        plain = oracle.run_dp(g, pat, z, nF)
+        assert np.array_equal(ref.count, plain.count)
+        shrunk = shrunk or int(ref.node_sizes.sum()) < int(plain.node_sizes.sum())
+        pid = cc.cc_load_pattern(ctx.h, *pat)
+        cid = cc.cc_set_colors(ctx.h, z, nF)
+        N, _ = cc.cc_pattern_info(ctx.h, pid)
+        for want in ("exact", "planned"):
+            run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(fuse=fuse, distance_prune=1))
+            assert cc.cc_run_mode(ctx.h, run) == want
+            assert np.array_equal(cc.cc_count(ctx.h, run, 2), ref.count)
+            assert np.array_equal(cc.cc_table_stats(ctx.h, run, N)[0], ref.node_sizes.sum(axis=0))
+            cc.cc_release(ctx.h, run)
+        run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts(retain=1, distance_prune=1))
+        lst, _ = cc.cc_enumerate(ctx.h, run, 10 ** 6, nF)
+        assert np.array_equal(lst, ref.enumerate(10 ** 6)[0])
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
+    assert shrunk
