@@ -18,7 +18,9 @@
  *   - Colours are 0-based; bit i of a colour set is colour i (Section 3.2).  k >= n_F, k <= 32.
  *   - One context is driven by one host thread at a time, except the cc_serve_* functions,
  *     which are thread-safe.
- *   - All device work runs on the stream given to cc_create, in the order of the calls.
+ *   - All device work is ordered on the stream given to cc_create, in the order of the calls
+ *     (a replayed graph's branches fork from it and join it again); a running server issues its
+ *     queries on streams of its own.
  */
 #ifndef CC_H
 #define CC_H
