@@ -535,21 +535,24 @@ def test_distance_bound_keeps_root_and_shrinks_tables(pat):
 
 
 def test_masks_and_distance_bound_together():
-    """Allowed mappings and the distance bound compose: the root and the enumeration are those
-    of the masks alone, and the brute-force count restricted to allowed maps."""
-    pat = synth.random_partial_ktree(6, 3, 11)
-    nF, e, td = pat
-    g = synth.erdos_renyi(9, 0.5, 21)
+    """Allowed mappings and the distance bound compose: on a path whose decomposition
+    introduces 2 next to 0 (F-distance 2), the bounded run's tables are smaller, its root and
+    enumeration are those of the masks alone, and its counts are the brute-force counts of
+    allowed colourful embeddings."""
+    e = np.array([(0, 1), (1, 2), (2, 3)], np.int32)
+    pat = (4, e, ([[0, 2], [0, 1, 2], [2, 3]], [1, -1, 1]))
+    g = synth.erdos_renyi(9, 0.6, 1)
     G = brute.adj_sets(*g)
-    rng = np.random.default_rng(2)
-    allow = np.array([sum(1 << y for y in range(nF) if rng.random() < 0.8) for _ in range(9)],
+    rng = np.random.default_rng(1)
+    allow = np.array([sum(1 << y for y in range(4) if rng.random() < 0.85) for _ in range(9)],
                      np.uint32)
-    zeta = rng.integers(0, nF, size=(2, 9)).astype(np.uint8)
-    a = oracle.run_dp(g, pat, zeta, nF, allow=allow, degree_filter=False)
-    b = oracle.run_dp(g, pat, zeta, nF, allow=allow, degree_filter=False, distance_prune=True)
-    assert np.array_equal(a.count, b.count)
+    zeta = rng.integers(0, 4, size=(2, 9)).astype(np.uint8)
+    a = oracle.run_dp(g, pat, zeta, 4, allow=allow, degree_filter=False)
+    b = oracle.run_dp(g, pat, zeta, 4, allow=allow, degree_filter=False, distance_prune=True)
+    assert b.node_sizes.sum() < a.node_sizes.sum()
+    assert np.array_equal(a.count, b.count) and int(b.count.min()) > 0
     assert np.array_equal(a.enumerate(10 ** 6)[0], b.enumerate(10 ** 6)[0])
     for t in range(2):
-        want = sum(1 for m in brute.embeddings(G, nF, e, zeta[t])
+        want = sum(1 for m in brute.embeddings(G, 4, e, zeta[t])
                    if all((int(allow[m[y]]) >> y) & 1 for y in m))
         assert int(b.count[t]) == want
