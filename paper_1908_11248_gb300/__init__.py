@@ -23,6 +23,7 @@ LEAF, INTRODUCE, FORGET, JOIN = 0, 1, 2, 3
 
 CC_OK, CC_EINVAL, CC_ENOMEM, CC_ECAPACITY, CC_ETIMEOUT, CC_ECUDA, CC_ENOTFOUND, CC_EKEYWIDTH = \
     0, -1, -2, -3, -4, -5, -6, -7
+CC_EBUSY = -8
 
 EXPORTS = [
     "cc_strerror", "cc_create", "cc_destroy", "cc_load_graph", "cc_load_pattern",
