@@ -1,13 +1,21 @@
 """Benchmark of the colour-coding dynamic programme (arXiv 1908.11248) on one GB300.
 
-Workload (default): Barabasi-Albert host graph n=20000, m=4 (seed 1, ~80k edges, int32 CSR);
-pattern the 2x4 grid (8 vertices, treewidth 2, column-sweep decomposition); k=8 colours from
-Philox4x32-10 seed 7; 64 colouring trials in one batched run.  One step = colour all trials,
-run every node of the nice decomposition for all trials at once, test the root and read the
-per-trial uint64 counts back.
+Default workload (the largest single-GPU configuration): Erdos-Renyi host graph n=100000,
+average degree 10 (seed 1, int32 CSR); pattern the 3x3 grid (9 vertices, treewidth 3); k=9
+colours from Philox4x32-10 seed 7; 32 colouring trials in one batched run with options picked by
+the library's autotuner; enumeration of the first 10^5 embeddings.  One step = colour all trials,
+run every node of the nice decomposition for all trials at once (tables kept for the
+reconstruction), test the root, read the per-trial uint64 counts back and enumerate.
 
 Metric: DP entries/s, entries = sum over nodes and trials of |D_x| (distinct table entries; the
 same number on the CPU oracle for the same decomposition and flags).
+
+Extra keys of the same JSON line: the Barabasi-Albert n=20000, 2x4 grid, 64-trial workload; the
+latency (p50/p99) of one query on Erdos-Renyi n=200 with the 5-cycle; the same 64 trials run
+plain (one trial per call), batched (all trials in one call) and as a batch of single-trial
+requests replayed from a captured CUDA graph; the serving workload (2000 Poisson queries on a
+resident Barabasi-Albert n=200000 graph) against the plain per-query path under the same
+arrivals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -18,6 +26,8 @@ replica with its own colouring seed; rank 0 prints the aggregate.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -33,14 +43,10 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-WORKLOAD = "ba20k_grid2x4"
 METRIC = "DP entries/s"
 UNIT = "entries/s"
-# DRAM bytes (read + write) per launch of each node rule's kernels, from one ncu capture of this
-# workload at full size (profiles/launches_ba20k_grid2x4.md): the timed step's sort passes,
-# digit counts, reduce-by-key and hash forgets moved 116.21 GB over the forget group's 14
-# launches.  A group missing here (or captured before a kernel change) reports null.
-TRAFFIC = {"forget": 116.211e9 / 14}
+MAIN = "er100k_grid3x3"
+ENUM_LIMIT = 100000
 
 
 def peaks():
@@ -50,6 +56,36 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def source_hash():
+    """Hash of the library's sources: a DRAM-traffic ratio measured on one build is reported only
+    while the sources are unchanged."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1908_11248_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratios(workload):
+    """Measured DRAM bytes per algorithmic byte of each node rule's kernels for `workload`, from
+    the committed capture summary of this build (profiles/dram_<workload>.txt: lines
+    `ratio <group> <dram bytes> <algorithmic bytes>` and `sources <hash>`); {} if there is none
+    or the sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"dram_{workload}.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return {}
+    src, out = None, {}
+    for ln in lines:
+        f = ln.split()
+        if len(f) == 2 and f[0] == "sources":
+            src = f[1]
+        if len(f) == 4 and f[0] == "ratio":
+            out[f[1]] = float(f[2]) / float(f[3])
+    return out if src == source_hash() else {}
 
 
 class ClockSampler:
@@ -156,78 +192,138 @@ GROUPS = {"color": "colour", "leaf": "leaf", "intro_count": "introduce",
           "join_write": "join", "root": "root"}
 
 
-def run_reference(args, rank):
-    """The CPU oracle, as it stands, on a bounded sample of the workload: each step runs as many
-    of the 64 trials as there are host cores (up to 16), one spawned process per trial."""
-    import multiprocessing as mp
+def describe(name):
+    w = synth.WORKLOADS[name]
+    g = w["graph"]
+    gd = {"er": lambda s: f"ER n={s[1]} p={s[2]:.6g} seed {s[3]}",
+          "ba": lambda s: f"BA n={s[1]} m={s[2]} seed {s[3]}",
+          "pl": lambda s: f"power-law n={s[1]} mean degree {s[2]} exponent {s[3]} seed {s[4]}"}
+    return {"workload": name, "graph": gd[g[0]](g), "pattern": " ".join(map(str, w["pattern"])),
+            "k": w["k"], "trials": w["trials"]}
 
-    import oracle
 
-    if rank != 0:
-        return
-    w = synth.WORKLOADS[WORKLOAD]
-    g = synth.make_graph(w["graph"])
-    pat = synth.make_pattern(w["pattern"])
-    n, k = len(g[0]) - 1, w["k"]
-    cores = max(1, min(os.cpu_count() or 1, 16))
-    z = oracle.colors(n, w["trials"], k, w["seed"])
-    oracle.build()
-    times, entries = [], 0
-    with mp.get_context("spawn").Pool(cores) as pool:  # leaving it terminates the workers
-        pool.map_async(_noop, range(cores)).get(timeout=120)
-        for s in range(args.warmup + args.steps):
-            rows = [(s * cores + i) % w["trials"] for i in range(cores)]
-            t0 = time.perf_counter()
-            res = pool.map_async(_oracle_one, [(g, pat, z[t], k) for t in rows]).get(timeout=600)
-            dt = time.perf_counter() - t0
-            if s >= args.warmup:
-                times.append(dt)
-                entries += sum(e for e, _ in res)
-    tot = sum(times)
-    value = entries / tot
-    sample = (f"{cores} of the 64 trials per step, one per process on {cores} host cores, "
-              "std::map oracle")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": "BA n=20000 m=4 seed 1",
-                   "pattern": "grid 2x4", "k": 8, "trials_per_step": cores,
-                   "l2": "n/a (host)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (test infrastructure): bounded samples timed on the host cores
+# ------------------------------------------------------------------------------------------------
 
 def _noop(x):
     return x
 
 
-def _oracle_one(job):
+_JOB = {}
+
+
+def _init_worker(g, pat, k, allow):
+    _JOB.update(g=g, pat=pat, k=k, allow=allow)
+
+
+def _oracle_one(row):
     """One oracle trial in a spawned worker: (table entries, count) of that colouring."""
-    g, pat, row, k = job
     import oracle
 
-    r = oracle.run_dp(g, pat, row[None, :], k)
+    r = oracle.run_dp(_JOB["g"], _JOB["pat"], row[None, :], _JOB["k"], allow=_JOB["allow"])
     return int(r.node_sizes.sum()), int(r.count[0])
 
 
-def oracle_all_cores(g, pat, z, k, cores):
-    """The oracle, as it stands, on trials 0..cores-1 at once, one process per host core
-    (spawned: the parent has touched the GPU).  Returns the per-trial results and the wall time
-    of the parallel run (workers started and warmed first)."""
+def host_cores(mem_per_trial_gb):
+    """Worker processes for the oracle: every host core, capped so that the workers' tables fit
+    the host memory available now; (workers, cores, cap reason or None)."""
+    cores = os.cpu_count() or 1
+    avail = None
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                avail = int(ln.split()[1]) * 1024 / 1e9
+    except OSError:
+        pass
+    workers, why = cores, None
+    if avail is not None and mem_per_trial_gb > 0:
+        fit = max(1, int(0.7 * avail / mem_per_trial_gb))
+        if fit < workers:
+            workers, why = fit, (f"capped at {fit} workers: {avail:.0f} GB host memory available, "
+                                 f"~{mem_per_trial_gb:g} GB per trial")
+    return workers, cores, why
+
+
+def oracle_trials(g, pat, k, rows, allow, workers):
+    """The oracle, as it stands, on the colourings `rows` (one trial per task), on `workers`
+    spawned processes (spawned: the parent has touched the GPU), the graph and pattern sent once
+    per worker.  Returns the per-trial (entries, count) and the wall time of the parallel run
+    (workers started and warmed first)."""
     import multiprocessing as mp
 
-    with mp.get_context("spawn").Pool(cores) as pool:  # leaving it terminates the workers
-        pool.map_async(_noop, range(cores)).get(timeout=120)
+    with mp.get_context("spawn").Pool(workers, initializer=_init_worker,
+                                      initargs=(g, pat, k, allow)) as pool:
+        pool.map_async(_noop, range(workers)).get(timeout=300)
         t0 = time.perf_counter()
-        res = pool.map_async(_oracle_one, [(g, pat, z[t], k) for t in range(cores)]).get(
-            timeout=300)
+        res = pool.map_async(_oracle_one, list(rows), chunksize=1).get(timeout=1800)
         return res, time.perf_counter() - t0
 
+
+def slice_allow(n, u, modulus, residue=0):
+    """Allowed-mapping masks (Section 3.2, masking unprofitable mappings) that restrict pattern
+    vertex u to the host vertices v = residue (mod modulus) and leave every other pattern vertex
+    free: the embeddings split by the image of u, so a slice's tables and counts are a bounded
+    part of the whole run's."""
+    allow = np.full(n, 0xFFFFFFFF, np.uint32)
+    off = np.arange(n) % modulus != residue
+    allow[off] &= np.uint32(~np.uint32(1 << u) & 0xFFFFFFFF)
+    return allow
+
+
+# sample of each workload the oracle is timed on: (colourings, pattern vertex sliced, modulus,
+# GB of host memory per trial)
+ORACLE_SAMPLE = {"er100k_grid3x3": (16, 0, 16, 6.0), "ba20k_grid2x4": (16, 0, 1, 2.0),
+                 "er200_c5": (1, 0, 1, 0.1)}
+
+
+def run_reference(args, rank):
+    """--impl reference: the CPU oracle, as it stands, on a bounded sample of the workload each
+    step (the same colourings and slice as the GPU leg's cpu_baseline), on the host cores."""
+    import oracle
+
+    if rank != 0:
+        return
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    n, k = len(g[0]) - 1, w["k"]
+    ntr, u, mod, gb = ORACLE_SAMPLE[name]
+    workers, cores, why = host_cores(gb)
+    workers = min(workers, ntr)
+    allow = slice_allow(n, u, mod) if mod > 1 else None
+    z = oracle.colors(n, w["trials"], k, w["seed"])
+    oracle.build()
+    times, entries = [], 0
+    for s in range(args.warmup + args.steps):
+        rows = [z[(s * workers + i) % w["trials"]] for i in range(workers)]
+        res, dt = oracle_trials(g, pat, k, rows, allow, workers)
+        if s >= args.warmup:
+            times.append(dt)
+            entries += sum(e for e, _ in res)
+    tot = sum(times)
+    value = entries / tot
+    sample = (f"{workers} of the {w['trials']} trials per step, one per process on {workers} of "
+              f"{cores} host cores" + (f", pattern vertex {u} sliced to 1/{mod} of the host "
+                                       "vertices" if mod > 1 else "") + ", std::map oracle"
+              + (f"; {why}" if why else ""))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": dict(describe(name), trials_per_step=workers, l2="n/a (host)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": sample, "host_cores": cores},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU legs
+# ------------------------------------------------------------------------------------------------
 
 def rank_seed(seed, rank):
     """Colouring seed of a replica: every rank colours its own independent trials."""
@@ -252,11 +348,308 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, max(0, int(np.ceil(q / 100.0 * len(xs))) - 1))]
 
 
+def roofline(kern, steps, workload):
+    """Roofline of the dominant node rule (largest share of device time): its algorithmic bytes
+    over its event-timed duration against the measured HBM copy bandwidth; traffic = the
+    measured DRAM-bytes ratio of that group (committed capture of this build) times its
+    algorithmic bytes per launch, or null."""
+    grp = {}
+    for kn, v in kern.items():
+        g2 = grp.setdefault(GROUPS.get(kn, kn), {"launches": 0, "ms": 0.0, "bytes": 0})
+        for f in ("launches", "ms", "bytes"):
+            g2[f] += v[f]
+    dom = max(grp, key=lambda x: grp[x]["ms"])
+    d = grp[dom]
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    peak, peak_kind = peaks()
+    ratios = traffic_ratios(workload)
+    total_kms = sum(x["ms"] for x in kern.values())
+    bpl = d["bytes"] / d["launches"]
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ratios[dom] * bpl if dom in ratios else None,
+            "bytes_per_launch": bpl, "ms_per_launch": d["ms"] / d["launches"],
+            "groups": {g: {"ms_per_step": v["ms"] / steps, "share": v["ms"] / total_kms,
+                           "launches_per_step": v["launches"] / steps,
+                           "gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None,
+                           "frac": (v["bytes"] / (v["ms"] / 1000.0) / 1e9 / peak
+                                    if v["ms"] else None),
+                           "traffic_per_launch": (ratios[g] * v["bytes"] / v["launches"]
+                                                  if g in ratios else None)}
+                       for g, v in sorted(grp.items(), key=lambda x: -x[1]["ms"])},
+            "kernels": {kn: {"launches": v["launches"] // steps, "ms_per_step": v["ms"] / steps,
+                             "share": v["ms"] / total_kms}
+                        for kn, v in sorted(kern.items(), key=lambda x: -x[1]["ms"])}}
+
+
+def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=None):
+    """The DP of workload `name` on one context: (optionally) autotune, W untimed warm-up steps,
+    K timed steps (colour, DP with profiled launches, counts back, enumerate), then the same
+    steps end to end through the C ABI with the graph copied from pinned host memory."""
+    w = synth.WORKLOADS[name]
+    g = synth.make_graph(w["graph"])
+    nF, edges, td = synth.make_pattern(w["pattern"])
+    n = len(g[0]) - 1
+    T, k = (args.trials or w["trials"]) if name == args.workload else w["trials"], w["k"]
+    seed = rank_seed(w["seed"], rank)
+    ctx = cc.Context(arena_bytes=args.arena_gb << 30, device=torch.cuda.current_device())
+    h = ctx.h
+    cc.cc_load_graph(h, *g)
+    pid = cc.cc_load_pattern(h, nF, edges, td)
+    out = {"config": describe(name)}
+    out["config"]["trials"] = T
+    tuned = cc.cc_default_opts()
+    if tune:
+        cid = cc.cc_color(h, seed, T, k)
+        t0 = time.perf_counter()
+        tuned, pid, best_ms, tried = cc.cc_autotune(h, pid, cid, None, 6, 2)
+        out["autotune"] = {"configs_tried": tried, "best_ms": best_ms,
+                           "seconds": time.perf_counter() - t0}
+        cc.cc_release_colors(h, cid)
+    out["config"]["opts"] = {f: getattr(tuned, f) for f, _ in tuned._fields_}
+    nodes = cc.cc_pattern_nodes(h, pid, nF)
+    opts = cc.cc_run_opts.from_buffer_copy(tuned)
+    opts.profile = 1
+    opts.retain = 1 if enum_limit else 0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(o):
+        cid = cc.cc_color(h, seed, T, k)
+        run = cc.cc_run_dp(h, pid, cid, o)
+        counts = cc.cc_count(h, run, T)
+        rows = cc.cc_enumerate(h, run, enum_limit, nF)[0] if enum_limit else None
+        return cid, run, counts, rows
+
+    for _ in range(args.warmup):
+        cid, run, counts, rows = step(opts)
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    if sampler:
+        sampler.start()
+    launches0 = cc.cc_context_stats(h)[0]
+    step_ms, entries, kern, modes = [], 0, {}, set()
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (256 MB > 129 MB L2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cid, run, counts, rows = step(opts)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sizes, total = cc.cc_table_stats(h, run, len(nodes))
+        entries += total
+        modes.add(cc.cc_run_mode(h, run))
+        node, kind, ms, cand = cc.cc_run_timings(h, run)
+        for i in range(len(node)):
+            kn = cc.KERNEL_KINDS[int(kind[i])]
+            d = kern.setdefault(kn, {"launches": 0, "ms": 0.0, "bytes": 0})
+            d["launches"] += 1
+            d["ms"] += float(ms[i])
+            d["bytes"] += algorithmic_bytes(kn, int(node[i]), nodes, sizes, cand[i], n, T, k)
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    torch.cuda.synchronize()
+    launches = cc.cc_context_stats(h)[0] - launches0
+    clocks = sampler.stop() if sampler else None
+    total_ms, entries_all = over_ranks(dist, torch, sum(step_ms), entries, "cuda")
+    out.update({
+        "value": entries_all / (total_ms / 1000.0), "ms_per_step": total_ms / args.steps,
+        "entries_per_step": int(entries / args.steps), "gpu_launches": launches,
+        "run_modes": sorted(modes), "roofline": roofline(kern, args.steps, name),
+        "counts": [int(c) for c in counts], "clocks": clocks,
+        "max_table_entries": int(max(sizes)),
+    })
+    if enum_limit:
+        out["enumerated_rows"] = int(len(rows))
+
+    # end to end through the C ABI: graph from pinned host memory, counts (and rows) back
+    if rank == 0:
+        rp_h = torch.from_numpy(np.asarray(g[0], np.int32)).pin_memory().numpy()
+        col_h = torch.from_numpy(np.asarray(g[1], np.int32)).pin_memory().numpy()
+        e_opts = cc.cc_run_opts.from_buffer_copy(tuned)
+        e_opts.retain = 1 if enum_limit else 0
+        e2e_t, e2e_ent, d2h = [], 0, 0
+        for _ in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cc.cc_load_graph(h, rp_h, col_h)
+            cid, run, c2, rows2 = step(e_opts)
+            e2e_t.append(time.perf_counter() - t0)
+            assert np.array_equal(c2, counts), "end-to-end counts differ from the timed steps"
+            d2h = T * 8 + (int(rows2.nbytes) if rows2 is not None else 0)
+            e2e_ent += cc.cc_table_stats(h, run, len(nodes))[1]
+            cc.cc_release(h, run)
+            cc.cc_release_colors(h, cid)
+        out["e2e"] = {"value": e2e_ent / sum(e2e_t), "unit": UNIT,
+                      "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes),
+                      "d2h_bytes_per_step": int(d2h)}
+    out["_ctx"] = (ctx, pid, tuned, g, (nF, edges, td), seed, T, k)
+    return out
+
+
+def cpu_baseline(cc, name, leg, gpu_counts):
+    """The oracle, as it stands, on a bounded sample of the workload: trials 0..C-1 (C = the
+    host-core count, capped by host memory), one per spawned process, and trial 0 alone on one
+    core; for config-3-sized graphs one pattern vertex is restricted to a slice of the host
+    vertices (allowed-mapping masks), and the GPU runs the same sliced pattern so that every
+    sampled count is checked against it."""
+    import oracle
+
+    ctx, pid, tuned, g, pat, seed, T, k = leg["_ctx"]
+    h = ctx.h
+    n = len(g[0]) - 1
+    ntr, u, mod, gb = ORACLE_SAMPLE[name]
+    workers, cores, why = host_cores(gb)
+    workers = min(workers, ntr, T)
+    allow = slice_allow(n, u, mod) if mod > 1 else None
+    if allow is not None:  # the GPU's counts for the same sliced pattern
+        spid = cc.cc_load_pattern_masked(h, pat[0], pat[1], pat[2], allow)
+        cid = cc.cc_color(h, seed, T, k)
+        run = cc.cc_run_dp(h, spid, cid, cc.cc_default_opts())
+        want = cc.cc_count(h, run, T)
+        cc.cc_release(h, run)
+        cc.cc_release_colors(h, cid)
+    else:
+        want = gpu_counts
+    z = oracle.colors(n, workers, k, seed)
+    oracle.build()
+    t0 = time.perf_counter()
+    ref = oracle.run_dp(g, pat, z[:1], k, allow=allow)
+    dt = time.perf_counter() - t0
+    assert int(ref.count[0]) == int(want[0]), "oracle and GPU disagree on trial 0"
+    slice_txt = (f", pattern vertex {u} sliced to the host vertices = 0 mod {mod}"
+                 if mod > 1 else "")
+    single = {"value": float(ref.node_sizes.sum()) / dt, "unit": UNIT, "cores": 1,
+              "kind": "oracle",
+              "sample": f"trial 0 of the {T}{slice_txt}, single-threaded std::map oracle, "
+                        f"{dt:.1f} s"}
+    if workers < 2:
+        return dict(single, host_cores=cores)
+    res, wall = oracle_trials(g, pat, k, [z[t] for t in range(workers)], allow, workers)
+    assert all(int(c) == int(want[t]) for t, (_, c) in enumerate(res)), "oracle and GPU disagree"
+    return {"value": sum(e for e, _ in res) / wall, "unit": UNIT, "cores": workers,
+            "kind": "oracle", "host_cores": cores,
+            "sample": f"trials 0..{workers - 1} of the {T}{slice_txt}, one per process on "
+                      f"{workers} of {cores} host cores, std::map oracle, {wall:.1f} s"
+                      + (f"; {why}" if why else ""),
+            "counts_checked": workers, "single_core": single}
+
+
+def latency_leg(cc, torch, reps=50):
+    """One query of the 1-trial workload (Erdos-Renyi n=200, 5-cycle, k=5): colour, DP with its
+    tables kept, counts back and every embedding reconstructed, sorted and copied back; p50/p99
+    of the host wall time over `reps` queries after a planning run."""
+    w = synth.WORKLOADS["er200_c5"]
+    g = synth.make_graph(w["graph"])
+    nF, edges, td = synth.make_pattern(w["pattern"])
+    with cc.Context(arena_bytes=1 << 30) as ctx:
+        h = ctx.h
+        cc.cc_load_graph(h, *g)
+        pid = cc.cc_load_pattern(h, nF, edges, td)
+        opts = cc.cc_default_opts(retain=1)
+        lat, rows = [], None
+        for i in range(reps + 3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cid = cc.cc_color(h, w["seed"], 1, w["k"])
+            run = cc.cc_run_dp(h, pid, cid, opts)
+            counts = cc.cc_count(h, run, 1)
+            rows, tot = cc.cc_enumerate(h, run, 1 << 20, nF)
+            dt = (time.perf_counter() - t0) * 1e3
+            cc.cc_release(h, run)
+            cc.cc_release_colors(h, cid)
+            if i >= 3:
+                lat.append(dt)
+    return {"workload": "er200_c5", "query": "colour 1 trial, DP (tables kept), count, "
+            "enumerate all embeddings sorted", "reps": reps, "p50_ms": pct(lat, 50),
+            "p99_ms": pct(lat, 99), "count": int(counts[0]), "rows": int(len(rows))}
+
+
+def batching_leg(cc, torch, name="ba20k_grid2x4"):
+    """The same colourings three ways: plain (one trial per cc_run_dp call, no graph), batched
+    (all trials in the key of one cc_run_dp call, planned launches) and graph-batched (the
+    single-trial requests as parallel branches of one captured CUDA graph, cc_run_batch with
+    use_graph); entries/s of each over the whole set, counts compared bit for bit."""
+    w = synth.WORKLOADS[name]
+    g = synth.make_graph(w["graph"])
+    nF, edges, td = synth.make_pattern(w["pattern"])
+    T, k = w["trials"], w["k"]
+    res = {"workload": name, "trials": T}
+    with cc.Context(arena_bytes=96 << 30) as ctx:
+        h = ctx.h
+        cc.cc_load_graph(h, *g)
+        pid = cc.cc_load_pattern(h, nF, edges, td)
+        N = len(cc.cc_pattern_nodes(h, pid, nF))
+        cid_all = cc.cc_color(h, w["seed"], T, k)
+        z = cc.cc_get_colors(h, cid_all, T, len(g[0]) - 1)
+        singles = [cc.cc_set_colors(h, z[t], k) for t in range(T)]
+        plain_o = cc.cc_default_opts()
+        graph_o = cc.cc_default_opts(use_graph=1)
+
+        def timed(fn, reps=3):
+            fn()  # plans every key (and captures the graph)
+            best = None
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                out = fn()
+                dt = time.perf_counter() - t0
+                if best is None or dt < best[0]:
+                    best = (dt, out)
+            return best
+
+        def plain():
+            c, e = [], 0
+            for cid in singles:
+                r = cc.cc_run_dp(h, pid, cid, plain_o)
+                c.append(int(cc.cc_count(h, r, 1)[0]))
+                e += cc.cc_table_stats(h, r, N)[1]
+                cc.cc_release(h, r)
+            return c, e
+
+        def batched():
+            r = cc.cc_run_dp(h, pid, cid_all, plain_o)
+            c = [int(x) for x in cc.cc_count(h, r, T)]
+            e = cc.cc_table_stats(h, r, N)[1]
+            cc.cc_release(h, r)
+            return c, e
+
+        def graphed():
+            rs = cc.cc_run_batch(h, [pid] * T, singles, graph_o)
+            c, e = [], 0
+            for r in rs:
+                c.append(int(cc.cc_count(h, r, 1)[0]))
+                e += cc.cc_table_stats(h, r, N)[1]
+                mode = cc.cc_run_mode(h, r)
+                cc.cc_release(h, r)
+            return c, e, mode
+
+        for label, fn in (("plain", plain), ("batched", batched), ("graph_batched", graphed)):
+            dt, out = timed(fn)
+            res[label] = {"entries_per_s": out[1] / dt, "seconds": dt, "entries": out[1]}
+            res[label]["_counts"] = out[0]
+            if label == "graph_batched":
+                res[label]["run_mode"] = out[2]
+    ref = res["plain"].pop("_counts")
+    res["identical"] = all(res[x].pop("_counts") == ref for x in ("batched", "graph_batched"))
+    res["note"] = ("entries/s = table entries of all trials / host wall time of the calls (counts "
+                   "and sizes read back); plain: one cc_run_dp per trial; batched: one cc_run_dp "
+                   "over all trials; graph_batched: cc_run_batch of the single-trial requests "
+                   "replayed from a captured CUDA graph; best of 3 after a planning pass")
+    return res
+
+
 def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
     """Serving workload: the first `count` queries of the seeded Poisson stream over the resident
-    BA n=200000 m=5 graph, submitted at their arrival times to the library's server, then the
-    queries it completed run again one by one through the plain calls (cc_color, cc_run_dp,
-    cc_count) with the results compared bit for bit."""
+    BA n=200000 m=5 graph, submitted at their arrival times to the library's server; then the
+    plain path (cc_color, cc_run_dp, cc_count, one query at a time, no server) under the same
+    arrivals: each query starts at its arrival or when the previous one ended, whichever is
+    later; results compared bit for bit."""
     w = synth.WORKLOADS["serve_ba200k"]
     g = synth.make_graph(w["graph"])
     stream = synth.serve_stream(w, count)
@@ -306,28 +699,28 @@ def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
     failed = len(stream) - len(ok) - refused
     lat_ms = [res[i][2] / 1e6 for i in ok]
     makespan = max(stream[i]["t"] + res[i][2] / 1e9 for i in range(len(stream)))
-    # plain path: the completed queries one after the other, no batching
-    plain_ms, same = [], True
+    # plain path under the same arrivals, measured: query i starts at max(arrival, previous end)
+    plain_lat, plain_ms, same = [], [], True
+    t0 = time.perf_counter()
     for i in ok:
         q = stream[i]
-        torch.cuda.synchronize()
+        dt = t0 + q["t"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
         t1 = time.perf_counter()
         cid = cc.cc_color(h, q["seed"], q["trials"], q["k"])
         run = cc.cc_run_dp(h, pids[q["pattern"]], cid, cc.cc_default_opts())
         counts = cc.cc_count(h, run, q["trials"])
-        plain_ms.append((time.perf_counter() - t1) * 1e3)
+        t2 = time.perf_counter()
+        plain_ms.append((t2 - t1) * 1e3)
+        plain_lat.append((t2 - (t0 + q["t"])) * 1e3)
         same = same and bool(np.array_equal(counts, res[i][1]))
         cc.cc_release(h, run)
         cc.cc_release_colors(h, cid)
+    plain_span = time.perf_counter() - t0
     ctx.close()
     del ctx
     torch.cuda.empty_cache()
-    # the plain path under the same arrivals: one query at a time, first come first served
-    free_at, plain_lat = 0.0, []
-    for i, ms in zip(ok, plain_ms):
-        start = max(stream[i]["t"], free_at)
-        free_at = start + ms / 1e3
-        plain_lat.append((free_at - stream[i]["t"]) * 1e3)
     return {
         "workload": "serve_ba200k", "graph": "BA n=200000 m=5 seed 1",
         "queries": len(stream), "offered_rate_qps": w["rate"],
@@ -335,15 +728,14 @@ def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
         "completed": len(ok), "refused_enomem": refused, "failed": failed,
         "served": {"qps": len(ok) / makespan, "p50_ms": pct(lat_ms, 50),
                    "p99_ms": pct(lat_ms, 99), "makespan_s": makespan},
-        "plain": {"qps": len(ok) / free_at, "p50_ms": pct(plain_lat, 50),
+        "plain": {"qps": len(ok) / plain_span, "p50_ms": pct(plain_lat, 50),
                   "p99_ms": pct(plain_lat, 99), "service_p50_ms": pct(plain_ms, 50),
-                  "service_p99_ms": pct(plain_ms, 99), "makespan_s": free_at},
+                  "service_p99_ms": pct(plain_ms, 99), "makespan_s": plain_span},
         "identical": same, "server": stats,
         "note": "one untimed query per (pattern, trials, k) first plans every key; latency runs "
-                "from arrival to completion and includes queueing (the offered rate is above "
-                "either path's capacity); plain = the completed queries run one at a time in "
-                "arrival order through cc_color, cc_run_dp and cc_count, its latency that of "
-                "first-come-first-served service at the measured per-query times",
+                "from arrival to completion and includes queueing; plain = the same queries "
+                "submitted at the same arrival times to the plain calls (cc_color, cc_run_dp, "
+                "cc_count) one at a time, measured",
     }
 
 
@@ -353,15 +745,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=MAIN, choices=sorted(ORACLE_SAMPLE),
+                    help="workload of the bench line")
+    ap.add_argument("--legs", default="ba20k,latency,batching,serve",
+                    help="extra keys to measure (comma list of ba20k, latency, batching, serve; "
+                         "'none' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default options instead of autotuning")
     ap.add_argument("--trials", type=int, default=0,
-                    help="colouring trials per step (default: the workload's 64); smaller values "
+                    help="colouring trials per step (default: the workload's); smaller values "
                          "only for small profiling captures")
-    ap.add_argument("--arena-gb", type=int, default=96,
+    ap.add_argument("--arena-gb", type=int, default=200,
                     help="device arena of the DP context (small values for profiling captures)")
-    ap.add_argument("--serve-queries", type=int, default=300,
-                    help="queries of the serving stream to run (0: skip the serving leg; the "
-                         "full stream has 2000)")
+    ap.add_argument("--serve-queries", type=int, default=2000,
+                    help="queries of the serving stream to run (the full stream has 2000)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -383,162 +780,53 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-
-    w = synth.WORKLOADS[WORKLOAD]
-    g = synth.make_graph(w["graph"])
-    nF, edges, td = synth.make_pattern(w["pattern"])
-    n = len(g[0]) - 1
-    T, k = args.trials or w["trials"], w["k"]
-    seed = rank_seed(w["seed"], rank)
-    ctx = cc.Context(arena_bytes=args.arena_gb << 30, device=local)
-    h = ctx.h
-    cc.cc_load_graph(h, *g)
-    pid = cc.cc_load_pattern(h, nF, edges, td)
-    nodes = cc.cc_pattern_nodes(h, pid, nF)
-    opts = cc.cc_default_opts(profile=1)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def step():
-        cid = cc.cc_color(h, seed, T, k)
-        run = cc.cc_run_dp(h, pid, cid, opts)
-        counts = cc.cc_count(h, run, T)
-        return cid, run, counts
-
-    for _ in range(args.warmup):
-        cid, run, counts = step()
-        cc.cc_release(h, run)
-        cc.cc_release_colors(h, cid)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-
+    legs = set() if args.legs == "none" else set(args.legs.split(","))
+    enum_limit = ENUM_LIMIT if args.workload == MAIN else 0
     sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
-    launches0 = cc.cc_context_stats(h)[0]
-    step_ms, entries, kern = [], 0, {}
-    sizes = None
-    for s in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (256 MB > 129 MB L2)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        cid, run, counts = step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        sizes, total = cc.cc_table_stats(h, run, len(nodes))
-        entries += total
-        node, kind, ms, cand = cc.cc_run_timings(h, run)
-        for i in range(len(node)):
-            kn = cc.KERNEL_KINDS[int(kind[i])]
-            d = kern.setdefault(kn, {"launches": 0, "ms": 0.0, "bytes": 0})
-            d["launches"] += 1
-            d["ms"] += float(ms[i])
-            d["bytes"] += algorithmic_bytes(kn, int(node[i]), nodes, sizes, cand[i], n, T, k)
-        cc.cc_release(h, run)
-        cc.cc_release_colors(h, cid)
-    torch.cuda.synchronize()
-    launches = cc.cc_context_stats(h)[0] - launches0
-    clocks = sampler.stop()
-    total_ms, entries_all = over_ranks(dist, torch, sum(step_ms), entries, "cuda")
-    value = entries_all / (total_ms / 1000.0)
-
-    # roofline of the dominant node rule (largest share of device time); sort passes and
-    # reduce-by-key are the forget's merge, so they carry the forget's algorithmic bytes
-    grp = {}
-    for kn, v in kern.items():
-        g2 = grp.setdefault(GROUPS.get(kn, kn), {"launches": 0, "ms": 0.0, "bytes": 0})
-        for f in ("launches", "ms", "bytes"):
-            g2[f] += v[f]
-    dom = max(grp, key=lambda x: grp[x]["ms"])
-    d = grp[dom]
-    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
-    peak, peak_kind = peaks()
-    total_kms = sum(x["ms"] for x in kern.values())
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get(dom),
-            "bytes_per_launch": d["bytes"] / d["launches"],
-            "ms_per_launch": d["ms"] / d["launches"],
-            "groups": {g: {"ms_per_step": v["ms"] / args.steps, "share": v["ms"] / total_kms,
-                           "gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None}
-                       for g, v in sorted(grp.items(), key=lambda x: -x[1]["ms"])},
-            "kernels": {kn: {"launches": v["launches"] // args.steps,
-                             "ms_per_step": v["ms"] / args.steps,
-                             "share": v["ms"] / total_kms}
-                        for kn, v in sorted(kern.items(), key=lambda x: -x[1]["ms"])}}
-
-    # end to end through the C ABI: graph from pinned host memory, counts back to the host
-    e2e = None
-    if rank == 0:
-        rp_h = torch.from_numpy(np.asarray(g[0], np.int32)).pin_memory().numpy()
-        col_h = torch.from_numpy(np.asarray(g[1], np.int32)).pin_memory().numpy()
-        e2e_t, e2e_ent = [], 0
-        for s in range(max(2, args.steps)):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            cc.cc_load_graph(h, rp_h, col_h)
-            cid = cc.cc_color(h, seed, T, k)
-            run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts())
-            counts = cc.cc_count(h, run, T)
-            e2e_t.append(time.perf_counter() - t0)
-            e2e_ent += cc.cc_table_stats(h, run, len(nodes))[1]
-            cc.cc_release(h, run)
-            cc.cc_release_colors(h, cid)
-        e2e = {"value": e2e_ent / sum(e2e_t), "unit": UNIT,
-               "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes),
-               "d2h_bytes_per_step": int(T * 8)}
-
+    main_leg = dp_leg(cc, torch, args.workload, args, rank, dist, tune=not args.no_tune,
+                      enum_limit=enum_limit, sampler=sampler)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        z = oracle.colors(n, 1, k, seed)
-        t0 = time.perf_counter()
-        ref = oracle.run_dp(g, (nF, edges, td), z, k)
-        dt = time.perf_counter() - t0
-        single = {"value": float(ref.node_sizes.sum()) / dt, "unit": UNIT, "cores": 1,
-                  "kind": "oracle",
-                  "sample": "trial 0 of the 64 (one colouring), single-threaded std::map oracle, "
-                            f"{dt:.1f} s"}
-        # the sampled trial's count must agree with the GPU's
-        assert int(ref.count[0]) == int(counts[0]), "oracle and GPU disagree on trial 0"
-        cpu = dict(single)
-        cores = max(1, min(os.cpu_count() or 1, 16, T))
-        if cores > 1:  # the same oracle on independent trials, one per host core
-            try:
-                zc = oracle.colors(n, cores, k, seed)
-                res, wall = oracle_all_cores(g, (nF, edges, td), zc, k, cores)
-                assert all(int(c) == int(counts[t]) for t, (_, c) in enumerate(res)), \
-                    "oracle and GPU disagree"
-                cpu = {"value": sum(e for e, _ in res) / wall, "unit": UNIT, "cores": cores,
-                       "kind": "oracle",
-                       "sample": f"trials 0..{cores - 1} of the 64, one per process on {cores} "
-                                 f"host cores, std::map oracle, {wall:.1f} s",
-                       "single_core": single}
-            except AssertionError:
-                raise
-            except Exception as ex:  # keep the single-core figure if processes are unavailable
-                cpu["multi_core_error"] = str(ex)[:200]
-
+        cpu = cpu_baseline(cc, args.workload, main_leg, main_leg["counts"])
+    main_leg.pop("_ctx")[0].close()
+    torch.cuda.empty_cache()
+    line = None
     if rank == 0:
+        cfg = dict(main_leg["config"], entries_per_step=main_leg["entries_per_step"],
+                   parallelism=f"replicas x{world}",
+                   l2="flushed between timed steps (256 MB write); tables exceed L2")
+        if enum_limit:
+            cfg["enumerate_limit"] = enum_limit
+            cfg["enumerated_rows"] = main_leg["enumerated_rows"]
+        cfg["max_table_entries"] = main_leg["max_table_entries"]
+        cfg["run_modes"] = main_leg["run_modes"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": "BA n=20000 m=4 seed 1",
-                       "pattern": "grid 2x4 (column-sweep decomposition)", "k": k,
-                       "trials": T, "entries_per_step": int(entries / args.steps),
-                       "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks,
+            "metric": METRIC, "value": main_leg["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_leg["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": cfg, "roofline": main_leg["roofline"],
+            "cpu_baseline": cpu, "e2e": main_leg.get("e2e"),
+            "gpu_launches": main_leg["gpu_launches"], "clocks": main_leg["clocks"],
+            "autotune": main_leg.get("autotune"),
         }
-    ctx.close()
-    if rank == 0:
-        if args.serve_queries > 0 and world == 1:
+    if rank == 0 and world == 1:
+        if "ba20k" in legs and args.workload != "ba20k_grid2x4":
+            a2 = argparse.Namespace(**vars(args))
+            a2.arena_gb = min(args.arena_gb, 96)
+            leg = dp_leg(cc, torch, "ba20k_grid2x4", a2, rank, None, tune=False,
+                         sampler=ClockSampler(torch.cuda.current_device()))
+            leg.pop("_ctx")[0].close()
+            leg.pop("counts")
+            torch.cuda.empty_cache()
+            line["ba20k_grid2x4"] = leg
+        if "latency" in legs:
+            line["er200_c5_latency"] = latency_leg(cc, torch)
+        if "batching" in legs:
+            line["batched_vs_plain"] = batching_leg(cc, torch)
+            torch.cuda.empty_cache()
+        if "serve" in legs and args.serve_queries > 0:
             line["serving"] = serve_leg(cc, torch, args.serve_queries, 200, 160, 8)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

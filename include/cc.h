@@ -321,18 +321,22 @@ int cc_context_stats(cc_ctx *ctx, uint64_t *kernel_launches, uint64_t *arena_use
 /* Size of the fixed device array cc_count_noalloc works in. */
 #define CC_NOALLOC_BYTES (64ull << 20)
 
-/* For callers that cannot allocate device memory: code running while a stream is captured into a
- * CUDA graph (an allocation would break the capture), processes whose device memory belongs to
- * another allocator, and hot paths that must not pay an allocation's implicit synchronisation.
+/* For callers that cannot allocate device memory: processes whose device memory belongs to
+ * another allocator that must not be bypassed (a framework's caching pool, a fixed partition of
+ * the GPU), and code loaded into such processes with no allocator of its own to call.
  * Returns what cc_count and cc_decide return for graph (n, h_row_ptr, h_col), pattern (n_F, m_F,
  * h_edges, td) and cc_color(seed, trials, k) under cc_default_opts, computing everything inside
  * one CC_NOALLOC_BYTES device array that is part of the library image (every GPU that loads the
  * library holds it until exit); the caller passes only host inputs and the host outputs
- * h_counts[trials] and h_exists[trials].  The first call on a device looks up the array's device
- * address, so make it before any stream capture.  Every call shares the array and leaves its
- * contents behind (each call clears what it needs); calls whose work overlaps on one GPU race
- * and must be serialised by the caller.  Errors: CC_ENOMEM when the graph, the colourings or the
- * tables do not fit the array; otherwise those of the calls it stands for. */
+ * h_counts[trials] and h_exists[trials].  The call copies its inputs from (pageable) host memory
+ * on `cuda_stream`, waits for that stream between steps and returns when the results are on the
+ * host.  On a stream that is being captured into a CUDA graph it does nothing and returns
+ * CC_EINVAL.  The first call on a device looks up the array's device address.  Every call
+ * shares the array and leaves its contents behind (each call clears what it needs); calls whose
+ * work overlaps on one GPU race and must be serialised by the caller.  Errors: CC_ENOMEM when
+ * the graph and colourings (4(n+1) + 4*h_row_ptr[n] + n(1 + trials) bytes plus under 1 MiB of
+ * fixed state) or later the tables do not fit the array; CC_EINVAL as above; otherwise those of
+ * the calls it stands for. */
 int cc_count_noalloc(int device, void *cuda_stream, int32_t n, const int32_t *h_row_ptr,
                      const int32_t *h_col, int32_t n_F, int32_t m_F, const int32_t *h_edges,
                      const cc_td *td, uint64_t seed, int32_t trials, int32_t k,

@@ -12,6 +12,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcc.so")
 SOURCES = ["cc_kernels.cu", "cc_sort.cu", "cc_enum.cu", "cc_host.cpp", "cc_serve.cpp",
            "cc_tune.cpp", "cc_solve.cpp", "cc_noalloc.cu"]
+HEADERS = ["cc_internal.h", "cc_device.cuh", "cc_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -27,8 +28,8 @@ def _nvcc():
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     deps = [os.path.join(CSRC, s) for s in SOURCES]
-    deps += [os.path.join(CSRC, "cc_internal.h"), os.path.join(CSRC, "cc_device.cuh"),
-             os.path.join(ROOT, "include", "cc.h")]
+    deps += [os.path.join(CSRC, h) for h in HEADERS]
+    deps.append(os.path.join(ROOT, "include", "cc.h"))
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

@@ -245,6 +245,44 @@ __device__ __forceinline__ void block_exclusive_scan(long long v, long long *s_o
   __syncthreads();
 }
 
+// Exclusive scan of m 64-bit values in[0, m) into out[0, m) (in == out allowed) by ONE block of
+// blockDim.x threads (a multiple of 32, at most 1024): chunks of blockDim.x values, each scanned
+// with warp shuffles and one pass over the warp totals, carry the running sum forward; *total
+// receives the sum of all m values.  Every thread of the block must call it.
+__device__ __forceinline__ void block_scan_array(const u64 *in, u64 *out, u64 m, u64 *total) {
+  __shared__ u64 s_w[32];
+  __shared__ u64 s_carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (u64 base = 0; base < m; base += blockDim.x) {
+    const u64 i = base + threadIdx.x;
+    const u64 v = i < m ? in[i] : 0;
+    u64 x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {  // inclusive scan of the warp totals
+      u64 s = lane < nw ? s_w[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      if (lane < nw) s_w[lane] = s;
+    }
+    __syncthreads();
+    const u64 carry = s_carry;
+    if (i < m) out[i] = carry + (w ? s_w[w - 1] : 0) + x - v;
+    __syncthreads();  // every thread has read s_carry and s_w
+    if (threadIdx.x == 0) s_carry = carry + s_w[nw - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = s_carry;
+}
+
 // exclusive rank of a flag within the block (deterministic order), and the block's count
 template <int BLOCK>
 __device__ __forceinline__ int block_flag_rank(bool f, int *s_wc, int &total) {

@@ -218,16 +218,8 @@ __global__ void block_sums_kernel(const unsigned *v, u64 n, u64 per, u64 *sums) 
   }
 }
 
-__global__ void scan_small_kernel(u64 *v, int m, u64 *total) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    u64 s = 0;
-    for (int i = 0; i < m; ++i) {
-      u64 x = v[i];
-      v[i] = s;
-      s += x;
-    }
-    *total = s;
-  }
+__global__ void __launch_bounds__(1024) scan_small_kernel(u64 *v, int m, u64 *total) {
+  block_scan_array(v, v, (u64)m, total);
 }
 
 // each block scans its range sequentially in chunks of blockDim (one block per range)
@@ -432,7 +424,7 @@ int launch_scan_u32(cudaStream_t s, const DevInfo &d, const unsigned *v, unsigne
   u64 *sums = scratch, *total = scratch + nb;
   if (n == 0) return (int)cudaMemsetAsync(off, 0, sizeof(u64), s);
   block_sums_kernel<<<nb, 256, 0, s>>>(v, n, per, sums);
-  scan_small_kernel<<<1, 32, 0, s>>>(sums, nb, total);
+  scan_small_kernel<<<1, 1024, 0, s>>>(sums, nb, total);
   block_scan_kernel<<<nb, 1024, 0, s>>>(v, n, per, sums, off);
   cudaMemcpyAsync(off + n, total, sizeof(u64), cudaMemcpyDeviceToDevice, s);
   return (int)cudaGetLastError();

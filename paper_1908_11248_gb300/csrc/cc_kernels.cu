@@ -728,16 +728,10 @@ __global__ void wait_probe_kernel(const u64 *flag, unsigned polls, int *err) {
   atomicOr(err, kErrTimeout);
 }
 
-// exclusive scan of the per-block counts (one block); writes bases and the grand total
-__global__ void scan_blocks_kernel(const u64 *cnt, int nblk, u64 *base, u64 *total) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    u64 s = 0;
-    for (int i = 0; i < nblk; ++i) {
-      base[i] = s;
-      s += cnt[i];
-    }
-    *total = s;
-  }
+// exclusive scan of the per-block counts (one block of 1024 threads); bases and the grand total
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(const u64 *cnt, int nblk, u64 *base,
+                                                           u64 *total) {
+  block_scan_array(cnt, base, (u64)nblk, total);
 }
 
 // ---- forget: project out slot q and aggregate into a hash table ---------------------------
@@ -945,7 +939,7 @@ int launch_intro_blk(cudaStream_t s, const DevInfo &d, int kw, int mode, int gro
 #undef CC_INTRO
   if (r) return r;
   if (mode == 0) {
-    scan_blocks_kernel<<<1, 32, 0, s>>>(cnt, grid, base, total);
+    scan_blocks_kernel<<<1, 1024, 0, s>>>(cnt, grid, base, total);
     r = (int)cudaGetLastError();
   }
   return r;

@@ -1,21 +1,24 @@
 // cc_count_noalloc: a colour-coding count that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc (or anything that does): code running while a CUDA stream
-// is being captured into a graph, where an allocation would break the capture; processes whose
-// device memory is owned by another allocator that must not be bypassed; and callers on a hot
-// path that must not pay for an allocation's implicit synchronisation.  For them this entry point
-// runs the whole count (graph upload, colouring, dynamic programme, root test) inside one
-// fixed-size device array that is part of the library image itself, so the only memory it touches
-// is that array and the caller's host buffers.
+// Some callers cannot call cudaMalloc (or anything that does): processes whose device memory is
+// owned by another allocator that must not be bypassed (a framework's caching pool, a fixed
+// partition of the GPU handed to a plug-in), and library code loaded into such processes that
+// has no allocator of its own to ask.  For them this entry point runs the whole count (graph
+// upload, colouring, dynamic programme, root test) inside one fixed-size device array that is
+// part of the library image itself, so the only memory it touches is that array and the
+// caller's host buffers.
+//
+// It copies the host inputs in and the results out, and waits for the caller's stream between
+// steps, so it returns only when its work is done.  Called on a stream that is being captured
+// into a CUDA graph it does nothing and returns CC_EINVAL.
 //
 // The array is a file-scope __device__ variable: every GPU that loads this library holds
 // CC_NOALLOC_BYTES of it until the process exits.  In host code its name is only a stand-in, so
 // its device address is looked up once per device (cudaGetSymbolAddress, with that device
-// current) on the first call made on that device; that first call should therefore come before
-// any stream capture.  All calls on a device share the array and it keeps the previous call's
-// contents; everything the count needs zeroed is cleared by the call itself.  Two calls whose
-// work overlaps on the same GPU (different streams or threads) race on the array and must be
-// serialised by the caller.
+// current) on the first call made on that device.  All calls on a device share the array and it
+// keeps the previous call's contents; everything the count needs zeroed is cleared by the call
+// itself.  Two calls whose work overlaps on the same GPU (different streams or threads) race on
+// the array and must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,10 +42,15 @@ extern "C" int cc_count_noalloc(int device, void *cuda_stream, int32_t n,
   if (device < 0 || device >= kMaxDevices || n < 0 || !h_row_ptr || trials < 1 || !h_counts ||
       !h_exists)
     return CC_EINVAL;
-  // the graph and the colourings alone must leave room in the array
-  const unsigned long long fixed = ((unsigned long long)n + 1 + (unsigned long long)h_row_ptr[n]) *
-                                       sizeof(int32_t) +
-                                   (unsigned long long)trials * (unsigned long long)n * 2 +
+  // a stream being captured must see no copy or wait from this call
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap) != cudaSuccess) return CC_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return CC_EINVAL;
+  // what a context holds before any table: the CSR (int32 row pointers and columns), one degree
+  // byte and one colour byte per vertex and trial, and its small words and scratch (under 1 MiB)
+  const unsigned long long m2 = (unsigned long long)h_row_ptr[n];
+  const unsigned long long fixed = 4ull * ((unsigned long long)n + 1 + m2) +
+                                   (unsigned long long)n * (1ull + (unsigned long long)trials) +
                                    (1ull << 20);
   if (fixed > CC_NOALLOC_BYTES) return CC_ENOMEM;
   int prev = 0;

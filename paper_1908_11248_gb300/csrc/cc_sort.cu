@@ -732,16 +732,10 @@ __global__ void __launch_bounds__(BLOCK) reduce_count_kernel(const void *src, co
   if (threadIdx.x == 0) blk[blockIdx.x] = s;
 }
 
-// exclusive scan of the per-block counts (one thread); bases at blk[G..2G), total at blk[2G]
-__global__ void blk_scan_kernel(u64 *blk, int G) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    u64 s = 0;
-    for (int i = 0; i < G; ++i) {
-      blk[G + i] = s;
-      s += blk[i];
-    }
-    blk[2 * G] = s;
-  }
+// exclusive scan of the per-block counts (one block of 1024 threads); bases at blk[G..2G),
+// total at blk[2G]
+__global__ void __launch_bounds__(1024) blk_scan_kernel(u64 *blk, int G) {
+  block_scan_array(blk, blk + G, (u64)G, blk + 2 * G);
 }
 
 template <typename K, int BLOCK, bool FROM_S>
@@ -924,7 +918,7 @@ int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
   const SortSpec sp = from_s ? *from_s : SortSpec{};
   if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
   else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
-  blk_scan_kernel<<<1, 32, 0, s>>>(blk, G);
+  blk_scan_kernel<<<1, 1024, 0, s>>>(blk, G);
   if (kw == 1) {
     if (from_s)
       reduce_write_kernel<u64, 256, true><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
