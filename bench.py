@@ -644,6 +644,76 @@ def batching_leg(cc, torch, name="ba20k_grid2x4"):
     return res
 
 
+def er_phase_point(cc, h, pat, k, seed, trials):
+    """One point of the Erdos-Renyi study on the loaded target: load the pattern (minimum-width
+    decomposition), colour `trials` times, run the DP over all colourings at once and decide.
+    Returns (status, width, any colourful copy, per-trial counts or None, table entries)."""
+    nF, edges, td = pat
+    pid = cc.cc_load_pattern(h, nF, edges, td)
+    width = cc.cc_pattern_info(h, pid)[1]
+    cid = cc.cc_color(h, seed, trials, k)
+    try:
+        run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts())
+    except cc.CCError as ex:
+        cc.cc_release_colors(h, cid)
+        return ex.code, width, None, None, 0
+    counts = cc.cc_count(h, run, trials)
+    found = bool(cc.cc_decide(h, run, trials).any())
+    N = cc.cc_pattern_info(h, pid)[0]
+    ent = cc.cc_table_stats(h, run, N)[1]
+    cc.cc_release(h, run)
+    cc.cc_release_colors(h, cid)
+    return 0, width, found, counts, ent
+
+
+def er_phase_leg(cc, torch, step=None, arena_gb=32):
+    """The Erdos-Renyi phase-transition study (Section 5.4): for every p, q on the grid of the
+    study, target G(150, p) against pattern G(10, q), ten colourings (iterations) with k = 10;
+    per point the time of the ten iterations, whether a copy was found, the pattern's
+    decomposition width and the status (0, or CC_ENOMEM / CC_EKEYWIDTH where the tables do not
+    fit the arena or the width exceeds what the kernels take: the paper's time-outs)."""
+    spec = dict(synth.ER_PHASE)
+    if step:
+        spec["step"] = step
+    probs = synth.er_phase_probs(spec["step"])
+    P = len(probs)
+    ms = np.zeros((P, P))
+    found = np.zeros((P, P), np.int8)
+    width = np.zeros((P, P), np.int8)
+    status = np.zeros((P, P), np.int8)
+    entries = 0
+    t_all = time.perf_counter()
+    with cc.Context(arena_bytes=arena_gb << 30) as ctx:
+        h = ctx.h
+        for ip in range(P):
+            for iq in range(P):
+                p, q, g, pat, seed = synth.er_phase_instance(ip, iq, spec)
+                if iq == 0:
+                    cc.cc_load_graph(h, *g)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, w, f, _, ent = er_phase_point(cc, h, pat, spec["n_pattern"], seed,
+                                                 spec["iterations"])
+                ms[ip, iq] = (time.perf_counter() - t0) * 1e3
+                status[ip, iq], width[ip, iq], found[ip, iq] = st, w, 1 if f else 0
+                entries += ent
+    ok = status == 0
+    return {
+        "workload": "er_phase", "target": f"G({spec['n_target']}, p)",
+        "pattern": f"G({spec['n_pattern']}, q)", "iterations": spec["iterations"],
+        "probs": probs, "points": P * P, "seconds": time.perf_counter() - t_all,
+        "completed": int(ok.sum()), "enomem": int((status == -2).sum()),
+        "width_limit": int((status == -7).sum()), "found": int(found.sum()),
+        "entries": int(entries),
+        # rows p, columns q
+        "ms": np.round(ms, 2).tolist(), "found_grid": found.tolist(),
+        "status_grid": status.tolist(),
+        "width_vs_q": [float(np.mean(width[:, j])) for j in range(P)],
+        "note": "per point: load the pattern (minimum-width decomposition), colour ten times, one "
+                "DP over the ten colourings, decide; ms = host wall time of those calls",
+    }
+
+
 def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
     """Serving workload: the first `count` queries of the seeded Poisson stream over the resident
     BA n=200000 m=5 graph, submitted at their arrival times to the library's server; then the
@@ -747,9 +817,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=MAIN, choices=sorted(ORACLE_SAMPLE),
                     help="workload of the bench line")
-    ap.add_argument("--legs", default="ba20k,latency,batching,serve",
-                    help="extra keys to measure (comma list of ba20k, latency, batching, serve; "
-                         "'none' for none)")
+    ap.add_argument("--legs", default="ba20k,latency,batching,serve,er_phase",
+                    help="extra keys to measure (comma list of ba20k, latency, batching, serve, "
+                         "er_phase; 'none' for none)")
+    ap.add_argument("--er-phase-step", type=float, default=0.0,
+                    help="grid step of the Erdos-Renyi study (default: the paper's 0.03)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default options instead of autotuning")
     ap.add_argument("--trials", type=int, default=0,
@@ -823,6 +895,9 @@ def main():
             line["er200_c5_latency"] = latency_leg(cc, torch)
         if "batching" in legs:
             line["batched_vs_plain"] = batching_leg(cc, torch)
+            torch.cuda.empty_cache()
+        if "er_phase" in legs:
+            line["er_phase"] = er_phase_leg(cc, torch, args.er_phase_step or None)
             torch.cuda.empty_cache()
         if "serve" in legs and args.serve_queries > 0:
             line["serving"] = serve_leg(cc, torch, args.serve_queries, 200, 160, 8)

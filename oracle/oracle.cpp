@@ -26,10 +26,10 @@
 //     be mapped to it, is an optional mask array (bit y of allow[x]: y may map to x); maps that
 //     break it are not counted anywhere.
 //   * the distance bound of Section 3.2 (mapping expansion) is a switch: an introduced vertex u
-//     with no neighbour in the bag, whose nearest bag vertex w of its F-component is at
-//     F-distance 2, takes only the host vertices within distance 2 of phi(w); farther anchors,
-//     and vertices of another component, take every host vertex.  It never changes the root
-//     result.
+//     with no neighbour in the bag takes only the host vertices within distance d of phi(w),
+//     where w is the bag vertex nearest to u in F (the first in bag order among the nearest) and
+//     d = dist_F(w, u); a vertex with no bag vertex in its F-component takes every host vertex.
+//     It never changes the root result.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -90,6 +90,23 @@ struct Graph {
   bool adjacent(int32_t a, int32_t b) const {  // rows are sorted
     return std::binary_search(col.begin() + row_ptr[a], col.begin() + row_ptr[a + 1], b);
   }
+  // the host vertices within distance r of a (a itself included), increasing: breadth-first
+  // search stopped at depth r
+  std::vector<int32_t> ball(int32_t a, int32_t r) const {
+    std::vector<int32_t> depth(n, -1), q{a};
+    depth[a] = 0;
+    for (size_t h = 0; h < q.size(); ++h) {
+      const int32_t x = q[h];
+      if (depth[x] == r) continue;
+      for (int32_t i = row_ptr[x]; i < row_ptr[x + 1]; ++i)
+        if (depth[col[i]] < 0) {
+          depth[col[i]] = depth[x] + 1;
+          q.push_back(col[i]);
+        }
+    }
+    std::sort(q.begin(), q.end());
+    return q;
+  }
 };
 
 struct Pattern {
@@ -142,12 +159,48 @@ struct NiceTD {
   std::vector<NiceNode> nodes;  // post-order; the root (empty bag) is last
 };
 
-// Introduces the vertices `add` on top of node `top`, one introduce node each.  The paper does
-// not fix their order; we take, each time, the smallest remaining vertex that has an F-neighbour
-// in the current bag, or the smallest remaining vertex if none has, so that an introduce finds
-// its candidates in adjacency lists whenever F allows (Section 3.2, mapping expansion).
-int32_t introduce_all(NiceTD &T, const Pattern &F, int32_t top, std::vector<int32_t> add) {
+int32_t push_forget(NiceTD &T, int32_t top, int32_t u) {
+  NiceNode f;
+  f.type = FORGET;
+  f.child0 = top;
+  f.vertex = u;
+  for (int32_t w : T.nodes[top].bag)
+    if (w != u) f.bag.push_back(w);
+  T.nodes.push_back(f);
+  return (int32_t)T.nodes.size() - 1;
+}
+
+bool in_bag(const NiceTD &T, int32_t node, int32_t u) {
+  const std::vector<int32_t> &b = T.nodes[node].bag;
+  return std::find(b.begin(), b.end(), u) != b.end();
+}
+
+// Introduces the vertices `add` on top of node `top`, one introduce node each, while the
+// decomposition bag `target` is being built.  The paper does not fix their order; we take, each
+// time, the smallest remaining vertex that has an F-neighbour in the current bag, or the
+// smallest remaining vertex if none has, so that an introduce finds its candidates in adjacency
+// lists whenever F allows (Section 3.2, mapping expansion).  Nor does it fix where forgets go:
+// a vertex of `drop` (vertices of `target` absent from the next bag up) is forgotten, in
+// increasing vertex order, as soon as every F-neighbour it has in `target` has been in the bag,
+// except when that would empty the bag before an introduce.
+int32_t introduce_all(NiceTD &T, const Pattern &F, int32_t top, std::vector<int32_t> add,
+                      const std::vector<int32_t> &drop, const std::vector<int32_t> &target) {
   std::sort(add.begin(), add.end());
+  std::vector<char> gone(F.n, 0);
+  auto forget_ripe = [&](int32_t t) {
+    for (int32_t q : drop) {
+      if (!in_bag(T, t, q)) continue;
+      bool waiting = false;  // an F-neighbour of q in the target bag not yet in the bag
+      for (int32_t w : target)
+        if (F.adj[q][w] && !in_bag(T, t, w) && !gone[w]) waiting = true;
+      if (waiting) continue;
+      if (T.nodes[t].bag.size() == 1 && !add.empty()) continue;
+      t = push_forget(T, t, q);
+      gone[q] = 1;
+    }
+    return t;
+  };
+  top = forget_ripe(top);
   while (!add.empty()) {
     size_t pick = 0;
     for (size_t j = 0; j < add.size(); ++j) {
@@ -168,19 +221,34 @@ int32_t introduce_all(NiceTD &T, const Pattern &F, int32_t top, std::vector<int3
     in.bag.push_back(u);
     std::sort(in.bag.begin(), in.bag.end());
     T.nodes.push_back(in);
-    top = (int32_t)T.nodes.size() - 1;
+    top = forget_ripe((int32_t)T.nodes.size() - 1);
   }
   return top;
 }
 
-// Builds the nice decomposition rooted at decomposition node i: its top node has bag B_i.
-// Children of a decomposition node are taken in increasing id; going from a child's bag to
-// B_i first forgets B_c \ B_i in increasing vertex order, then introduces B_i \ B_c (order of
-// introduce_all); several children are combined by left-deep joins.  A leaf bag becomes a
-// size-one leaf node holding its smallest vertex followed by introductions of the rest.
+// Vertices of decomposition bag i that its parent's bag lacks (all of them at the root).
+std::vector<int32_t> leaving_bag(const std::vector<std::vector<int32_t>> &bags,
+                                 const std::vector<int32_t> &parent, int32_t i) {
+  std::vector<int32_t> d;
+  for (int32_t u : bags[i])
+    if (parent[i] < 0 ||
+        std::find(bags[parent[i]].begin(), bags[parent[i]].end(), u) == bags[parent[i]].end())
+      d.push_back(u);
+  return d;
+}
+
+// Builds the nice decomposition rooted at decomposition node i: its top node has bag B_i minus
+// the vertices of B_i that left early (those B_i does not pass to its parent).  Children of a
+// decomposition node are taken in increasing id; going from a child's bag to B_i first forgets
+// what remains of B_c \ B_i in increasing vertex order, then introduces B_i \ B_c (order of
+// introduce_all, with early forgets unless several children must be joined at B_i); several
+// children are combined by left-deep joins.  A leaf bag becomes a size-one leaf node holding its
+// smallest vertex followed by introductions of the rest.
 int32_t nice_build(NiceTD &T, const Pattern &F, const std::vector<std::vector<int32_t>> &bags,
+                   const std::vector<int32_t> &parent,
                    const std::vector<std::vector<int32_t>> &kids, int32_t i) {
   const std::vector<int32_t> &B = bags[i];
+  const std::vector<int32_t> none;
   if (kids[i].empty()) {
     NiceNode leaf;
     leaf.type = LEAF;
@@ -188,27 +256,22 @@ int32_t nice_build(NiceTD &T, const Pattern &F, const std::vector<std::vector<in
     leaf.bag = {B[0]};
     T.nodes.push_back(leaf);
     int32_t top = (int32_t)T.nodes.size() - 1;
-    return introduce_all(T, F, top, std::vector<int32_t>(B.begin() + 1, B.end()));
+    return introduce_all(T, F, top, std::vector<int32_t>(B.begin() + 1, B.end()),
+                         leaving_bag(bags, parent, i), B);
   }
   std::vector<int32_t> tops;
   for (int32_t c : kids[i]) {
-    int32_t top = nice_build(T, F, bags, kids, c);
+    int32_t top = nice_build(T, F, bags, parent, kids, c);
     const std::vector<int32_t> &Bc = bags[c];
     for (int32_t u : Bc) {
       if (std::find(B.begin(), B.end(), u) != B.end()) continue;
-      NiceNode f;
-      f.type = FORGET;
-      f.child0 = top;
-      f.vertex = u;
-      for (int32_t w : T.nodes[top].bag)
-        if (w != u) f.bag.push_back(w);
-      T.nodes.push_back(f);
-      top = (int32_t)T.nodes.size() - 1;
+      if (in_bag(T, top, u)) top = push_forget(T, top, u);
     }
     std::vector<int32_t> add;
     for (int32_t u : B)
       if (std::find(Bc.begin(), Bc.end(), u) == Bc.end()) add.push_back(u);
-    top = introduce_all(T, F, top, add);
+    top = introduce_all(T, F, top, add,
+                        kids[i].size() == 1 ? leaving_bag(bags, parent, i) : none, B);
     tops.push_back(top);
   }
   int32_t top = tops[0];
@@ -277,17 +340,10 @@ bool make_nice(const Pattern &F, int32_t nbags, const int32_t *bag_ptr, const in
       if (!ok) return false;
     }
   T.nodes.clear();
-  int32_t top = nice_build(T, F, bags, kids, root);
-  for (int32_t u : bags[root]) {
-    NiceNode f;
-    f.type = FORGET;
-    f.child0 = top;
-    f.vertex = u;
-    for (int32_t w : T.nodes[top].bag)
-      if (w != u) f.bag.push_back(w);
-    T.nodes.push_back(f);
-    top = (int32_t)T.nodes.size() - 1;
-  }
+  std::vector<int32_t> par(parent, parent + nbags);
+  int32_t top = nice_build(T, F, bags, par, kids, root);
+  for (int32_t u : bags[root])
+    if (in_bag(T, top, u)) top = push_forget(T, top, u);
   return true;
 }
 
@@ -342,19 +398,18 @@ void run_trial(Run &R, int32_t t) {
       std::vector<int32_t> nb_slots;  // slots in the child tuple of u's bag neighbours
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (F.adj[u][ch.bag[s]]) nb_slots.push_back((int32_t)s);
-      // distance bound: the bag vertex of u's component nearest to u, if it is at distance 2
-      int32_t near_slot = -1;
+      // distance bound: the bag vertex w of u's component nearest to u (first in bag order
+      // among the nearest) and its F-distance to u
+      int32_t near_slot = -1, near_dist = -1;
       if (nb_slots.empty() && R.distance_prune) {
         const std::vector<int32_t> du = F.dist(u);
-        int32_t best = -1;
         for (size_t s = 0; s < ch.bag.size(); ++s) {
           const int32_t d = du[ch.bag[s]];
-          if (d >= 0 && (best < 0 || d < best)) {
-            best = d;
+          if (d >= 0 && (near_dist < 0 || d < near_dist)) {
+            near_dist = d;
             near_slot = (int32_t)s;
           }
         }
-        if (best != 2) near_slot = -1;
       }
       for (const auto &e : D[nd.child0]) {
         const std::vector<int32_t> &phi_c = e.first.first;
@@ -363,16 +418,8 @@ void run_trial(Run &R, int32_t t) {
         if (!nb_slots.empty()) {
           int32_t a = phi_c[nb_slots[0]];
           cand.assign(G.col.begin() + G.row_ptr[a], G.col.begin() + G.row_ptr[a + 1]);
-        } else if (near_slot >= 0) {  // the host vertices within distance 2 of phi(w)
-          const int32_t a = phi_c[near_slot];
-          cand.push_back(a);
-          for (int32_t i = G.row_ptr[a]; i < G.row_ptr[a + 1]; ++i) {
-            const int32_t b = G.col[i];
-            cand.push_back(b);
-            cand.insert(cand.end(), G.col.begin() + G.row_ptr[b], G.col.begin() + G.row_ptr[b + 1]);
-          }
-          std::sort(cand.begin(), cand.end());
-          cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        } else if (near_slot >= 0) {  // the host vertices within distance d of phi(w)
+          cand = G.ball(phi_c[near_slot], near_dist);
         } else {
           cand.resize(G.n);
           for (int32_t v = 0; v < G.n; ++v) cand[v] = v;

@@ -119,10 +119,39 @@ void build_nice(const std::vector<uint32_t> &adj, const std::vector<std::vector<
   auto contains = [](const std::vector<int> &v, int u) {
     return std::binary_search(v.begin(), v.end(), u);
   };
-  // introduces `todo` (increasing) on top of node t: each step takes the smallest vertex with an
-  // F-neighbour already in the bag, else the smallest, so introduces are anchored in adjacency
-  // lists whenever the pattern allows
-  auto introduce_all = [&](int t, std::vector<int> todo) {
+  auto forget_node = [&](int t, int u) {
+    NiceNode f;
+    f.type = 2;
+    f.child0 = t;
+    f.vertex = u;
+    for (int w : out[t].bag)
+      if (w != u) f.bag.push_back(w);
+    return push(f);
+  };
+  // Introduces `todo` (increasing) on top of node t while building decomposition bag `target`:
+  // each step takes the smallest vertex with an F-neighbour already in the bag, else the
+  // smallest, so introduces are anchored in adjacency lists whenever the pattern allows.  A
+  // vertex of `drop` (vertices of `target` that the next bag up no longer holds) is forgotten as
+  // soon as all its F-neighbours in `target` are in the bag (increasing order, never emptying
+  // the bag while introduces remain): no later node needs it, and a forget taken before an
+  // introduce of a non-neighbour shrinks that introduce's table
+  auto introduce_all = [&](int t, std::vector<int> todo, const std::vector<int> &drop,
+                           const std::vector<int> &target) {
+    uint32_t tmask = 0, gone = 0;  // gone: forgotten early in this chain
+    for (int w : target) tmask |= 1u << w;
+    auto early_forgets = [&](int t0) {
+      for (int q : drop) {
+        uint32_t bagmask = 0;
+        for (int w : out[t0].bag) bagmask |= 1u << w;
+        if (!(bagmask >> q & 1u)) continue;
+        if ((adj[q] & tmask & ~(bagmask | gone)) != 0) continue;  // a neighbour still to come
+        if (out[t0].bag.size() == 1 && !todo.empty()) continue;
+        t0 = forget_node(t0, q);
+        gone |= 1u << q;
+      }
+      return t0;
+    };
+    t = early_forgets(t);
     while (!todo.empty()) {
       uint32_t bagmask = 0;
       for (int w : out[t].bag) bagmask |= 1u << w;
@@ -141,26 +170,30 @@ void build_nice(const std::vector<uint32_t> &adj, const std::vector<std::vector<
       in.bag = out[t].bag;
       in.bag.insert(std::upper_bound(in.bag.begin(), in.bag.end(), u), u);
       t = push(in);
+      t = early_forgets(t);
     }
     return t;
   };
-  // chain from bag `from` to bag `to` on top of node t: forgets in increasing vertex order,
-  // then introduces
-  auto transition = [&](int t, const std::vector<int> &from, const std::vector<int> &to) {
+  // the vertices of bag i that the next bag up no longer holds (all of them at the root)
+  auto leaving = [&](int i) {
+    std::vector<int> d;
+    for (int u : bags[i])
+      if (parent[i] < 0 || !contains(bags[parent[i]], u)) d.push_back(u);
+    return d;
+  };
+  // chain from child bag `c` to its parent bag p on top of node t: forgets (increasing vertex
+  // order) of what is still in the bag and not in B_p, then the introduces of B_p \ B_c, with
+  // early forgets of B_p's leaving vertices when p has no other child (a join needs all of B_p)
+  auto transition = [&](int t, int c, int p) {
+    const std::vector<int> &from = bags[c], &to = bags[p];
     for (int u : from)
-      if (!contains(to, u)) {
-        NiceNode f;
-        f.type = 2;
-        f.child0 = t;
-        f.vertex = u;
-        for (int w : out[t].bag)
-          if (w != u) f.bag.push_back(w);
-        t = push(f);
-      }
+      if (!contains(to, u) && contains(out[t].bag, u)) t = forget_node(t, u);
     std::vector<int> todo;
     for (int u : to)
       if (!contains(from, u)) todo.push_back(u);
-    return introduce_all(t, todo);
+    const std::vector<int> none;
+    return kids[p].size() == 1 ? introduce_all(t, todo, leaving(p), to)
+                               : introduce_all(t, todo, none, to);
   };
   // explicit post-order walk of the decomposition tree; a finished child's subtree is followed
   // at once by its transition to the parent's bag, and a node with several children joins their
@@ -183,7 +216,7 @@ void build_nice(const std::vector<uint32_t> &adj, const std::vector<std::vector<
       leaf.type = 0;
       leaf.vertex = B[0];
       leaf.bag = {B[0]};
-      t = introduce_all(push(leaf), std::vector<int>(B.begin() + 1, B.end()));
+      t = introduce_all(push(leaf), std::vector<int>(B.begin() + 1, B.end()), leaving(i), B);
     } else {
       for (int c : kids[i]) {
         if (t < 0) {
@@ -198,18 +231,11 @@ void build_nice(const std::vector<uint32_t> &adj, const std::vector<std::vector<
         }
       }
     }
-    top[i] = (parent[i] >= 0) ? transition(t, B, bags[parent[i]]) : t;
+    top[i] = (parent[i] >= 0) ? transition(t, i, parent[i]) : t;
   }
   int t = top[root];
-  for (int u : bags[root]) {  // empty-bag root of degree one
-    NiceNode f;
-    f.type = 2;
-    f.child0 = t;
-    f.vertex = u;
-    for (int w : out[t].bag)
-      if (w != u) f.bag.push_back(w);
-    t = push(f);
-  }
+  for (int u : bags[root])  // empty-bag root of degree one
+    if (contains(out[t].bag, u)) t = forget_node(t, u);
   for (size_t i = 0; i < out.size(); ++i) {
     if (out[i].child0 >= 0) out[out[i].child0].parent = (int)i;
     if (out[i].child1 >= 0) out[out[i].child1].parent = (int)i;
@@ -375,7 +401,7 @@ int pos_in(const std::vector<int32_t> &bag, int u) {
 
 // ---- the planner: node by node in post-order, exact capacities ----------------------------
 int finish_run(Ctx *c, Run *R);
-int near_slot2(const Pattern &P, int u, const std::vector<int32_t> &child_bag);
+int near_slot(const Pattern &P, int u, const std::vector<int32_t> &child_bag, int *dist);
 
 // Runs every node of the nice decomposition in post-order (Section 3.1).
 //
@@ -461,6 +487,19 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     for (int j = 0; j < m; ++j) {
       bool in = false;
       for (int i = 0; i < m; ++i) in = in || t.sort_slots[i] == sl[j];
+      if (!in) return false;
+    }
+    return true;
+  };
+  // true if table t comes in runs of equal images of exactly the slots sl[0..m), sorted or
+  // clustered (a grouped introduce then shares candidate lists without sorting it; its results
+  // do not depend on the runs being whole)
+  auto grouped_by = [&](const cc::NodeTable &t, int m, const int *sl) {
+    if (sorted_by(t, m, sl)) return true;
+    if (t.hashed || t.cluster_n < m) return false;
+    for (int j = 0; j < m; ++j) {
+      bool in = false;
+      for (int i = 0; i < m; ++i) in = in || t.cluster_slots[i] == sl[j];
       if (!in) return false;
     }
     return true;
@@ -556,15 +595,18 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       a.nnb = 0;
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
-      if (a.nnb == 0 && R->opts.distance_prune && c->d_ball_ptr) {
-        // distance bound: candidates are the ball of radius 2 around the nearest bag vertex's
-        // image, walked like an adjacency list (no other bag neighbour is then checked)
-        const int s2 = near_slot2(P, nd.vertex, ch.bag);
-        if (s2 >= 0) {
+      if (a.nnb == 0 && R->opts.distance_prune) {
+        // distance bound: candidates are the ball of radius dist_F(w, u) around the image of
+        // the nearest bag vertex w, walked like an adjacency list (no other bag neighbour is
+        // then checked)
+        int dist = 0;
+        const int s = near_slot(P, nd.vertex, ch.bag, &dist);
+        auto bl = c->balls.find(dist);
+        if (s >= 0 && bl != c->balls.end()) {
           a.nnb = 1;
-          a.nb_slot[0] = s2;
-          a.G.row_ptr = c->d_ball_ptr;
-          a.G.col = c->d_ball_col;
+          a.nb_slot[0] = s;
+          a.G.row_ptr = bl->second.first;
+          a.G.col = bl->second.second;
         }
       }
       a.degF = df ? P.deg[nd.vertex] : 0;
@@ -577,7 +619,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       // that a run shares one candidate list; sort it unless its order already starts with them
       const int grouped = R->opts.group && a.nnb >= 2 && a.nnb * R->L.nb <= 64;
       void *sorted = nullptr;
-      if (grouped && !sorted_by(R->tables[y], a.nnb, a.nb_slot)) {
+      if (grouped && !grouped_by(R->tables[y], a.nnb, a.nb_slot)) {
         cc::SortSpec sp{};
         sp.L = R->L;
         sp.b = a.b_in;
@@ -702,11 +744,23 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         if (f == N - 1) break;
         continue;
       }
+      // the entries of a child sorted or clustered by some slots come out in runs of equal
+      // images of those slots: the ungrouped kernels emit each child entry's extensions
+      // together, in child order
+      int cl_n = 0, cl[cc::kMaxBag];
+      if (!grouped) {
+        const cc::NodeTable &ty = R->tables[y];
+        const int *src = ty.sort_n ? ty.sort_slots : ty.cluster_slots;
+        cl_n = ty.sort_n ? ty.sort_n : ty.cluster_n;
+        for (int j = 0; j < cl_n; ++j) cl[j] = src[j] + (src[j] >= a.p ? 1 : 0);
+      }
       void *p = A.alloc(raw * rb);
       if (!p) return CC_ENOMEM;
       rc = write_dense(p, raw, -1);
       if (rc) return rc;
       R->tables[x] = {p, raw, 0, true};
+      R->tables[x].cluster_n = cl_n;
+      for (int j = 0; j < cl_n; ++j) R->tables[x].cluster_slots[j] = cl[j];
       if (planned) R->tables[x].bound = cursor + x;  // holes: scan up to the cursor
       release_child(y);
       continue;  // size already known (exact) or on the device (planned)
@@ -1021,9 +1075,10 @@ long long csr_fingerprint(int32_t n, const int32_t *row_ptr, const int32_t *col)
 }
 
 // The distance bound of Section 3.2 (mapping expansion): for a vertex u introduced with no
-// neighbour in the bag, the slot (in the child bag) of the bag vertex of u's F-component nearest
-// to u, if that vertex is at F-distance 2; else -1 (no bound: every host vertex is a candidate).
-int near_slot2(const Pattern &P, int u, const std::vector<int32_t> &child_bag) {
+// neighbour in the bag, the slot (in the child bag) of the bag vertex w nearest to u in F (the
+// first in bag order among the nearest) and *dist = dist_F(w, u) >= 2; -1 if no bag vertex is in
+// u's component (no bound: every host vertex is a candidate).
+int near_slot(const Pattern &P, int u, const std::vector<int32_t> &child_bag, int *dist) {
   std::vector<int> d(P.nF, -1), q{u};
   d[u] = 0;
   for (size_t h = 0; h < q.size(); ++h)
@@ -1040,28 +1095,33 @@ int near_slot2(const Pattern &P, int u, const std::vector<int32_t> &child_bag) {
       slot = (int)s;
     }
   }
-  return best == 2 ? slot : -1;
+  *dist = best;
+  return best >= 2 ? slot : -1;
 }
 
-// Builds, once per graph, the CSR of every host vertex's ball of radius 2 (itself, its
-// neighbours and theirs, each once, increasing) in the context's arena.
-int ensure_ball2(Ctx *c) {
-  if (c->d_ball_ptr) return CC_OK;
+// Builds, once per graph and radius r, the CSR of every host vertex's ball of radius r (the
+// vertices a breadth-first search from it reaches within r steps, each once, increasing) in the
+// context's arena.  CC_ENOMEM if the balls hold more than 2^31 - 1 entries or do not fit.
+int ensure_ball(Ctx *c, int r) {
+  if (c->balls.count(r)) return CC_OK;
   const int32_t n = c->n;
-  std::vector<int32_t> ptr(n + 1, 0), col, stamp(n, -1), one;
+  std::vector<int32_t> ptr(n + 1, 0), col, stamp(n, -1), depth(n, 0), one;
   for (int32_t s = 0; s < n; ++s) {
     one.clear();
-    auto add = [&](int32_t v) {
-      if (stamp[v] != s) {
-        stamp[v] = s;
-        one.push_back(v);
+    one.push_back(s);
+    stamp[s] = s;
+    depth[s] = 0;
+    for (size_t h = 0; h < one.size(); ++h) {
+      const int32_t x = one[h];
+      if (depth[x] == r) continue;
+      for (int32_t i = c->h_row_ptr[x]; i < c->h_row_ptr[x + 1]; ++i) {
+        const int32_t b = c->h_col[i];
+        if (stamp[b] != s) {
+          stamp[b] = s;
+          depth[b] = depth[x] + 1;
+          one.push_back(b);
+        }
       }
-    };
-    add(s);
-    for (int32_t i = c->h_row_ptr[s]; i < c->h_row_ptr[s + 1]; ++i) {
-      const int32_t b = c->h_col[i];
-      add(b);
-      for (int32_t j = c->h_row_ptr[b]; j < c->h_row_ptr[b + 1]; ++j) add(c->h_col[j]);
     }
     std::sort(one.begin(), one.end());
     if (col.size() + one.size() > (size_t)INT32_MAX) return CC_ENOMEM;
@@ -1084,8 +1144,7 @@ int ensure_ball2(Ctx *c) {
     c->arena.release(dc);
     return CC_ECUDA;
   }
-  c->d_ball_ptr = dp;
-  c->d_ball_col = dc;
+  c->balls[r] = {dp, dc};
   return CC_OK;
 }
 
@@ -1096,19 +1155,18 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
   const Pattern &P = pi->second;
   if (col.k < P.nF) return CC_EINVAL;
   if (P.allow_fp && P.allow_fp != c->graph_fp) return CC_EINVAL;  // masks of another graph
-  if (opts && opts->distance_prune) {  // the distance bound needs the graph's radius-2 balls
-    bool need = false;
+  if (opts && opts->distance_prune) {  // the distance bound needs the graph's balls
     for (const auto &nd : P.nodes)
       if (nd.type == 1) {
         const auto &cb = P.nodes[nd.child0].bag;
         bool nb = false;
         for (int32_t w : cb) nb = nb || (P.adj[nd.vertex] >> w & 1u);
-        need = need || (!nb && near_slot2(P, nd.vertex, cb) >= 0);
+        int dist = 0;
+        if (!nb && near_slot(P, nd.vertex, cb, &dist) >= 0) {
+          const int rc = ensure_ball(c, dist);
+          if (rc) return rc;
+        }
       }
-    if (need) {
-      const int rc = ensure_ball2(c);
-      if (rc) return rc;
-    }
   }
   R.reset(new Run());
   cc_default_opts(&R->opts);
@@ -1708,9 +1766,11 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   c->arena.release(c->d_row_ptr);
   c->arena.release(c->d_col);
   c->arena.release(c->d_deg8);
-  c->arena.release(c->d_ball_ptr);
-  c->arena.release(c->d_ball_col);
-  c->d_ball_ptr = c->d_ball_col = nullptr;
+  for (auto &b : c->balls) {
+    c->arena.release(b.second.first);
+    c->arena.release(b.second.second);
+  }
+  c->balls.clear();
   c->d_row_ptr = arena_alloc<int32_t>(c, (size_t)n + 1);
   c->d_col = arena_alloc<int32_t>(c, std::max<int64_t>(1, m2));
   c->d_deg8 = arena_alloc<uint8_t>(c, std::max<int64_t>(1, n));

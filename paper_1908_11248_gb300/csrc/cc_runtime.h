@@ -148,6 +148,11 @@ struct NodeTable {
   // a dense table sorted with these bag slots most significant (sort_n == 0: no known order)
   int sort_n = 0;
   int sort_slots[kMaxBag] = {};
+  // a dense table whose entries come in runs of equal images of these slots, except where an
+  // append chunk or a kernel's tile ends (written in the order of a child sorted or clustered
+  // by them); cluster_n == 0: no known clustering
+  int cluster_n = 0;
+  int cluster_slots[kMaxBag] = {};
   // scan bound of a dense table written in chunks (holes up to it); null: the entry counter
   unsigned long long *bound = nullptr;
 };
@@ -219,8 +224,9 @@ struct Ctx {
   int32_t *d_row_ptr = nullptr, *d_col = nullptr;
   uint8_t *d_deg8 = nullptr;  // min(degree, 255) per vertex
   std::vector<int32_t> h_row_ptr, h_col;
-  // per vertex the vertices within distance 2 (CSR, built on first use by the distance bound)
-  int32_t *d_ball_ptr = nullptr, *d_ball_col = nullptr;
+  // per radius r, per vertex the vertices within distance r (CSR row pointers and columns,
+  // built on first use by the distance bound)
+  std::map<int, std::pair<int32_t *, int32_t *>> balls;
   int *d_err = nullptr;
   u64 *d_ones = nullptr;     // a device word holding ~0 (an unbounded scan limit)
   // content fingerprint of the loaded graph: plans stay valid while the graph's content is the

@@ -376,6 +376,29 @@ WORKLOADS = {
 
 GRID_SHAPES = {4: (2, 2), 6: (2, 3), 8: (2, 4), 9: (3, 3), 10: (2, 5)}
 
+# Erdos-Renyi phase-transition study (paper Section 5.4): target G(150, p) against pattern
+# G(10, q), p and q from 0 in steps of 0.03; ten colourings (iterations) per point, k = 10
+ER_PHASE = dict(n_target=150, n_pattern=10, step=0.03, iterations=10, seed=1)
+
+
+def er_phase_probs(step=ER_PHASE["step"]):
+    """Edge probabilities 0, step, 2*step, ... up to 1 (the axes of the study)."""
+    m = int(np.floor(1.0 / step + 1e-9))
+    return [round(i * step, 10) for i in range(m + 1)]
+
+
+def er_phase_instance(ip, iq, spec=ER_PHASE):
+    """Point (ip, iq) of the study: (p, q, target CSR, pattern (n_F, edges, None), colouring
+    seed).  Every point has its own seeded target and pattern; td None asks the library for a
+    minimum-width decomposition, as the paper computes one (Section 3)."""
+    probs = er_phase_probs(spec["step"])
+    p, q = probs[ip], probs[iq]
+    base = spec["seed"] * 1_000_003
+    g = erdos_renyi(spec["n_target"], p, base + 1000 * ip + iq)
+    pg = erdos_renyi(spec["n_pattern"], q, base + 500_000 + 1000 * iq + ip)
+    edges = edges_from_csr(*pg).astype(np.int32)
+    return p, q, g, (spec["n_pattern"], edges, None), base + 7 * (1000 * ip + iq) + 1
+
 
 def serve_stream(spec, count=None):
     """The query stream of a serving workload: a list of dicts with the arrival time (s), the

@@ -70,3 +70,67 @@ def node_table(G, nF, edges, zeta, bag, verts, degG=None, degF=None, allow=None)
             C |= 1 << int(zeta[v])
         tab[(tuple(m[u] for u in bag), C)] += 1
     return tab
+
+
+def _reach_through(adj, S, v):
+    """Q(S, v): the vertices outside S and v that some path from v reaches with every inner
+    vertex in S."""
+    seen, stack, out = {v}, [v], set()
+    while stack:
+        x = stack.pop()
+        for y in adj[x]:
+            if y in seen:
+                continue
+            seen.add(y)
+            if y in S:
+                stack.append(y)
+            else:
+                out.add(y)
+    return out
+
+
+def exact_treewidth(n, edges):
+    """Treewidth by definition through elimination orderings: TW(S) = min over v in S of
+    max(TW(S - v), |Q(S - v, v)|) over all vertex subsets S (Bodlaender, Fomin, Koster, Kratsch,
+    Thilikos), tw = TW(V); plain dictionary over frozensets, for n up to about 12."""
+    adj = [set() for _ in range(n)]
+    for a, b in np.asarray(edges).reshape(-1, 2):
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    tw = {frozenset(): -1}
+    for size in range(1, n + 1):
+        for S in map(frozenset, __import__("itertools").combinations(range(n), size)):
+            tw[S] = min(max(tw[S - {v}], len(_reach_through(adj, S - {v}, v))) for v in S)
+    return max(0, tw[frozenset(range(n))])
+
+
+def elimination_td(n, edges):
+    """A tree decomposition (bags, parent) from the greedy minimum-degree elimination ordering:
+    bag(v) = v and its neighbours when v is eliminated (which then become a clique); the parent
+    of bag(v) is the bag of the first-eliminated of those neighbours; bags whose vertex has no
+    later neighbour (one per connected component) are chained under the last one."""
+    adj = [set() for _ in range(n)]
+    for a, b in np.asarray(edges).reshape(-1, 2):
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    left, order, nbrs = set(range(n)), [], {}
+    while left:
+        v = min(left, key=lambda x: (len(adj[x] & left), x))
+        nb = adj[v] & left - {v}
+        nbrs[v] = nb
+        for a in nb:
+            adj[a] |= nb - {a}
+        left.remove(v)
+        order.append(v)
+    pos = {v: i for i, v in enumerate(order)}
+    bags = [sorted({v} | nbrs[v]) for v in order]
+    parent, roots = [], []
+    for i, v in enumerate(order):
+        if nbrs[v]:
+            parent.append(pos[min(nbrs[v], key=lambda a: pos[a])])
+        else:
+            parent.append(-1)
+            roots.append(i)
+    for a, b in zip(roots, roots[1:]):
+        parent[a] = b
+    return bags, parent

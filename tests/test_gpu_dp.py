@@ -495,13 +495,16 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
 
 @pytest.mark.parametrize("fuse", [2, 1, 0])
 def test_distance_bound_matches_oracle(ctx, fuse):
-    """distance_prune (Section 3.2, mapping expansion): an introduced vertex whose nearest
-    same-component bag vertex is two steps away takes only the radius-2 ball of that vertex's
-    image.  Counts, table sizes (exact and planned) and the enumeration equal the oracle's with
-    the same bound; the root equals the unbounded run's."""
+    """distance_prune (Section 3.2, mapping expansion): an introduced vertex with no bag
+    neighbour takes only the ball of radius dist_F(w, u) around the image of its nearest bag
+    vertex w (distances 2, 3 and 4 here).  Counts, table sizes (exact and planned) and the
+    enumeration equal the oracle's with the same bound; the root equals the unbounded run's."""
     n = 300
     g = synth.erdos_renyi(n, 6.0 / n, 12)
-    pats = [(3, np.array([(0, 1), (1, 2)], np.int32), ([[0, 2], [0, 1, 2]], [1, -1])),
+    path = lambda m: np.array([(i, i + 1) for i in range(m - 1)], np.int32)  # noqa: E731
+    pats = [(3, path(3), ([[0, 2], [0, 1, 2]], [1, -1])),
+            (4, path(4), ([[0, 3], [0, 1, 3], [1, 2, 3]], [1, 2, -1])),
+            (5, path(5), ([[0, 4], [0, 1, 4], [1, 2, 4], [2, 3, 4]], [1, 2, 3, -1])),
             synth.random_partial_ktree(8, 3, 4), synth.random_partial_ktree(7, 3, 2)]
     cc.cc_load_graph(ctx.h, *g)
     shrunk = False

@@ -40,7 +40,7 @@ def test_nice_decomposition_equals_oracle(pi):
     nodes, width = cc.cc_nice_decomposition(nF, e, td)
     assert nodes == oracle.nice_td(nF, e, td)
     check_nice(nF, e, td, nodes)
-    assert width == max(len(b) for b in td[0]) - 1
+    assert width == max(len(nd[4]) for nd in nodes) - 1 <= max(len(b) for b in td[0]) - 1
 
 
 @pytest.mark.parametrize("pat,tw", [
@@ -108,3 +108,16 @@ def test_solve_trials_count():
     assert cc.cc_solve_trials(0, 0.1) == -1
     assert cc.cc_solve_trials(5, 0.0) == -1
     assert cc.cc_solve_trials(5, 1.0) == -1
+
+
+def test_width_of_phase_study_patterns():
+    """The width the Erdos-Renyi study records for a pattern G(10, q) (the minimum-width
+    decomposition the library computes when none is given) is its treewidth, by the subset
+    recurrence over elimination orderings, across the q axis."""
+    from tests import brute
+    import synth
+
+    for iq in range(0, 34, 3):
+        _, q, _, pat, _ = synth.er_phase_instance(7, iq)
+        nodes, w = cc.cc_nice_decomposition(pat[0], pat[1], None)
+        assert w == brute.exact_treewidth(pat[0], pat[1]), q

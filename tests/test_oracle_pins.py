@@ -108,8 +108,10 @@ def check_nice(nF, edges, td, nodes):
         assert len(tops) == 1
     for a, b in np.asarray(edges).reshape(-1, 2):
         assert any(a in nd[4] and b in nd[4] for nd in nodes)
-    width = max(len(b) for b in td[0])
-    assert max(len(nd[4]) for nd in nodes) == width
+    # built from the given decomposition: every bag lies inside one of its bags (so the width
+    # is at most the given width; forgetting a vertex early can make it smaller)
+    assert all(any(set(nd[4]) <= set(b) for b in td[0]) for nd in nodes)
+    assert max(len(nd[4]) for nd in nodes) <= max(len(b) for b in td[0])
 
 
 PATTERNS = [
@@ -504,6 +506,37 @@ def test_distance_bound_table_by_definition():
             got = {(tuple(int(v) for v in phi[i]), int(mask[i])): int(cnt[i])
                    for i in range(len(mask))}
             assert got == want
+
+
+def test_distance_bound_at_distance_three_by_definition():
+    """Path 0-1-2-3 with bags {0,3} under {0,1,3} under {1,2,3}: vertex 3 is introduced next to
+    0 at F-distance 3 with no bag neighbour, so the pruned table is the definition's table
+    restricted to phi(3) within distance 3 of phi(0) (a breadth-first ball, not the radius-2
+    one); the root is unchanged."""
+    e = np.array([(0, 1), (1, 2), (2, 3)], np.int32)
+    td = ([[0, 3], [0, 1, 3], [1, 2, 3]], [1, 2, -1])
+    nodes = oracle.nice_td(4, e, td)
+    x = next(i for i, nd in enumerate(nodes) if nd[0] == 1 and nd[3] == 3 and len(nd[4]) == 2)
+    vs = brute.vstar(nodes)
+    shrunk = beyond2 = False
+    for seed in range(4):
+        g = synth.erdos_renyi(16, 0.13, 60 + seed)
+        G = brute.adj_sets(*g)
+        zeta = np.random.default_rng(seed).integers(0, 4, size=(2, 16)).astype(np.uint8)
+        plain = oracle.run_dp(g, (4, e, td), zeta, 4, degree_filter=False)
+        pruned = oracle.run_dp(g, (4, e, td), zeta, 4, degree_filter=False, distance_prune=True)
+        assert np.array_equal(plain.count, pruned.count)
+        shrunk = shrunk or pruned.node_sizes[:, x].sum() < plain.node_sizes[:, x].sum()
+        for t in range(2):
+            full = brute.node_table(G, 4, e, zeta[t], nodes[x][4], vs[x])
+            want = {k: v for k, v in full.items() if k[0][1] in _gdist(g, k[0][0], 3)}
+            near2 = {k for k in full if k[0][1] in _gdist(g, k[0][0], 2)}
+            phi, mask, cnt = pruned.table(t, x, 2)
+            got = {(tuple(int(v) for v in phi[i]), int(mask[i])): int(cnt[i])
+                   for i in range(len(mask))}
+            assert got == want
+            beyond2 = beyond2 or len(set(want) - near2) > 0  # radius 3, not 2
+    assert shrunk and beyond2
 
 
 @pytest.mark.parametrize("pat", [synth.random_partial_ktree(7, 3, 2),
