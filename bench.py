@@ -738,7 +738,7 @@ def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
         while len(res) < len(tickets):
             for i, t in enumerate(tickets):
                 if i not in res:
-                    done, status, counts, exists, lat = cc.cc_serve_poll(h, t, trials[i])
+                    done, status, counts, exists, lat, _ = cc.cc_serve_poll(h, t, trials[i])
                     if done:
                         res[i] = (status, counts, lat)
             time.sleep(0.0005)

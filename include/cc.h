@@ -160,23 +160,26 @@ typedef struct {
                          /*    per pass (decoupled look-back); 2: as 1, each block bringing its */
                          /*    next tile into shared memory by bulk copy while it works on the  */
                          /*    current one; 0: histogram+scan+scatter passes                    */
-  int32_t distance_prune; /* 1: an introduced vertex with no bag neighbour whose nearest bag   */
-                         /*    vertex w of its F-component is at F-distance 2 takes only the   */
-                         /*    host vertices within distance 2 of phi(w) (Section 3.2, mapping  */
-                         /*    expansion); root results are unchanged, tables shrink            */
+  int32_t distance_prune; /* 1: an introduced vertex with no bag neighbour takes only the host */
+                         /*    vertices within distance dist_F(w, u) of phi(w), w the bag vertex */
+                         /*    nearest to it in F (Section 3.2, mapping expansion); root results */
+                         /*    are unchanged, tables shrink                                      */
+  int32_t max_slices;    /* most slices a single trial that does not fit may be split into     */
+                         /*    (CC_MODE_SLICED); 0 = 4096                                        */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
- * 0.5, block 256, profile 0, group 1, sort_sweep 1, distance_prune 0). */
+ * 0.5, block 256, profile 0, group 1, sort_sweep 1, distance_prune 0, max_slices 0). */
 void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in
  * the same launches: the trial index is part of every table key).  Requires k >= n_F.  On
  * success *run_id names the result; per-trial results stay on the device until read.  When all
  * trials together do not fit the arena and no tables are to be kept (retain 0), the trials run in
- * halves, recursively, until they fit (trial streaming; cc_run_mode gives CC_MODE_STREAMED).
- * Errors: CC_EINVAL, CC_ENOTFOUND, CC_ENOMEM (arena too small even for one trial: nothing is
- * kept),
+ * halves, recursively, until they fit (trial streaming; cc_run_mode gives CC_MODE_STREAMED), and
+ * a single trial that does not fit runs in slices by the image of one pattern vertex
+ * (CC_MODE_SLICED).  Errors: CC_EINVAL, CC_ENOTFOUND, CC_ENOMEM (arena too small even for one
+ * trial in opts->max_slices slices: nothing is kept),
  * CC_EKEYWIDTH (ceil(log2 trials) + width_bags * ceil(log2 n) + k > 128), CC_ECUDA. */
 int cc_run_dp(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_run_opts *opts,
               int32_t *run_id);
@@ -241,6 +244,14 @@ int cc_solve(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t k, double e
 #define CC_MODE_STREAMED 3 /* all trials together did not fit: ran in chunks of trials (halved
                             * until they fit); counts, exists flags and table sizes as for one
                             * run, no tables kept */
+#define CC_MODE_SLICED 4   /* as CC_MODE_STREAMED, and a single trial did not fit either: it ran
+                            * in s slices, slice i restricting the vertex of the decomposition's
+                            * first leaf to host vertices v = i (mod s) through allowed-mapping
+                            * masks (Section 3.2); the embeddings split by that vertex's image,
+                            * so counts (summed mod 2^64) and exists flags are exact, while table
+                            * sizes are sums over slices (an upper bound for nodes whose bag
+                            * lacks that vertex); s doubles from 2 until every slice fits, at most
+                            * max_slices of the run's options (then CC_ENOMEM) */
 
 /* *mode = one of CC_MODE_* for run `run_id`.  Errors: CC_EINVAL, CC_ENOTFOUND. */
 int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode);
@@ -354,32 +365,43 @@ int cc_count_noalloc(int device, void *cuda_stream, int32_t n, const int32_t *h_
  * others run share the GPU with them.  Each query colours the graph (cc_color with its seed,
  * trials and k) and runs the DP with cc_default_opts inside its own arena range, reserved at
  * admission and trimmed to what its kernels use.  A query whose (pattern, trials, k) has no
- * plan yet runs exactly, synchronously on its slot; later ones of the same key run planned, and
- * one that outgrows its plan runs again exactly.  A query that runs out of memory while running
- * alone ends with CC_ENOMEM, and later queries of its key are refused with CC_ENOMEM at once.  Results are those of cc_count and cc_decide
- * for the same inputs, whatever else runs.  Errors: CC_EINVAL (no graph, bad max_inflight),
- * CC_EBUSY (already serving), CC_ECUDA. */
+ * plan yet runs exactly, synchronously on its slot while the other slots keep running; later
+ * ones of the same key run planned, and one that outgrows its plan runs again exactly.  A query
+ * whose tables do not fit the budget while running alone runs as cc_run_dp would (its trials in
+ * chunks, a single trial in slices by the image of one pattern vertex), synchronously; only if
+ * that fails too does it end with CC_ENOMEM, and later queries of its key are refused with
+ * CC_ENOMEM at once.  A query with limit > 0 keeps its tables and, once its DP is done,
+ * reconstructs the `limit` lexicographically smallest distinct embeddings over its trials
+ * (cc_enumerate), synchronously on its slot; such a query must fit without slicing.  Results
+ * are those of cc_count, cc_decide and cc_enumerate for the same inputs, whatever else runs.
+ * Errors: CC_EINVAL (no graph, bad max_inflight), CC_EBUSY (already serving), CC_ECUDA. */
 int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight);
 
 /* Queues a query of pattern `pattern_id` under colouring (seed, trials, k) and returns at once
- * with *ticket.  A bad pattern id or k < n_F is reported by the query's status.  Thread-safe.
- * Errors: CC_EINVAL (not serving or stopping, trials < 1, k outside [1, 32]). */
+ * with *ticket; limit > 0 also asks for its first `limit` embeddings.  A bad pattern id or
+ * k < n_F is reported by the query's status.  Thread-safe.  Errors: CC_EINVAL (not serving or
+ * stopping, trials < 1, k outside [1, 32]). */
 int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t trials, int32_t k,
-                    int64_t *ticket);
+                    uint64_t limit, int64_t *ticket);
 
 /* Polls a ticket: *done = 0 while it waits or runs.  Once done, *status is its result code and,
- * if that is CC_OK, h_counts[trials] and h_exists[trials] (either may be NULL) hold its counts
- * and exists flags and *latency_ns the time from submission to completion; the ticket is then
- * forgotten (a later poll gives CC_ENOTFOUND).  Thread-safe. */
+ * if that is CC_OK, h_counts[trials] and h_exists[trials] hold its counts and exists flags,
+ * h_rows[limit * n_F] its embeddings (lexicographic, without repeats) and *n_rows their number
+ * (0 when the query's limit was 0), and *latency_ns the time from submission to completion; any
+ * output pointer may be NULL.  The ticket is then forgotten (a later poll gives CC_ENOTFOUND).
+ * Thread-safe. */
 int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
-                  uint64_t *h_counts, uint8_t *h_exists, int64_t *latency_ns);
+                  uint64_t *h_counts, uint8_t *h_exists, int32_t *h_rows, uint64_t *n_rows,
+                  int64_t *latency_ns);
 
 /* Server counters since it last started: queries submitted and completed, the most queries seen
  * running at once, the most arena bytes they held at once, exact runs (first queries of a key
- * and reruns) and reruns of queries that outgrew their plan.  Any pointer may be NULL.
- * Errors: CC_EINVAL, CC_ENOTFOUND (the context never served). */
+ * and reruns), reruns of queries that outgrew their plan, and queries that ran split (their
+ * tables did not fit the budget whole).  Any pointer may be NULL.  Errors: CC_EINVAL,
+ * CC_ENOTFOUND (the context never served). */
 int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed, int32_t *inflight_max,
-                   uint64_t *reserved_max, uint64_t *exact_runs, uint64_t *reruns);
+                   uint64_t *reserved_max, uint64_t *exact_runs, uint64_t *reruns,
+                   uint64_t *sliced);
 
 /* Stops the server after the queued and running queries finish; results not yet polled stay
  * available.  Returns CC_OK if no server runs. */

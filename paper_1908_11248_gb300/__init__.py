@@ -35,7 +35,7 @@ EXPORTS = [
     "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
     "cc_load_pattern_masked", "cc_enumerate_sets", "cc_probe_bounded_wait",
 ]
-RUN_MODES = ["exact", "planned", "graph", "streamed"]
+RUN_MODES = ["exact", "planned", "graph", "streamed", "sliced"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
                 "join_build", "join_count", "join_write", "root", "sort", "reduce"]
 
@@ -56,7 +56,8 @@ class cc_run_opts(ctypes.Structure):
                 ("fuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("load_factor", ctypes.c_float), ("block", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("group", ctypes.c_int32),
-                ("sort_sweep", ctypes.c_int32), ("distance_prune", ctypes.c_int32)]
+                ("sort_sweep", ctypes.c_int32), ("distance_prune", ctypes.c_int32),
+                ("max_slices", ctypes.c_int32)]
 
 
 _lib = None
@@ -96,15 +97,15 @@ def lib():
         "cc_probe_bounded_wait": ([P, ctypes.c_uint32], ctypes.c_int),
         "cc_release": ([P, i32], ctypes.c_int),
         "cc_serve_start": ([P, sz, i32], ctypes.c_int),
-        "cc_serve_submit": ([P, i32, u64, i32, i32, P], ctypes.c_int),
-        "cc_serve_poll": ([P, i64, P, P, P, P, P], ctypes.c_int),
+        "cc_serve_submit": ([P, i32, u64, i32, i32, u64, P], ctypes.c_int),
+        "cc_serve_poll": ([P, i64, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_serve_stop": ([P], ctypes.c_int),
         "cc_run_timings": ([P, i32, i32, P, P, P, P, P], ctypes.c_int),
         "cc_context_stats": ([P, P, P, P], ctypes.c_int),
         "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_check_graph": ([i32, P, P], ctypes.c_int),
         "cc_run_mode": ([P, i32, P], ctypes.c_int),
-        "cc_serve_stats": ([P, P, P, P, P, P, P], ctypes.c_int),
+        "cc_serve_stats": ([P, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_autotune": ([P, i32, i32, P, i32, i32, P, P, P, P], ctypes.c_int),
         "cc_solve_trials": ([i32, ctypes.c_double], i32),
         "cc_load_pattern_masked": ([P, i32, i32, P, P, P, P], ctypes.c_int),
@@ -409,26 +410,33 @@ def cc_serve_start(ctx, mem_budget: int = 0, max_inflight: int = 8):
     _check(lib().cc_serve_start(ctx, mem_budget, max_inflight), "cc_serve_start")
 
 
-def cc_serve_submit(ctx, pid: int, seed: int, trials: int, k: int) -> int:
+def cc_serve_submit(ctx, pid: int, seed: int, trials: int, k: int, limit: int = 0) -> int:
     t = ctypes.c_int64(0)
-    _check(lib().cc_serve_submit(ctx, pid, seed, trials, k, ctypes.byref(t)), "cc_serve_submit")
+    _check(lib().cc_serve_submit(ctx, pid, seed, trials, k, limit, ctypes.byref(t)),
+           "cc_serve_submit")
     return t.value
 
 
-def cc_serve_poll(ctx, ticket: int, trials: int):
+def cc_serve_poll(ctx, ticket: int, trials: int, limit: int = 0, nF: int = 0):
+    """(done, status, counts, exists, latency ns, rows int32[n_rows, nF])."""
     done, status, lat = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
     counts = np.zeros(trials, np.uint64)
     exists = np.zeros(trials, np.uint8)
+    rows = np.zeros((max(1, limit), max(1, nF)), np.int32)
+    nrows = ctypes.c_uint64(0)
     _check(lib().cc_serve_poll(ctx, ticket, ctypes.byref(done), ctypes.byref(status), _p(counts),
-                               _p(exists), ctypes.byref(lat)), "cc_serve_poll")
-    return bool(done.value), status.value, counts, exists, lat.value
+                               _p(exists), _p(rows) if limit else None, ctypes.byref(nrows),
+                               ctypes.byref(lat)), "cc_serve_poll")
+    return (bool(done.value), status.value, counts, exists, lat.value,
+            rows[:nrows.value, :nF] if limit else rows[:0, :0])
 
 
 def cc_serve_stats(ctx) -> dict:
     v = [ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_int32(0), ctypes.c_uint64(0),
-         ctypes.c_uint64(0), ctypes.c_uint64(0)]
+         ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)]
     _check(lib().cc_serve_stats(ctx, *[ctypes.byref(x) for x in v]), "cc_serve_stats")
-    names = ["submitted", "completed", "inflight_max", "reserved_max", "exact_runs", "reruns"]
+    names = ["submitted", "completed", "inflight_max", "reserved_max", "exact_runs", "reruns",
+             "sliced"]
     return {k: int(x.value) for k, x in zip(names, v)}
 
 

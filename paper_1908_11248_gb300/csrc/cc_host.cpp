@@ -1468,9 +1468,13 @@ int replay_graph(Ctx *c, cc::GraphSet &gs, const std::vector<Run *> &Rs) {
   return worst;
 }
 
+int run_sliced(Ctx *c, Run *R, const cc::Coloring &view, int32_t t0,
+               const std::vector<long long> &ckey, int s0);
+
 // Trials [t0, t0 + nt) of run R as a run of their own over their rows of the colouring; if
-// they do not fit either, each half in turn.  Per-trial results do not depend on the other
-// trials, so the chunk's exists flags and counts are R's, and table sizes add over chunks.
+// they do not fit either, each half in turn, and a single trial in slices (run_sliced).
+// Per-trial results do not depend on the other trials, so the chunk's exists flags and counts
+// are R's, and table sizes add over chunks.
 int run_chunk(Ctx *c, Run *R, const cc::Coloring &col, int32_t t0, int32_t nt) {
   cc::Coloring view;
   view.trials = nt;
@@ -1480,6 +1484,11 @@ int run_chunk(Ctx *c, Run *R, const cc::Coloring &col, int32_t t0, int32_t nt) {
   std::vector<long long> key;
   int rc = init_run(c, R->pattern, view, -1, &R->opts, S, key);
   if (rc) return rc;
+  auto pl = c->plans.find(key);
+  if (nt == 1 && pl != c->plans.end() && pl->second.slices > 0) {  // known not to fit whole
+    free_run(c, S.get());
+    return run_sliced(c, R, view, t0, key, pl->second.slices);
+  }
   rc = run_direct(c, S.get(), view, key, false);
   if (!rc) {
     if (cudaMemcpyAsync(R->d_exists + t0, S->d_exists, nt * sizeof(unsigned),
@@ -1497,12 +1506,101 @@ int run_chunk(Ctx *c, Run *R, const cc::Coloring &col, int32_t t0, int32_t nt) {
     const int32_t h = nt / 2;
     rc = run_chunk(c, R, col, t0, h);
     if (!rc) rc = run_chunk(c, R, col, t0 + h, nt - h);
+  } else if (rc == CC_ENOMEM) {
+    rc = run_sliced(c, R, view, t0, key, 2);
   }
   return rc;
 }
 
-// Runs R's trials in chunks after all of them together ran out of memory (trial streaming).
-int run_streamed(Ctx *c, Run *R, const cc::Coloring &col) {
+// Trial t0 of run R (colouring `view` of that one trial, plan key ckey) split by the image of
+// one pattern vertex, after the trial alone ran out of memory.  The colourful embeddings of F
+// fall into disjoint classes by the host vertex that pattern vertex r (the vertex of the first
+// leaf: every node on the way from that leaf to the root holds r in V*_x, so its tables shrink)
+// is mapped to.  Slice i of s restricts r to the host vertices v = i (mod s) through
+// allowed-mapping masks (Section 3.2, masking unprofitable mappings), so it counts exactly the
+// classes of those vertices: the trial's count is the sum of the slices' counts (mod 2^64) and a
+// copy exists iff a slice finds one.  s doubles, from s0 (or from the count remembered for the
+// key), until every slice fits, up to 4096 slices.  Table sizes add over slices: exact for the
+// nodes whose bag holds r, an upper bound for the others.
+int run_sliced(Ctx *c, Run *R, const cc::Coloring &view, int32_t t0,
+               const std::vector<long long> &ckey, int s0) {
+  constexpr int32_t kSlicePattern = INT32_MIN + 1;  // the slices' masked copy of the pattern
+  const int kMaxSlices = R->opts.max_slices > 0 ? R->opts.max_slices : 4096;
+  const Pattern &P = c->patterns.at(R->pattern);
+  const int r = P.nodes[0].vertex;
+  Arena &A = active_arena(c);
+  uint32_t *mask = arena_alloc<uint32_t>(c, std::max<size_t>(1, (size_t)c->n));
+  if (!mask) return CC_ENOMEM;
+  {
+    Pattern Ps = P;
+    Ps.d_allow = mask;
+    Ps.allow_fp = c->graph_fp;
+    c->patterns[kSlicePattern] = Ps;
+  }
+  const size_t N = R->sizes.size();
+  int rc = CC_ENOMEM;
+  for (int s = std::max(2, s0); s <= kMaxSlices && rc == CC_ENOMEM; s *= 2) {
+    u64 count = 0;
+    unsigned exists = 0;
+    std::vector<u64> sizes(N, 0), pairs(N, 0);
+    rc = CC_OK;
+    for (int i = 0; i < s && !rc; ++i) {
+      if (cc::launch_slice_mask(c->stream, c->dev, P.d_allow, c->n, 1u << r, s, i, mask)) {
+        rc = CC_ECUDA;
+        break;
+      }
+      c->launches++;
+      std::unique_ptr<Run> S;
+      std::vector<long long> key;
+      rc = init_run(c, kSlicePattern, view, -1, &R->opts, S, key);
+      if (rc) break;
+      key = ckey;  // the slice's own plan: the trial's key with (slices, slice) appended
+      key.push_back(-2);
+      key.push_back(s);
+      key.push_back(i);
+      rc = run_direct(c, S.get(), view, key, false);
+      u64 hc = 0;
+      unsigned he = 0;
+      if (!rc &&
+          (cudaMemcpyAsync(&hc, S->d_count, sizeof(u64), cudaMemcpyDeviceToHost, c->stream) !=
+               cudaSuccess ||
+           cudaMemcpyAsync(&he, S->d_exists, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           c->stream) != cudaSuccess ||
+           cudaStreamSynchronize(c->stream) != cudaSuccess))
+        rc = CC_ECUDA;
+      if (!rc) {
+        count += hc;
+        exists |= he ? 1u : 0u;
+        for (size_t x = 0; x < N; ++x) {
+          sizes[x] += S->sizes[x];
+          pairs[x] = std::max(pairs[x], S->pairs[x]);
+        }
+      }
+      free_run(c, S.get());
+    }
+    if (!rc) {
+      if (cudaMemcpyAsync(R->d_count + t0, &count, sizeof(u64), cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess ||
+          cudaMemcpyAsync(R->d_exists + t0, &exists, sizeof(unsigned), cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        rc = CC_ECUDA;
+      for (size_t x = 0; x < N && !rc; ++x) {
+        R->sizes[x] += sizes[x];
+        R->pairs[x] = std::max(R->pairs[x], pairs[x]);
+      }
+      if (!rc) c->plans[ckey].slices = s;
+      R->sliced = std::max(R->sliced, s);
+    }
+  }
+  c->patterns.erase(kSlicePattern);
+  A.release(mask);
+  return rc;
+}
+
+// Runs R's trials in chunks after all of them together ran out of memory (trial streaming),
+// down to single trials in slices.
+int run_split(Ctx *c, Run *R, const cc::Coloring &col) {
   const int N = (int)c->patterns.at(R->pattern).nodes.size();
   int rc = reset_run(c, R, N);
   if (rc) return rc;
@@ -1510,9 +1608,13 @@ int run_streamed(Ctx *c, Run *R, const cc::Coloring &col) {
   R->pairs.assign(N, 0);
   R->planned = R->graphed = false;
   R->streamed = true;
-  const int32_t h = R->trials / 2;
-  rc = run_chunk(c, R, col, 0, h);
-  if (!rc) rc = run_chunk(c, R, col, h, R->trials - h);
+  if (R->trials == 1) {
+    rc = run_chunk(c, R, col, 0, 1);
+  } else {
+    const int32_t h = R->trials / 2;
+    rc = run_chunk(c, R, col, 0, h);
+    if (!rc) rc = run_chunk(c, R, col, h, R->trials - h);
+  }
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CC_ECUDA;
   return rc;
 }
@@ -1527,7 +1629,7 @@ int run_one(Ctx *c, Run *R, const std::vector<long long> &key) {
     drop_all_graphs(c);
     rc = run_direct(c, R, col, key, false);
   }
-  if (rc == CC_ENOMEM && R->trials > 1 && !R->retained) rc = run_streamed(c, R, col);
+  if (rc == CC_ENOMEM && !R->retained) rc = run_split(c, R, col);
   return rc;
 }
 
@@ -1674,6 +1776,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->fuse = 2;
   o->sort_sweep = 1;
   o->distance_prune = 0;
+  o->max_slices = 0;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
@@ -2185,7 +2288,8 @@ int cc_run_mode(cc_ctx *ctx, int32_t run_id, int32_t *mode) {
   if (!c || !mode) return CC_EINVAL;
   Run *R = find_run(c, run_id);
   if (!R) return CC_ENOTFOUND;
-  *mode = R->streamed  ? CC_MODE_STREAMED
+  *mode = R->sliced     ? CC_MODE_SLICED
+          : R->streamed ? CC_MODE_STREAMED
           : R->graphed ? CC_MODE_GRAPH
           : R->planned ? CC_MODE_PLANNED
                        : CC_MODE_EXACT;

@@ -177,6 +177,10 @@ int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
 int launch_intro_warp(cudaStream_t s, const DevInfo &d, int kw, int mode, const IntroArgs &a);
 // one warp polls *flag (which nothing sets) `polls` times, then sets kErrTimeout in *err
 int launch_wait_probe(cudaStream_t s, const unsigned long long *flag, unsigned polls, int *err);
+// allowed-mapping masks restricting the pattern vertex of bit ubit to the host vertices
+// v = slice (mod slices), other bits from base (null: all allowed)
+int launch_slice_mask(cudaStream_t s, const DevInfo &d, const uint32_t *base, int32_t n,
+                      uint32_t ubit, int32_t slices, int32_t slice, uint32_t *out);
 int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
                 uint8_t *deg8);
 // Grouped introduce (child sorted by bag-neighbour images), warp by warp, for planned runs;

@@ -952,6 +952,23 @@ __global__ void deg8_kernel(const int32_t *row_ptr, int32_t n, uint8_t *deg8) {
   }
 }
 
+// Allowed-mapping masks of one slice of a run: pattern vertex u (bit ubit) may be mapped only to
+// host vertices v with v mod slices == slice; every other bit comes from base (all ones when
+// base is null).
+__global__ void slice_mask_kernel(const uint32_t *base, int32_t n, uint32_t ubit, int32_t slices,
+                                  int32_t slice, uint32_t *out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const uint32_t m = base ? base[v] : 0xFFFFFFFFu;
+    out[v] = v % slices == slice ? m : (m & ~ubit);
+  }
+}
+
+int launch_slice_mask(cudaStream_t s, const DevInfo &d, const uint32_t *base, int32_t n,
+                      uint32_t ubit, int32_t slices, int32_t slice, uint32_t *out) {
+  if (n > 0) slice_mask_kernel<<<d.sms * 4, 256, 0, s>>>(base, n, ubit, slices, slice, out);
+  return (int)cudaGetLastError();
+}
+
 int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_t n,
                 uint8_t *deg8) {
   if (n > 0) deg8_kernel<<<d.sms * 4, 256, 0, s>>>(row_ptr, n, deg8);

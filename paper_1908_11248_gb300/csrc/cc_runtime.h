@@ -164,6 +164,7 @@ struct Plan {
   size_t peak_bytes = 0;  // largest arena use of a run beyond what it started with
   int runs = 0;
   size_t refused = 0;  // a served run of this key ran out of memory in a range this large
+  int slices = 0;      // a single trial of this key fitted once split into this many slices
 };
 
 struct Timing {
@@ -190,6 +191,7 @@ struct Run {
   bool planned = false;
   bool graphed = false;
   bool streamed = false;  // its trials ran in chunks (all at once did not fit)
+  int sliced = 0;         // most slices one of its trials was split into (0: none)
   u64 *d_blk = nullptr;  // per-run scratch: block counts and bases, pair counters
   int *d_err = nullptr;  // per-run device error word
   Arena *home = nullptr;  // the arena its memory came from (null: the context's)
@@ -289,6 +291,10 @@ void update_plan(Ctx *c, const std::vector<long long> &key, const Run *R, size_t
 // false (exactly again if it proves too small), else exactly; updates the plan.
 int run_direct(Ctx *c, Run *R, const Coloring &col, const std::vector<long long> &key,
                bool exact_only);
+// Runs R (tables not kept) after it ran out of memory: its trials in halves, and a single trial
+// split by the image of one pattern vertex into slices that fit (results exact; table sizes add
+// over chunks and slices).
+int run_split(Ctx *c, Run *R, const Coloring &col);
 // Destroys every captured graph and gives back its memory.
 void drop_all_graphs(Ctx *c);
 // Checks the tree decomposition (bags, parent) of P's graph (P.nF, P.adj set) and builds P's

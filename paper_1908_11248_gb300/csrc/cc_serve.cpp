@@ -37,6 +37,7 @@ struct ServeQuery {
   int64_t ticket = 0;
   int32_t pattern = 0, trials = 0, k = 0;
   uint64_t seed = 0;
+  uint64_t limit = 0;  // > 0: also reconstruct the first `limit` embeddings (Section 4)
   bool exact = false;  // run exactly (the plan proved too small)
   Clock::time_point submitted;
 };
@@ -46,6 +47,8 @@ struct ServeResult {
   int32_t status = CC_OK;
   std::vector<u64> counts;
   std::vector<uint8_t> exists;
+  std::vector<int32_t> rows;  // n_rows * n_F embeddings, lexicographic
+  u64 n_rows = 0;
   int64_t latency_ns = 0;
 };
 
@@ -76,7 +79,7 @@ struct Server {
   std::vector<ServeSlot> slots;
   cc_run_opts opts{};
   // counters
-  u64 submitted = 0, completed = 0, exact_runs = 0, reruns = 0;
+  u64 submitted = 0, completed = 0, exact_runs = 0, reruns = 0, sliced = 0;
   int32_t inflight_max = 0;
   size_t reserved_max = 0;
 };
@@ -86,13 +89,15 @@ namespace {
 void wake(Server *S) { S->cv.notify_all(); }
 
 void publish(Server *S, const ServeQuery &q, int32_t status, std::vector<u64> counts,
-             std::vector<uint8_t> exists) {
+             std::vector<uint8_t> exists, std::vector<int32_t> rows = {}, u64 n_rows = 0) {
   std::lock_guard<std::mutex> g(S->mu);
   ServeResult &r = S->results[q.ticket];
   r.done = true;
   r.status = status;
   r.counts = std::move(counts);
   r.exists = std::move(exists);
+  r.rows = std::move(rows);
+  r.n_rows = n_rows;
   r.latency_ns =
       std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - q.submitted).count();
   S->completed++;
@@ -194,13 +199,16 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
   sl.view.trials = q.trials;
   sl.view.k = q.k;
   sl.view.d_colors = colours;
-  if (!rc) rc = rt::init_run(c, q.pattern, sl.view, -1, &S->opts, sl.run, sl.key);
+  cc_run_opts qo = S->opts;
+  qo.retain = q.limit > 0 ? 1 : 0;  // a reconstruction needs every node's table
+  if (!rc) rc = rt::init_run(c, q.pattern, sl.view, -1, &qo, sl.run, sl.key);
   Outcome out = kDone;
   bool published = false;
   if (!rc) {
     bool exact = true;
     auto pl = c->plans.find(sl.key);
-    if (!q.exact && pl != c->plans.end() && pl->second.runs > 0) {
+    const bool split = pl != c->plans.end() && pl->second.slices > 0 && q.limit == 0;
+    if (!q.exact && !split && q.limit == 0 && pl != c->plans.end() && pl->second.runs > 0) {
       exact = false;
       rc = rt::reset_run(c, sl.run.get(), (int)P.nodes.size());
       if (!rc) rc = rt::run_nodes(c, sl.run.get(), P, sl.view, &pl->second);
@@ -219,20 +227,47 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
       }
     }
     if (!rc && exact) {
+      // run here, to completion: exactly (first query of its key, or one that outgrew its
+      // plan), in slices when a single trial of its key needs more than the budget, or
+      // planned with its tables kept when it asks for embeddings
       {
         std::lock_guard<std::mutex> g2(S->mu);
-        S->exact_runs++;
+        if (q.limit == 0 || q.exact || pl == c->plans.end() || pl->second.runs == 0)
+          S->exact_runs++;
       }
-      rc = rt::run_direct(c, sl.run.get(), sl.view, sl.key, true);
+      const bool planned_enum = q.limit > 0 && !q.exact && pl != c->plans.end() &&
+                                pl->second.runs > 0;
+      if (split && alone) {
+        rc = rt::run_split(c, sl.run.get(), sl.view);
+      } else if (split) {
+        rc = CC_ENOMEM;  // wait until it runs alone
+      } else {
+        rc = rt::run_direct(c, sl.run.get(), sl.view, sl.key, !planned_enum);
+        if (rc == CC_ENOMEM && alone && q.limit == 0) {
+          {
+            std::lock_guard<std::mutex> g2(S->mu);
+            S->sliced++;
+          }
+          rc = rt::run_split(c, sl.run.get(), sl.view);
+        }
+      }
       if (rc == CC_ENOMEM && alone) {
         size_t &r = c->plans[sl.key].refused;
         r = std::max(r, sl.bytes);
       }
       std::vector<u64> counts;
       std::vector<uint8_t> exists;
+      std::vector<int32_t> rows;
+      uint64_t n_rows = 0, n_total = 0;
       if (!rc) rc = read_results(c, sl, counts, exists);
+      if (!rc && q.limit > 0) {
+        const int32_t nF = c->patterns.at(q.pattern).nF;
+        rows.assign((size_t)q.limit * nF, 0);
+        rc = rt::enumerate_run(c, sl.run.get(), q.limit, rows.data(), &n_rows, &n_total, false);
+        rows.resize((size_t)n_rows * nF);
+      }
       if (!rc) {
-        publish(S, q, CC_OK, std::move(counts), std::move(exists));
+        publish(S, q, CC_OK, std::move(counts), std::move(exists), std::move(rows), n_rows);
         published = true;
       }
     }
@@ -365,7 +400,7 @@ int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight) {
   const size_t free_bytes = c->arena.free_bytes();
   S->budget = mem_budget ? std::min(mem_budget, free_bytes) : free_bytes / 2;
   S->reserved = 0;
-  S->submitted = S->completed = S->exact_runs = S->reruns = 0;
+  S->submitted = S->completed = S->exact_runs = S->reruns = S->sliced = 0;
   S->inflight_max = 0;
   S->reserved_max = 0;
   cc_default_opts(&S->opts);
@@ -387,7 +422,7 @@ int cc_serve_start(cc_ctx *ctx, size_t mem_budget, int32_t max_inflight) {
 }
 
 int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t trials, int32_t k,
-                    int64_t *ticket) {
+                    uint64_t limit, int64_t *ticket) {
   Ctx *c = (Ctx *)ctx;
   if (!c || !ticket || trials < 1 || k < 1 || k > 32) return CC_EINVAL;
   Server *S = c->server;
@@ -401,6 +436,7 @@ int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t tria
     q.trials = trials;
     q.k = k;
     q.seed = seed;
+    q.limit = limit;
     q.submitted = cc::Clock::now();
     S->results[q.ticket] = cc::ServeResult{};
     S->queue.push_back(q);
@@ -412,7 +448,8 @@ int cc_serve_submit(cc_ctx *ctx, int32_t pattern_id, uint64_t seed, int32_t tria
 }
 
 int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
-                  uint64_t *h_counts, uint8_t *h_exists, int64_t *latency_ns) {
+                  uint64_t *h_counts, uint8_t *h_exists, int32_t *h_rows, uint64_t *n_rows,
+                  int64_t *latency_ns) {
   Ctx *c = (Ctx *)ctx;
   if (!c || !done) return CC_EINVAL;
   Server *S = c->server;
@@ -429,13 +466,16 @@ int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
     for (size_t t = 0; t < r.counts.size(); ++t) h_counts[t] = r.counts[t];
   if (h_exists)
     for (size_t t = 0; t < r.exists.size(); ++t) h_exists[t] = r.exists[t];
+  if (n_rows) *n_rows = r.n_rows;
+  if (h_rows)
+    for (size_t i = 0; i < r.rows.size(); ++i) h_rows[i] = r.rows[i];
   S->results.erase(it);
   return CC_OK;
 }
 
 int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed,
                    int32_t *inflight_max, uint64_t *reserved_max, uint64_t *exact_runs,
-                   uint64_t *reruns) {
+                   uint64_t *reruns, uint64_t *sliced) {
   Ctx *c = (Ctx *)ctx;
   if (!c) return CC_EINVAL;
   Server *S = c->server;
@@ -447,6 +487,7 @@ int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed,
   if (reserved_max) *reserved_max = S->reserved_max;
   if (exact_runs) *exact_runs = S->exact_runs;
   if (reruns) *reruns = S->reruns;
+  if (sliced) *sliced = S->sliced;
   return CC_OK;
 }
 

@@ -367,6 +367,11 @@ WORKLOADS = {
     # Erdos-Renyi n=100000, average degree 10 (seed 1); 3x3 grid; k=9; 32 trials
     "er100k_grid3x3": dict(graph=("er", 100000, 10.0 / 99999.0, 1), pattern=("grid", 3, 3), k=9,
                            seed=7, trials=32),
+    # erased power-law configuration model n=10^6, mean degree 8, exponent 2.5 (seed 1); a batch
+    # of 64 random partial 3-trees of 10-12 vertices (pattern seeds 7000..7063); k = n_F; 16
+    # trials each
+    "pl1m_ktree3": dict(graph=("pl", 1_000_000, 8.0, 2.5, 1), patterns=64, sizes=(10, 12),
+                        width=3, pattern_seed=7000, trials=16, seed=7),
     # serving: Barabasi-Albert n=200000, m=5 (seed 1) resident; 2000 queries, Poisson arrivals
     # at 200/s (seed 1); families path, cycle, grid, random partial k-tree (k <= 3); n_F = k
     # uniform in 4..10; one trial per query
@@ -398,6 +403,15 @@ def er_phase_instance(ip, iq, spec=ER_PHASE):
     pg = erdos_renyi(spec["n_pattern"], q, base + 500_000 + 1000 * iq + ip)
     edges = edges_from_csr(*pg).astype(np.int32)
     return p, q, g, (spec["n_pattern"], edges, None), base + 7 * (1000 * ip + iq) + 1
+
+
+def ktree_batch(spec):
+    """The pattern batch of a batched workload: `patterns` random partial k-trees (k = width) with
+    n_F uniform in sizes (numpy seed 1), pattern i from seed pattern_seed + i."""
+    rng = np.random.default_rng(1)
+    lo, hi = spec["sizes"]
+    return [random_partial_ktree(int(rng.integers(lo, hi + 1)), spec["width"],
+                                 spec["pattern_seed"] + i) for i in range(spec["patterns"])]
 
 
 def serve_stream(spec, count=None):

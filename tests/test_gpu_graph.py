@@ -228,6 +228,43 @@ def test_trials_stream_when_memory_is_short(ctx):
     assert np.array_equal(want[0][:2], ref.count)
 
 
+def test_single_trial_runs_in_slices_when_memory_is_short(ctx):
+    """In an arena too small for even one trial, a run without kept tables splits each trial by
+    the image of one pattern vertex (allowed-mapping masks, Section 3.2): the counts and exists
+    flags are those of the run in a large arena and of the oracle, table sizes add up to at least
+    the true ones, and a second run reuses the slice count it found."""
+    g = synth.barabasi_albert(3000, 4, 13)
+    pat = synth.cycle_pattern(6)
+    z = oracle.colors(3000, 2, 6, seed=21)
+    cc.cc_load_graph(ctx.h, *g)
+    pid = _load(ctx, pat)
+    cid = cc.cc_set_colors(ctx.h, z, 6)
+    run = cc.cc_run_dp(ctx.h, pid, cid, cc.cc_default_opts())
+    N, _ = cc.cc_pattern_info(ctx.h, pid)
+    want = (cc.cc_count(ctx.h, run, 2), cc.cc_decide(ctx.h, run, 2),
+            cc.cc_table_stats(ctx.h, run, N)[0])
+    cc.cc_release(ctx.h, run)
+    cc.cc_release_colors(ctx.h, cid)
+    small = cc.Context(arena_bytes=256 << 20)
+    try:
+        cc.cc_load_graph(small.h, *g)
+        spid = cc.cc_load_pattern(small.h, *pat)
+        scid = cc.cc_set_colors(small.h, z, 6)
+        used = cc.cc_context_stats(small.h)[1]
+        for _ in range(2):
+            srun = cc.cc_run_dp(small.h, spid, scid, cc.cc_default_opts())
+            assert cc.cc_run_mode(small.h, srun) == "sliced"
+            assert np.array_equal(cc.cc_count(small.h, srun, 2), want[0])
+            assert np.array_equal(cc.cc_decide(small.h, srun, 2), want[1])
+            assert (cc.cc_table_stats(small.h, srun, N)[0] >= want[2]).all()
+            cc.cc_release(small.h, srun)
+        assert cc.cc_context_stats(small.h)[1] == used
+    finally:
+        small.close()
+    ref = oracle.run_dp(g, pat, z[:1], 6)
+    assert int(want[0][0]) == int(ref.count[0]) > 0
+
+
 def test_batch_of_partial_3trees(ctx):
     """The batched-patterns configuration at small scale: an erased power-law configuration
     graph (n=2000, exponent 2.5, mean degree 8) and 16 random partial 3-trees of 10-12 vertices,

@@ -55,7 +55,7 @@ def _wait(ctx, tickets, trials, timeout=120.0):
         for i, t in enumerate(tickets):
             if i in res:
                 continue
-            done, status, counts, exists, lat = cc.cc_serve_poll(ctx.h, t, trials[i])
+            done, status, counts, exists, lat, _ = cc.cc_serve_poll(ctx.h, t, trials[i])
             if done:
                 res[i] = (status, counts, exists, lat)
         assert time.time() - t0 < timeout, "served queries did not finish"
@@ -148,3 +148,65 @@ def test_serving_errors_and_busy(ctx, graph):
         cc.cc_serve_submit(ctx.h, pid, 1, 1, 5)
     want_c, _ = _plain(ctx, pid2, 3, 2, 3)
     assert np.array_equal(res[2][1], want_c)
+
+
+def test_served_enumeration_equals_alone_and_oracle(ctx, graph):
+    """Queries with a limit reconstruct their embeddings (Section 4) inside the server: the rows
+    equal cc_enumerate of the same query run alone with its tables kept, and the oracle's."""
+    cc.cc_load_graph(ctx.h, *graph)
+    pats = [synth.cycle_pattern(4), synth.path_pattern(3), synth.grid_pattern(2, 2)]
+    pids = [cc.cc_load_pattern(ctx.h, *p) for p in pats]
+    qs = [(i % 3, 500 + i, 1 + i % 2, pats[i % 3][0], [0, 50, 10 ** 6][i % 3]) for i in range(9)]
+    cc.cc_serve_start(ctx.h, 0, 4)
+    tickets = [cc.cc_serve_submit(ctx.h, pids[p], s, T, k, lim) for p, s, T, k, lim in qs]
+    got, t0 = {}, time.time()
+    while len(got) < len(qs):
+        for i, (t, (p, s, T, k, lim)) in enumerate(zip(tickets, qs)):
+            if i not in got:
+                r = cc.cc_serve_poll(ctx.h, t, T, lim, pats[p][0])
+                if r[0]:
+                    got[i] = r
+        assert time.time() - t0 < 120
+        time.sleep(0.001)
+    cc.cc_serve_stop(ctx.h)
+    for i, (p, s, T, k, lim) in enumerate(qs):
+        done, status, counts, exists, lat, rows = got[i]
+        assert status == 0
+        cid = cc.cc_color(ctx.h, s, T, k)
+        run = cc.cc_run_dp(ctx.h, pids[p], cid, cc.cc_default_opts(retain=1))
+        assert np.array_equal(counts, cc.cc_count(ctx.h, run, T))
+        if lim:
+            want, _ = cc.cc_enumerate(ctx.h, run, lim, pats[p][0])
+            assert np.array_equal(rows, want) and len(rows) > 0
+            ref = oracle.run_dp(graph, pats[p], oracle.colors(N, T, k, s), k)
+            assert np.array_equal(rows, ref.enumerate(lim)[0])
+        else:
+            assert len(rows) == 0
+        cc.cc_release(ctx.h, run)
+        cc.cc_release_colors(ctx.h, cid)
+
+
+def test_big_query_runs_split_alone_and_in_the_mix(ctx, graph):
+    """A query whose tables exceed the serving budget is not refused: it runs split (one trial
+    in slices by the image of one pattern vertex), alone and among smaller queries, and its
+    counts equal those of the same query run in the whole arena."""
+    g = synth.barabasi_albert(3000, 4, 13)
+    cc.cc_load_graph(ctx.h, *g)
+    big = cc.cc_load_pattern(ctx.h, *synth.cycle_pattern(6))
+    small = cc.cc_load_pattern(ctx.h, *synth.path_pattern(4))
+    want = _plain(ctx, big, 77, 1, 6)
+    want_s = [_plain(ctx, small, 900 + i, 1, 4) for i in range(6)]
+    cc.cc_serve_start(ctx.h, 256 << 20, 4)
+    alone = _wait(ctx, [cc.cc_serve_submit(ctx.h, big, 77, 1, 6)], [1])
+    mix_t = [cc.cc_serve_submit(ctx.h, small, 900 + i, 1, 4) for i in range(3)]
+    mix_t.append(cc.cc_serve_submit(ctx.h, big, 77, 1, 6))
+    mix_t += [cc.cc_serve_submit(ctx.h, small, 903 + i, 1, 4) for i in range(3)]
+    mix = _wait(ctx, mix_t, [1] * 7)
+    stats = cc.cc_serve_stats(ctx.h)
+    cc.cc_serve_stop(ctx.h)
+    assert stats["sliced"] >= 1
+    for status, counts, exists, _ in alone + [mix[3]]:
+        assert status == 0
+        assert np.array_equal(counts, want[0]) and np.array_equal(exists, want[1])
+    for (status, counts, exists, _), w in zip(mix[:3] + mix[4:], want_s):
+        assert status == 0 and np.array_equal(counts, w[0])
