@@ -652,8 +652,8 @@ def er_phase_point(cc, h, pat, k, seed, trials):
     pid = cc.cc_load_pattern(h, nF, edges, td)
     width = cc.cc_pattern_info(h, pid)[1]
     cid = cc.cc_color(h, seed, trials, k)
-    try:
-        run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts())
+    try:  # a point whose tables do not fit is reported, not split into slices
+        run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts(max_slices=1))
     except cc.CCError as ex:
         cc.cc_release_colors(h, cid)
         return ex.code, width, None, None, 0
@@ -666,7 +666,7 @@ def er_phase_point(cc, h, pat, k, seed, trials):
     return 0, width, found, counts, ent
 
 
-def er_phase_leg(cc, torch, step=None, arena_gb=32):
+def er_phase_leg(cc, torch, step=None, arena_gb=8):
     """The Erdos-Renyi phase-transition study (Section 5.4): for every p, q on the grid of the
     study, target G(150, p) against pattern G(10, q), ten colourings (iterations) with k = 10;
     per point the time of the ten iterations, whether a copy was found, the pattern's

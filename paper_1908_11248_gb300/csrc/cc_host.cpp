@@ -859,9 +859,11 @@ int finish_run(Ctx *c, Run *R) {
 
 // ---- reconstruction driver (Section 4): pre-order steps over device state arrays -----------
 int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_out,
-                  uint64_t *n_total, bool sets) {
+                  uint64_t *n_total, bool sets, const cc::Coloring *colouring) {
   const Pattern &P = c->patterns.at(R->pattern);
-  const cc::Coloring &col = c->colorings.at(R->coloring);
+  auto ci = c->colorings.find(R->coloring);
+  if (!colouring && ci == c->colorings.end()) return CC_ENOTFOUND;
+  const cc::Coloring &col = colouring ? *colouring : ci->second;
   const int N = (int)P.nodes.size();
   const int nF = P.nF;
   // node descriptors

@@ -404,6 +404,9 @@ __global__ void __launch_bounds__(BLOCK) intro_kernel(IntroArgs a, u64 *blk_coun
 // A warp reserves a.chunk output slots at a time (a power of two in [32, 256], chosen by the
 // planner from the table's planned size so that the holes left in the warps' last chunks stay a
 // small part of the table).
+// Each lane first builds its entry's output key with the new vertex's field left zero (the
+// vertex inserted at slot p and, when the entries are written projected, the parent forget's
+// slot removed), so that a candidate only ORs in its vertex and its colour bit.
 
 __device__ __forceinline__ u64 shfl_key(u64 v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
@@ -414,134 +417,28 @@ __device__ __forceinline__ u128 shfl_key(u128 v, int src) {
   return ((u128)hi << 64) | (u128)lo;
 }
 
-// I: integer type of candidate positions within a window (int when 32 * n < 2^31).
-template <typename K, int MODE, typename I>
-__global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
-  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
-  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
-  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
-  const u64 chunk = a.chunk;
-  u64 cbase = 0, cfill = chunk;  // warp-uniform chunk state
-  u64 produced = 0, fresh = 0, examined = 0;
-  bool full = false;
-  for (u64 base = wid * 32; base < bound; base += warps * 32) {
-    const u64 i = base + lane;
-    K key = 0;
-    u64 c = 0;
-    if (i < bound) load_slot(in, i, key, c);
-    I nc = 0;
-    int rs = 0;
-    if (key != 0) {
-      if (a.nnb == 0) {
-        nc = (I)a.G.n;
-      } else {
-        const int w = key_slot(key, a.L, a.nb_slot[0]);
-        rs = a.G.row_ptr[w];
-        nc = a.G.row_ptr[w + 1] - rs;
-      }
-    }
-    I incl = nc;
-    for (int o = 1; o < 32; o <<= 1) {
-      const I y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const I excl = incl - nc;
-    const I total = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane == 0) examined += (u64)total;
-    for (I j0 = 0; j0 < total; j0 += 32) {
-      const I j = j0 + lane;
-      bool valid = false;
-      K okey = 0;
-      u64 oc = 0;
-      // owner: smallest lane o with incl[o] > j
-      int lo = 0, hi = 31;
-#pragma unroll
-      for (int step = 0; step < 5; ++step) {
-        const int mid = (lo + hi) >> 1;
-        const I v = __shfl_sync(0xffffffffu, incl, mid);
-        if (v > j) hi = mid;
-        else lo = mid + 1;
-      }
-      const int o = lo;
-      const K ekey = shfl_key(key, o);
-      const u64 ec = __shfl_sync(0xffffffffu, c, o);
-      const int ers = __shfl_sync(0xffffffffu, rs, o);
-      const I eexcl = __shfl_sync(0xffffffffu, excl, o);
-      if (j < total) {
-        const I r = j - eexcl;
-        const int v = a.nnb ? __ldg(a.G.col + ers + r) : (int)r;
-        const int t = key_trial(ekey, a.L);
-        const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
-        valid = !((key_mask(ekey, a.L) >> cv) & 1u);
-        if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
-        if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
-        if (valid) {
-          okey = key_insert(ekey, a.L, a.p, v) | ((K)1 << cv);
-          oc = ec;
-        }
-      }
-      if (MODE == 1) {
-        const unsigned bal = __ballot_sync(0xffffffffu, valid);
-        const u64 tot = __popc(bal);
-        const u64 idx = cfill + __popc(bal & lt);
-        u64 nb = 0;
-        const bool spill = cfill + tot > chunk;
-        if (spill) {
-          if (lane == 0) nb = atomicAdd(a.cursor, chunk);
-          nb = __shfl_sync(0xffffffffu, nb, 0);
-        }
-        if (valid) {
-          const u64 pos = idx < chunk ? cbase + idx : nb + (idx - chunk);
-          ++produced;
-          if (pos < a.out.cap)
-            store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
-          else
-            full = true;
-        }
-        if (spill) {
-          cbase = nb;
-          cfill = cfill + tot - chunk;
-        } else {
-          cfill += tot;
-        }
-      } else if (valid) {
-        ++produced;
-        if (!full) {
-          const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
-          if (r > 0) ++fresh;
-          if (r < 0) full = true;
-        }
-      }
-    }
-  }
-  if (MODE == 1 && cfill < chunk)  // the unused tail of the warp's last chunk: holes
-    for (u64 j = cfill + lane; j < chunk; j += 32)
-      if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
-  if (full) atomicOr(a.err, kErrOverflow);
-  for (int o = 16; o > 0; o >>= 1) {
-    produced += __shfl_down_sync(0xffffffffu, produced, o);
-    fresh += __shfl_down_sync(0xffffffffu, fresh, o);
-  }
-  if (lane == 0) {
-    if (a.valid && produced) atomicAdd(a.valid, produced);
-    if (MODE == 2 && fresh) atomicAdd(a.out.count, fresh);
-    if (a.cand && examined) atomicAdd(a.cand, examined);
-  }
+// The output key of an introduce for a child entry `key` with the new vertex's field zero: the
+// vertex inserted at slot p, then slot q removed when the parent forget's projection is applied
+// (q < 0: none; q == p: the new vertex is forgotten at once, so only its colour enters the key).
+template <typename K>
+__device__ __forceinline__ K intro_base(K key, const KeyLayout &L, int p, int q) {
+  if (q == p) return key;
+  const K b = key_insert(key, L, p, 0);
+  return q >= 0 ? key_remove(b, L, q) : b;
+}
+// bit position of the new vertex in that output key, -1 when it is forgotten at once
+__device__ __forceinline__ int intro_vshift(const KeyLayout &L, int p, int q) {
+  if (q == p) return -1;
+  return L.k + (q >= 0 && q < p ? p - 1 : p) * L.nb;
+}
+// the output key of candidate v with colour cv
+template <typename K>
+__device__ __forceinline__ K intro_out(K base, int vsh, int v, int cv) {
+  return base | (vsh >= 0 ? (K)(unsigned)v << vsh : (K)0) | ((K)1 << cv);
 }
 
-// ---- grouped introduce, warp by warp (planned capacities) -----------------------------------
-// The child is sorted by the images of u's bag neighbours.  Each warp takes a window of 32
-// consecutive entries; the first entry of every run of equal images in the window leads: the
-// warp walks the lead's anchor list 32 candidates at a time, keeps those adjacent to every bag
-// neighbour's image (and passing the degree filter) in a small per-warp buffer, and then every
-// entry of the run tests only its own colour set against that list.  A window whose lists do not
-// fit the buffer is processed entry by entry.
-constexpr int kGroupCap = 128;  // candidate-list buffer per warp
-
+// Appends the warp's valid outputs (already projected) in chunks (MODE 1) or adds them into the
+// hashed output (MODE 2).
 template <typename K, int MODE>
 __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey, u64 oc,
                                           int lane, unsigned lt, u64 &cbase, u64 &cfill,
@@ -562,10 +459,8 @@ __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey
     if (valid) {
       const u64 pos = idx < chunk ? cbase + idx : nb + (idx - chunk);
       ++produced;
-      if (pos < a.out.cap)
-        store_slot(out, pos, a.proj_q >= 0 ? key_remove(okey, a.L, a.proj_q) : okey, oc);
-      else
-        full = true;
+      if (pos < a.out.cap) store_slot(out, pos, okey, oc);
+      else full = true;
     }
     if (spill) {
       cbase = nb;
@@ -576,26 +471,28 @@ __device__ __forceinline__ void warp_emit(const IntroArgs &a, bool valid, K okey
   } else if (valid) {
     ++produced;
     if (!full) {
-      const int r = hash_add(out, a.out.cap, key_remove(okey, a.L, a.q), oc);
+      const int r = hash_add(out, a.out.cap, okey, oc);
       if (r > 0) ++fresh;
       if (r < 0) full = true;
     }
   }
 }
 
-template <typename K, int MODE>
-__global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
-  __shared__ int s_buf[8][kGroupCap];
+// I: integer type of candidate positions within a window (int when 32 * n < 2^31).
+template <typename K, int MODE, typename I>
+__global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  int *buf = s_buf[wib];
   const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
-  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + wib;
+  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
+  const int q = MODE == 2 ? a.q : a.proj_q;
+  const int vsh = intro_vshift(a.L, a.p, q);
+  const u64 n = (u64)a.G.n;
   const u64 chunk = a.chunk;
-  u64 cbase = 0, cfill = chunk;
+  u64 cbase = 0, cfill = chunk;  // warp-uniform chunk state
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
   for (u64 base = wid * 32; base < bound; base += warps * 32) {
@@ -603,11 +500,126 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
     K key = 0;
     u64 c = 0;
     if (i < bound) load_slot(in, i, key, c);
+    I nc = 0;
+    int rs = 0;
+    K ob = 0;          // output key without the new vertex
+    uint32_t cm = 0;   // colour set
+    u64 crow = 0;      // first colour of the entry's trial
+    if (key != 0) {
+      if (a.nnb == 0) {
+        nc = (I)a.G.n;
+      } else {
+        const int w = key_slot(key, a.L, a.nb_slot[0]);
+        rs = a.G.row_ptr[w];
+        nc = a.G.row_ptr[w + 1] - rs;
+      }
+      ob = intro_base(key, a.L, a.p, q);
+      cm = key_mask(key, a.L);
+      crow = (u64)key_trial(key, a.L) * n;
+    }
+    I incl = nc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const I y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const I excl = incl - nc;
+    const I total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) examined += (u64)total;
+    for (I j0 = 0; j0 < total; j0 += 32) {
+      const I j = j0 + lane;
+      // owner: smallest lane o with incl[o] > j
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const I v = __shfl_sync(0xffffffffu, incl, mid);
+        if (v > j) hi = mid;
+        else lo = mid + 1;
+      }
+      const int o = lo;
+      const K eb = shfl_key(ob, o);
+      const u64 ec = __shfl_sync(0xffffffffu, c, o);
+      const int ers = __shfl_sync(0xffffffffu, rs, o);
+      const I eexcl = __shfl_sync(0xffffffffu, excl, o);
+      const uint32_t ecm = __shfl_sync(0xffffffffu, cm, o);
+      const u64 ecrow = __shfl_sync(0xffffffffu, crow, o);
+      bool valid = false;
+      K okey = 0;
+      if (j < total) {
+        const I r = j - eexcl;
+        const int v = a.nnb ? __ldg(a.G.col + ers + r) : (int)r;
+        const int cv = a.G.colors[ecrow + (u64)v];
+        valid = !((ecm >> cv) & 1u);
+        if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+        if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
+        if (valid) okey = intro_out(eb, vsh, v, cv);
+      }
+      warp_emit<K, MODE>(a, valid, okey, ec, lane, lt, cbase, cfill, produced, fresh, full);
+    }
+  }
+  if (MODE == 1 && cfill < chunk)  // the unused tail of the warp's last chunk: holes
+    for (u64 j = cfill + lane; j < chunk; j += 32)
+      if (cbase + j < a.out.cap) store_slot(out, cbase + j, (K)0, 0ull);
+  if (full) atomicOr(a.err, kErrOverflow);
+  for (int o = 16; o > 0; o >>= 1) {
+    produced += __shfl_down_sync(0xffffffffu, produced, o);
+    fresh += __shfl_down_sync(0xffffffffu, fresh, o);
+  }
+  if (lane == 0) {
+    if (a.valid && produced) atomicAdd(a.valid, produced);
+    if (MODE == 2 && fresh) atomicAdd(a.out.count, fresh);
+    if (a.cand && examined) atomicAdd(a.cand, examined);
+  }
+}
+
+// ---- grouped introduce, warp by warp (planned capacities) -----------------------------------
+// The child comes in runs of equal images of u's bag neighbours (sorted or clustered by them).
+// Each warp takes a contiguous range of windows of 32 consecutive entries.  The first entry of
+// every run in a window leads: the warp walks the lead's anchor list 32 candidates at a time,
+// keeps those adjacent to every bag neighbour's image (and passing the degree filter and the
+// allowed mappings) in a per-warp buffer, and every entry of the run then only tests its own
+// colour set against that list.  A window that begins inside the run the previous window ended
+// in takes that run's list as it is: two buffers alternate, the one holding the carried list
+// being left alone while the window's new lists are built in the other.  A window whose new
+// lists do not fit a buffer is processed entry by entry.
+constexpr int kGroupCap = 256;  // candidate-list buffer per warp (two of them)
+
+template <typename K, int MODE>
+__global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
+  __shared__ int s_buf[8][2 * kGroupCap];
+  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
+  Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int *bufs = s_buf[wib];
+  const u64 warps = (u64)gridDim.x * (blockDim.x / 32);
+  const u64 wid = (u64)blockIdx.x * (blockDim.x / 32) + wib;
+  const u64 bound = warp_run_failed(a.err) ? 0 : table_bound<K>(a.in);
+  const u64 nwin = (bound + 31) / 32, per = (nwin + warps - 1) / warps;
+  const u64 w0 = min(nwin, wid * per), w1 = min(nwin, w0 + per);
+  const int q = MODE == 2 ? a.q : a.proj_q;
+  const int vsh = intro_vshift(a.L, a.p, q);
+  const u64 n = (u64)a.G.n;
+  const u64 chunk = a.chunk;
+  u64 cbase = 0, cfill = chunk;
+  u64 produced = 0, fresh = 0, examined = 0;
+  bool full = false;
+  // the run the previous window ended in (warp-uniform): its tuple and its list
+  // bufs[cb * kGroupCap + cs .. + cl) (cl < 0: none)
+  u64 ctup = ~0ull;
+  int cb = 0, cs = 0, cl = -1;
+  for (u64 win = w0; win < w1; ++win) {
+    const u64 i = win * 32 + lane;
+    K key = 0;
+    u64 c = 0;
+    if (i < bound) load_slot(in, i, key, c);
     const u64 tup = key != 0 ? nb_tuple(key, a) : ~0ull;
     const u64 up = __shfl_up_sync(0xffffffffu, tup, 1);
-    const bool lead = key != 0 && (lane == 0 || up != tup);
+    const bool lead = key != 0 && (lane == 0 ? (cl < 0 || tup != ctup) : up != tup);
     const unsigned leads = __ballot_sync(0xffffffffu, lead);
-    // candidate lists of the window's runs, one after the other in buf
+    const int nbuf = cb ^ 1;  // the new lists go where the carried one is not
+    int *nb_base = bufs + nbuf * kGroupCap;
+    // candidate lists of the window's new runs, one after the other in the new buffer
     int lstart = 0, llen = 0;  // held by lead lanes
     int used = 0;              // warp-uniform
     bool overflow = false;
@@ -634,12 +646,12 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
           v = __ldg(a.G.col + rs + j);
           ok = (a.degF == 0 || a.G.deg8[v] >= a.degF) &&
                (!a.G.allow || (a.G.allow[v] & a.ubit));
-          for (int q = 0; q < a.nnb && ok; ++q)
-            if (q != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[q]), v);
+          for (int qq = 0; qq < a.nnb && ok; ++qq)
+            if (qq != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[qq]), v);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         const int pos = used + __popc(bal & lt);
-        if (ok && pos < kGroupCap) buf[pos] = v;
+        if (ok && pos < kGroupCap) nb_base[pos] = v;
         used += __popc(bal);
       }
       if (used > kGroupCap) overflow = true;
@@ -650,27 +662,45 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
     }
     __syncwarp();
     if (!overflow) {
-      // each entry takes the list of the last lead at or before it
+      // each entry takes the list of the last lead at or before it; entries before the first
+      // lead continue the carried run
       const unsigned mine = leads & (lt | (1u << lane));
       const int from = mine ? 31 - __clz(mine) : 0;
       // every lane takes part in both shuffles (a full-mask shuffle in a branch is undefined)
-      const int s0 = __shfl_sync(0xffffffffu, lstart, from);
-      const int n0all = __shfl_sync(0xffffffffu, llen, from);
-      const int n0 = key != 0 ? n0all : 0;
+      int s0 = __shfl_sync(0xffffffffu, lstart, from);
+      int n0 = __shfl_sync(0xffffffffu, llen, from);
+      const int *lst = nb_base;
+      if (!mine) {
+        lst = bufs + cb * kGroupCap;
+        s0 = cs;
+        n0 = cl < 0 ? 0 : cl;
+      }
+      if (key == 0) n0 = 0;
       int nmax = n0;
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-      const int t = key != 0 ? key_trial(key, a.L) : 0;
+      const K ob = key != 0 ? intro_base(key, a.L, a.p, q) : (K)0;
+      const uint32_t cm = key_mask(key, a.L);
+      const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
       for (int r = 0; r < nmax; ++r) {
         bool valid = false;
         K okey = 0;
-        if (r < n0 && s0 + r < kGroupCap) {
-          const int v = buf[s0 + r];
-          const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
-          valid = !((key_mask(key, a.L) >> cv) & 1u);
-          if (valid) okey = key_insert(key, a.L, a.p, v) | ((K)1 << cv);
+        if (r < n0) {
+          const int v = lst[s0 + r];
+          const int cv = a.G.colors[crow + (u64)v];
+          valid = !((cm >> cv) & 1u);
+          if (valid) okey = intro_out(ob, vsh, v, cv);
         }
         warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
       }
+      // carry the run of the window's last entry: a new one, or the carried one continued
+      if (leads) {
+        const int l = 31 - __clz(leads);
+        cb = nbuf;
+        cs = __shfl_sync(0xffffffffu, lstart, l);
+        cl = __shfl_sync(0xffffffffu, llen, l);
+      }
+      ctup = __shfl_sync(0xffffffffu, tup, 31);
+      if (ctup == ~0ull) cl = -1;
     } else {  // entry by entry, every check in full
       int best = INT_MAX, rs = 0, anc = 0;
       if (key != 0)
@@ -686,24 +716,27 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       const int nc = key != 0 ? best : 0;
       int nmax = nc;
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-      const int t = key != 0 ? key_trial(key, a.L) : 0;
+      const K ob = key != 0 ? intro_base(key, a.L, a.p, q) : (K)0;
+      const uint32_t cm = key_mask(key, a.L);
+      const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
       for (int j = 0; j < nmax; ++j) {
         bool valid = false;
         K okey = 0;
         if (j < nc) {
           const int v = __ldg(a.G.col + rs + j);
-          const int cv = a.G.colors[(u64)t * (u64)a.G.n + (u64)v];
-          valid = !((key_mask(key, a.L) >> cv) & 1u);
+          const int cv = a.G.colors[crow + (u64)v];
+          valid = !((cm >> cv) & 1u);
           if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
           if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
-          for (int q = 0; q < a.nnb && valid; ++q)
-            if (q != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[q]), v);
-          if (valid) okey = key_insert(key, a.L, a.p, v) | ((K)1 << cv);
+          for (int qq = 0; qq < a.nnb && valid; ++qq)
+            if (qq != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[qq]), v);
+          if (valid) okey = intro_out(ob, vsh, v, cv);
         }
         warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
       }
+      cl = -1;  // no list to carry
     }
-    __syncwarp();  // buf is rewritten by the next window
+    __syncwarp();  // the buffers are rewritten by the next window
   }
   if (MODE == 1 && cfill < chunk)
     for (u64 j = cfill + lane; j < chunk; j += 32)

@@ -304,8 +304,9 @@ int nice_from_td(Pattern &P, const std::vector<std::vector<int>> &bags,
 // The `limit` lexicographically smallest distinct embeddings over a retained run's trials
 // (Section 4), into h_out[n_out][n_F]; *n_total the number of distinct ones.  With `sets`, each
 // embedding is replaced by its vertex set in increasing order before the distinct ones are kept.
+// `colouring`: the run's colouring when it is not one of the context's (a served query's own).
 int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_out,
-                  uint64_t *n_total, bool sets);
+                  uint64_t *n_total, bool sets, const Coloring *colouring = nullptr);
 // Runs (pattern, colouring) requests with one set of options (cc_run_batch without ids).
 int make_runs(Ctx *c, int32_t npat, const int32_t *pids, const int32_t *cids,
               const cc_run_opts *opts, std::vector<std::unique_ptr<Run>> &out);

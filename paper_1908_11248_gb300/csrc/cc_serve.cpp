@@ -20,6 +20,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <stdexcept>
 #include <thread>
 #include <vector>
 
@@ -191,6 +192,9 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
   c->active = &sl.sub;
   sl.q = q;
   int rc = CC_OK;
+  Outcome out = kDone;
+  bool published = false;
+  try {  // a host allocation failure ends this query only, with CC_ENOMEM
   uint8_t *colours = (uint8_t *)sl.sub.alloc(std::max<size_t>(1, (size_t)q.trials * c->n));
   if (!colours) rc = CC_ENOMEM;
   else if (launch_color(sl.stream, c->dev, colours, c->n, q.trials, q.k, q.seed) != 0) rc = CC_ECUDA;
@@ -202,8 +206,6 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
   cc_run_opts qo = S->opts;
   qo.retain = q.limit > 0 ? 1 : 0;  // a reconstruction needs every node's table
   if (!rc) rc = rt::init_run(c, q.pattern, sl.view, -1, &qo, sl.run, sl.key);
-  Outcome out = kDone;
-  bool published = false;
   if (!rc) {
     bool exact = true;
     auto pl = c->plans.find(sl.key);
@@ -263,7 +265,8 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
       if (!rc && q.limit > 0) {
         const int32_t nF = c->patterns.at(q.pattern).nF;
         rows.assign((size_t)q.limit * nF, 0);
-        rc = rt::enumerate_run(c, sl.run.get(), q.limit, rows.data(), &n_rows, &n_total, false);
+        rc = rt::enumerate_run(c, sl.run.get(), q.limit, rows.data(), &n_rows, &n_total, false,
+                               &sl.view);
         rows.resize((size_t)n_rows * nF);
       }
       if (!rc) {
@@ -271,6 +274,12 @@ Outcome issue(Server *S, Ctx *c, ServeSlot &sl, const ServeQuery &q, bool alone)
         published = true;
       }
     }
+  }
+  } catch (const std::exception &) {
+    cudaStreamSynchronize(sl.stream);
+    out = kDone;
+    rc = CC_ENOMEM;
+    if (published) rc = CC_OK;
   }
   c->stream = origin;
   c->active = nullptr;
