@@ -165,7 +165,7 @@ def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
         if kind != "intro_count":  # the introduce's own table, written once
             b += int(sizes[node]) * S(node)
         return b
-    if kind in ("forget", "sort", "reduce"):
+    if kind in ("forget", "sort", "reduce", "merge"):
         if ty != 2:
             return 0
         # the sort's share of the forget is its whole read of the child's entries; the
@@ -188,8 +188,8 @@ def algorithmic_bytes(kind, node, nodes, sizes, cand, n, T, k):
 # kernel kinds grouped by the node rule they implement (Section 3.1)
 GROUPS = {"color": "colour", "leaf": "leaf", "intro_count": "introduce",
           "intro_write": "introduce", "intro_fused": "introduce+forget", "forget": "forget",
-          "sort": "forget", "reduce": "forget", "join_build": "join", "join_count": "join",
-          "join_write": "join", "root": "root"}
+          "sort": "forget", "reduce": "forget", "merge": "forget", "join_build": "join",
+          "join_count": "join", "join_write": "join", "root": "root"}
 
 
 def describe(name):

@@ -159,17 +159,23 @@ typedef struct {
   int32_t sort_sweep;    /* 1: radix sorts take all digit counts in one read and one kernel   */
                          /*    per pass (decoupled look-back); 2: as 1, each block bringing its */
                          /*    next tile into shared memory by bulk copy while it works on the  */
-                         /*    current one; 0: histogram+scan+scatter passes                    */
+                         /*    current one; 0: histogram+scan+scatter passes; 3: a forget after */
+                         /*    an introduce merges by buckets (a hash of the next introduce's   */
+                         /*    bag-neighbour images split the records, each bucket is sorted    */
+                         /*    and merged in shared memory), other sorts as 1                    */
   int32_t distance_prune; /* 1: an introduced vertex with no bag neighbour takes only the host */
                          /*    vertices within distance dist_F(w, u) of phi(w), w the bag vertex */
                          /*    nearest to it in F (Section 3.2, mapping expansion); root results */
                          /*    are unchanged, tables shrink                                      */
   int32_t max_slices;    /* most slices a single trial that does not fit may be split into     */
                          /*    (CC_MODE_SLICED); 0 = 4096                                        */
+  int32_t part_bits;     /* sort_sweep 3: log2 of the bucket count (1..20); 0 = from the size  */
+                         /*    of the table, about 1024 records a bucket                         */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
- * 0.5, block 256, profile 0, group 1, sort_sweep 1, distance_prune 0, max_slices 0). */
+ * 0.5, block 256, profile 0, group 1, sort_sweep 1, distance_prune 0, max_slices 0,
+ * part_bits 0). */
 void cc_default_opts(cc_run_opts *opts);
 
 /* Runs the DP of pattern `pattern_id` for every trial of colouring `coloring_id` (all trials in
@@ -307,6 +313,7 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 #define CC_K_ROOT 9
 #define CC_K_SORT 10   /* all passes of one radix sort of a table's records */
 #define CC_K_REDUCE 11 /* reduce-by-key of sorted records (a forget's merge) */
+#define CC_K_MERGE 12  /* a forget's whole bucketed merge (sort_sweep 3): split, sort, merge */
 
 /* Per-launch device times of a run made with profile = 1, in launch order: node id, kernel
  * kind (CC_K_*), milliseconds between CUDA events recorded on the context's stream just before

@@ -37,7 +37,7 @@ EXPORTS = [
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed", "sliced"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
-                "join_build", "join_count", "join_write", "root", "sort", "reduce"]
+                "join_build", "join_count", "join_write", "root", "sort", "reduce", "merge"]
 
 
 class CCError(RuntimeError):
@@ -57,7 +57,7 @@ class cc_run_opts(ctypes.Structure):
                 ("load_factor", ctypes.c_float), ("block", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("group", ctypes.c_int32),
                 ("sort_sweep", ctypes.c_int32), ("distance_prune", ctypes.c_int32),
-                ("max_slices", ctypes.c_int32)]
+                ("max_slices", ctypes.c_int32), ("part_bits", ctypes.c_int32)]
 
 
 _lib = None

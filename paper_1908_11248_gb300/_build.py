@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcc.so")
 SOURCES = ["cc_kernels.cu", "cc_sort.cu", "cc_enum.cu", "cc_host.cpp", "cc_serve.cpp",
-           "cc_tune.cpp", "cc_solve.cpp", "cc_noalloc.cu"]
+           "cc_tune.cpp", "cc_solve.cpp", "cc_noalloc.cu", "cc_part.cu"]
 HEADERS = ["cc_internal.h", "cc_device.cuh", "cc_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

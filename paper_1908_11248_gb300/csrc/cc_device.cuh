@@ -314,8 +314,24 @@ static __device__ __forceinline__ bool adjacent(const GraphDev &G, int a, int v)
 }
 
 
-// The value records are sorted by (SortSpec): the G-vertices of slots order[0..) first, then,
-// for a full order, the trial and the colour set.
+// Bucket of a key in a bucketed order: the top sp.hbits bits of a hash of the images of the
+// first sp.hslots slots of sp.order (of the whole key when hslots is 0).
+template <typename K>
+__device__ __forceinline__ uint32_t sort_bucket(K key, const SortSpec &sp) {
+  u64 h;
+  if (sp.hslots > 0) {
+    h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int j = 0; j < kMaxBag; ++j)
+      if (j < sp.hslots) h = fmix64(h + (u64)(unsigned)key_slot(key, sp.L, sp.order[j]));
+  } else {
+    h = key_hash(key);
+  }
+  return (uint32_t)(h >> (64 - sp.hbits));
+}
+
+// The value records are sorted by (SortSpec): in a bucketed order the bucket first, then the
+// G-vertices of slots order[0..), then, for a full order, the trial and the colour set.
 template <typename SK, typename K>
 __device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
   SK s = 0;
@@ -327,6 +343,7 @@ __device__ __forceinline__ SK sort_key(K key, const SortSpec &sp) {
     if (sp.L.tb) s = (s << sp.L.tb) | (SK)(unsigned)key_trial(key, sp.L);
     s = (s << sp.L.k) | (SK)key_mask(key, sp.L);
   }
+  if (sp.hbits) s |= (SK)sort_bucket(key, sp) << sp.bits;
   return s;
 }
 

@@ -81,8 +81,9 @@ __device__ bool member(const EnumArgs &a, int y, K key) {
     }
     if (nd.hashed) return hash_find(s, nd.cap, key) >= 0;
     if (nd.sorted)
-      return nd.spec.bits <= 64 ? sorted_contains<u64>(s, nd.count, nd.spec, key)
-                                : sorted_contains<u128>(s, nd.count, nd.spec, key);
+      return nd.spec.bits + nd.spec.hbits <= 64
+                 ? sorted_contains<u64>(s, nd.count, nd.spec, key)
+                 : sorted_contains<u128>(s, nd.count, nd.spec, key);
     return false;
   }
   return false;

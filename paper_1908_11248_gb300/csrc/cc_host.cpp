@@ -483,7 +483,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   };
   // true if table t is sorted with exactly the slots sl[0..n) (in any order) most significant
   auto sorted_by = [&](const cc::NodeTable &t, int m, const int *sl) {
-    if (t.hashed || t.sort_n < m) return false;
+    if (t.hashed || t.sort_n < m || m < t.sort_min) return false;
     for (int j = 0; j < m; ++j) {
       bool in = false;
       for (int i = 0; i < m; ++i) in = in || t.sort_slots[i] == sl[j];
@@ -496,7 +496,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
   // do not depend on the runs being whole)
   auto grouped_by = [&](const cc::NodeTable &t, int m, const int *sl) {
     if (sorted_by(t, m, sl)) return true;
-    if (t.hashed || t.cluster_n < m) return false;
+    if (t.hashed || t.cluster_n < m || m < t.cluster_min) return false;
     for (int j = 0; j < m; ++j) {
       bool in = false;
       for (int i = 0; i < m; ++i) in = in || t.cluster_slots[i] == sl[j];
@@ -710,6 +710,75 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         if (f == N - 1) break;
         continue;
       }
+      if (fuse == 2 && R->opts.sort_sweep == 3) {
+        // write projected entries densely, then the bucketed merge: split by a hash of the next
+        // introduce's bag-neighbour images, sort and merge each bucket in shared memory
+        void *buf = A.alloc(raw * rb);
+        if (!buf) return CC_ENOMEM;
+        rc = write_dense(buf, raw, pos_in(nd.bag, P.nodes[f].vertex));
+        if (!rc) release_child(y);
+        cc::SortSpec sp = forget_order(f);
+        const u64 records = planned ? room(plan->entries[x]) : std::max<u64>(1, total);
+        sp.hbits = R->opts.part_bits > 0 ? std::min(20, R->opts.part_bits)
+                                         : cc::part_bucket_bits(records, R->kw);
+        sp.hslots = sp.nsl;  // 0: the whole key
+        const u64 F = 1ull << sp.hbits;
+        const u64 *bound = planned ? cursor + x : R->d_counters + x;
+        void *mid = A.alloc(raw * rb);
+        void *spare = sp.hbits > 10 ? A.alloc(raw * rb) : nullptr;
+        void *out = A.alloc(raw * rb);
+        cc::PartScratch ps{};
+        ps.hist = arena_alloc<unsigned>(c, F);
+        ps.base = arena_alloc<u64>(c, F + 1);
+        ps.cur1 = arena_alloc<u64>(c, 1024);
+        ps.cur2 = arena_alloc<u64>(c, F);
+        ps.status = arena_alloc<u64>(c, F);
+        ps.claim = arena_alloc<unsigned>(c, 1);
+        ps.scan = arena_alloc<u64>(c, cc::scan_scratch_words(c->dev) + 8);
+        ps.err = R->d_err;
+        auto give_back = [&]() {
+          A.release(buf);
+          A.release(mid);
+          A.release(spare);
+          A.release(ps.hist);
+          A.release(ps.base);
+          A.release(ps.cur1);
+          A.release(ps.cur2);
+          A.release(ps.status);
+          A.release(ps.claim);
+          A.release(ps.scan);
+        };
+        if (!mid || (sp.hbits > 10 && !spare) || !out || !ps.hist || !ps.base || !ps.cur1 ||
+            !ps.cur2 || !ps.status || !ps.claim || !ps.scan) {
+          give_back();
+          A.release(out);
+          return CC_ENOMEM;
+        }
+        if (!rc)
+          rc = timed(f, CC_K_MERGE, 7 + (sp.hbits > 10 ? 1 : 0), [&] {
+            return cc::launch_part_merge(c->stream, c->dev, R->kw, sp, buf, bound, raw, mid,
+                                         spare, raw, ps, out, raw, R->d_counters + f);
+          });
+        give_back();
+        if (rc) {
+          A.release(out);
+          return rc;
+        }
+        if (planned) check(R->d_counters + f, raw);
+        R->tables[f] = {out, raw, 0, true};
+        R->tables[f].sort_n = sp.b;
+        R->tables[f].sort_min = sp.nsl ? sp.nsl : sp.b + 1;
+        R->tables[f].sort_hbits = sp.hbits;
+        R->tables[f].sort_hslots = sp.hslots;
+        for (int j = 0; j < sp.b; ++j) R->tables[f].sort_slots[j] = sp.order[j];
+        made[f] = true;
+        if (!planned) {
+          rc = read_u64(c, R->d_counters + f, &R->sizes[f]);
+          if (rc) return rc;
+        }
+        if (f == N - 1) break;
+        continue;
+      }
       if (fuse == 2) {  // write projected entries densely, sort them, reduce equal keys
         void *buf = A.alloc(raw * rb);
         if (!buf) return CC_ENOMEM;
@@ -747,11 +816,12 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       // the entries of a child sorted or clustered by some slots come out in runs of equal
       // images of those slots: the ungrouped kernels emit each child entry's extensions
       // together, in child order
-      int cl_n = 0, cl[cc::kMaxBag];
+      int cl_n = 0, cl_min = 0, cl[cc::kMaxBag];
       if (!grouped) {
         const cc::NodeTable &ty = R->tables[y];
         const int *src = ty.sort_n ? ty.sort_slots : ty.cluster_slots;
         cl_n = ty.sort_n ? ty.sort_n : ty.cluster_n;
+        cl_min = ty.sort_n ? ty.sort_min : ty.cluster_min;
         for (int j = 0; j < cl_n; ++j) cl[j] = src[j] + (src[j] >= a.p ? 1 : 0);
       }
       void *p = A.alloc(raw * rb);
@@ -760,6 +830,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       if (rc) return rc;
       R->tables[x] = {p, raw, 0, true};
       R->tables[x].cluster_n = cl_n;
+      R->tables[x].cluster_min = cl_min;
       for (int j = 0; j < cl_n; ++j) R->tables[x].cluster_slots[j] = cl[j];
       if (planned) R->tables[x].bound = cursor + x;  // holes: scan up to the cursor
       release_child(y);
@@ -914,6 +985,8 @@ int enumerate_run(Ctx *c, Run *R, uint64_t limit, int32_t *h_out, uint64_t *n_ou
       for (int s = 0; s < e.b; ++s) e.spec.order[s] = t.sort_slots[s];
       e.spec.full = 1;
       e.spec.bits = e.b * R->L.nb + R->L.tb + R->L.k;
+      e.spec.hbits = t.sort_hbits;
+      e.spec.hslots = t.sort_hslots;
     }
     if (nd.type != 0 && nd.type != 1 && !e.hashed && !e.sorted) return CC_EINVAL;
   }
@@ -1212,7 +1285,7 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
 std::vector<long long> plan_key(const Ctx *c, int32_t pid, int32_t trials, int32_t k,
                                 const cc_run_opts &o) {
   return {pid, c->graph_fp, trials, k, o.degree_filter, o.fuse, o.group, o.block,
-          (long long)(o.load_factor * 1000), o.sort_sweep, o.distance_prune};
+          (long long)(o.load_factor * 1000), o.sort_sweep, o.distance_prune, o.part_bits};
 }
 
 // init_run for colouring id cid of the context, which the run then holds a reference to.
@@ -1779,6 +1852,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->sort_sweep = 1;
   o->distance_prune = 0;
   o->max_slices = 0;
+  o->part_bits = 0;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
@@ -1796,7 +1870,7 @@ int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t aren
     return CC_ECUDA;
   }
   c->dev.blocks_per_sm = 8;
-  if (cc::prepare_sort_kernels() != 0) {
+  if (cc::prepare_sort_kernels() != 0 || cc::prepare_part_kernels() != 0) {
     delete c;
     return CC_ECUDA;
   }

@@ -137,6 +137,11 @@ struct SortSpec {
   int order[kMaxBag];
   int full;
   int bits;
+  // bucketed order (hbits > 0): the top hbits of a hash of the first hslots slots of `order`
+  // (of the whole key when hslots == 0) come before everything else, so equal keys and equal
+  // images of those slots stay together while buckets spread evenly
+  int hbits;
+  int hslots;
 };
 // Stable LSD radix sort of the nonempty records of `src` (n_src slots, n of them nonempty) into
 // buf_a / buf_b (n records each); *which (0 or 1) names the buffer holding the result.  hist
@@ -164,6 +169,30 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
                         unsigned long long src_cap, const unsigned long long *n,
                         unsigned long long buf_cap, void *buf_a, void *buf_b,
                         unsigned long long *hist, int *which, const SweepScratch *sw);
+// Bucketed merge of a forget's records (cc_part.cu): the nonempty records of src (scan bound
+// *n_src, at most src_cap slots) merged by key into dst (room for dst_cap records, *dst_count
+// receives the merged count), sorted by (bucket, full key order) for a spec with sp.full = 1 and
+// sp.hbits = part_bucket_bits(records) (at most 20).  mid, and spare when sp.hbits > 10, are
+// record spaces of space_cap >= records slots; src must hold at least that many slots too (it is
+// reused as scratch).  The scratch words:
+struct PartScratch {
+  unsigned *hist;     // 2^hbits bucket sizes
+  unsigned long long *base;    // 2^hbits + 1 bucket starts (the last: the record count)
+  unsigned long long *cur1;    // 2^(first split's bits) cursors
+  unsigned long long *cur2;    // 2^hbits cursors
+  unsigned long long *status;  // 2^hbits look-back words
+  unsigned *claim;    // bucket counter
+  unsigned long long *scan;    // scan_scratch_words(d) words
+  int *err;           // the run's error word (a look-back wait that gave up sets kErrTimeout)
+};
+int part_bucket_bits(unsigned long long records, int kw);
+// lets the split and bucket-sort kernels use more than 48 KB of shared memory (once per device)
+int prepare_part_kernels();
+int launch_part_merge(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &sp,
+                      const void *src, const unsigned long long *n_src,
+                      unsigned long long src_cap, void *mid, void *spare,
+                      unsigned long long space_cap, const PartScratch &ps, void *dst,
+                      unsigned long long dst_cap, unsigned long long *dst_count);
 // One record per run of equal keys of the sorted `src` (min(*n, n_cap) records) with the summed
 // count, written densely to dst (room for n_cap records); *count receives the number of runs.
 // blk needs 2 * sort_grid(d) + 1 words.  With from_s non-null the records carry full sort keys of

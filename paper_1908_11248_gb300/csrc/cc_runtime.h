@@ -148,10 +148,13 @@ struct NodeTable {
   // a dense table sorted with these bag slots most significant (sort_n == 0: no known order)
   int sort_n = 0;
   int sort_slots[kMaxBag] = {};
+  // a bucketed order (sort_hbits > 0, see SortSpec): runs of equal images of the first m order
+  // slots are contiguous only for m >= sort_min
+  int sort_min = 0, sort_hbits = 0, sort_hslots = 0;
   // a dense table whose entries come in runs of equal images of these slots, except where an
   // append chunk or a kernel's tile ends (written in the order of a child sorted or clustered
   // by them); cluster_n == 0: no known clustering
-  int cluster_n = 0;
+  int cluster_n = 0, cluster_min = 0;
   int cluster_slots[kMaxBag] = {};
   // scan bound of a dense table written in chunks (holes up to it); null: the entry counter
   unsigned long long *bound = nullptr;

@@ -122,12 +122,12 @@ def test_min_width_decomposition(ctx):
         assert cc.cc_pattern_info(ctx.h, pid)[1] == tw
 
 
-def _check_small(ctx, g, pat, colours, k, df, fuse, block=256, tables=True):
+def _check_small(ctx, g, pat, colours, k, df, fuse, block=256, tables=True, **opt):
     nF, e, td = pat
     T = colours.shape[0]
     ref = oracle.run_dp(g, pat, colours, k, degree_filter=df)
     r = gpu_dp(ctx, g, pat, colours=colours, k=k, degree_filter=int(df), fuse=int(fuse),
-               retain=1, block=block)
+               retain=1, block=block, **opt)
     try:
         assert r["nodes"] == oracle.nice_td(nF, e, td)
         assert np.array_equal(r["count"], ref.count)
@@ -399,7 +399,52 @@ def test_planned_overflow_falls_back(ctx):
             release(ctx, r)
 
 
-@pytest.mark.parametrize("sweep", [0, 1, 2])
+@pytest.mark.parametrize("name", ["C4", "C5", "G23", "K4", "A", "B", "T3", "T2", "P4"])
+@pytest.mark.parametrize("bits", [0, 1])
+def test_bucketed_merge_small_parity(ctx, name, bits):
+    """The bucketed forget merge (sort_sweep 3) gives the oracle's tables entry by entry, its
+    counts and its enumeration (binary search in the bucketed order), both with buckets sized
+    to shared memory (bits 0) and with two buckets far larger than shared memory, which are
+    sorted in global scratch (bits 1)."""
+    pat = PATTERNS[name]
+    nF = pat[0]
+    g = synth.erdos_renyi(60, 0.15, 5)
+    colours = oracle.colors(60, 3, nF, seed=11 + nF)
+    _check_small(ctx, g, pat, colours, nF, True, 2, sort_sweep=3, part_bits=bits)
+    r = gpu_dp(ctx, g, pat, colours=colours, k=nF, fuse=2, retain=1, sort_sweep=3,
+               part_bits=bits)
+    ref = oracle.run_dp(g, pat, colours, nF)
+    try:
+        got, tot = cc.cc_enumerate(ctx.h, r["run"], 10 ** 6, nF)
+        want, wtot, _ = ref.enumerate(10 ** 6)
+        assert np.array_equal(got, want) and tot == wtot
+    finally:
+        release(ctx, r)
+
+
+def test_bucketed_merge_at_scale(ctx):
+    """The bucketed merge on the 64-trial Barabasi-Albert 2x4-grid step shape at reduced size
+    (n=20000, 4 trials): two-level splits, exact then planned, equal to the one-sweep sort's
+    tables and counts and to the oracle on two trials; and with two bucket bits, every bucket
+    far beyond shared memory."""
+    w = synth.WORKLOADS["ba20k_grid2x4"]
+    g = synth.make_graph(w["graph"])
+    pat = synth.make_pattern(w["pattern"])
+    z = oracle.colors(20000, 4, 8, seed=7)
+    base = gpu_dp(ctx, g, pat, colours=z, k=8)
+    want = (base["count"].copy(), base["sizes"].copy())
+    release(ctx, base)
+    pid = cc.cc_load_pattern(ctx.h, *pat)
+    for bits in (0, 0, 2):
+        r = gpu_dp(ctx, g, pat, colours=z, k=8, pid=pid, sort_sweep=3, part_bits=bits)
+        assert np.array_equal(r["count"], want[0])
+        assert np.array_equal(r["sizes"], want[1])
+        release(ctx, r)
+    ref = oracle.run_dp(g, pat, z[:2], 8)
+    assert np.array_equal(want[0][:2], ref.count)
+
+
+@pytest.mark.parametrize("sweep", [0, 1, 2, 3])
 def test_sort_variants_agree(ctx, sweep):
     """Every radix-sort schedule (separate histogram passes; one-sweep with look-back; one-sweep
     with the next tile brought in by bulk copy) gives the oracle's tables, with 64- and 128-bit
