@@ -635,6 +635,28 @@ def batching_leg(cc, torch, name="ba20k_grid2x4"):
             res[label]["_counts"] = out[0]
             if label == "graph_batched":
                 res[label]["run_mode"] = out[2]
+        # idle time of a graph replay: one all-trials request replayed from its captured graph
+        # (CUDA events around the replay) against the summed device time of the same kernels
+        # (a profiled run: events around every launch)
+        stream = torch.cuda.current_stream()
+        prof = cc.cc_run_dp(h, pid, cid_all, cc.cc_default_opts(profile=1))
+        ksum = float(cc.cc_run_timings(h, prof)[2].sum())
+        cc.cc_release(h, prof)
+        go = cc.cc_default_opts(use_graph=1)
+        reps, gms, mode = 5, [], None
+        for i in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            r = cc.cc_run_dp(h, pid, cid_all, go)
+            e1.record(stream)
+            e1.synchronize()
+            mode = cc.cc_run_mode(h, r)
+            cc.cc_release(h, r)
+            if i >= 2:
+                gms.append(e0.elapsed_time(e1))
+        res["graph_replay"] = {"run_mode": mode, "replay_ms": min(gms), "kernel_ms": ksum,
+                               "idle_fraction": max(0.0, 1.0 - ksum / min(gms))}
     ref = res["plain"].pop("_counts")
     res["identical"] = all(res[x].pop("_counts") == ref for x in ("batched", "graph_batched"))
     res["note"] = ("entries/s = table entries of all trials / host wall time of the calls (counts "

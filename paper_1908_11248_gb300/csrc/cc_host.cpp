@@ -721,7 +721,10 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         const u64 records = planned ? room(plan->entries[x]) : std::max<u64>(1, total);
         sp.hbits = R->opts.part_bits > 0 ? std::min(20, R->opts.part_bits)
                                          : cc::part_bucket_bits(records, R->kw);
-        sp.hslots = sp.nsl;  // 0: the whole key
+        // buckets by the images of all bag slots: equal images stay in one run (so do those of
+        // any prefix of the order that holds them all) while the records sharing them are few
+        // (colour sets times trials); a one-slot bag hashes the whole key
+        sp.hslots = sp.b >= 2 ? sp.b : 0;
         const u64 F = 1ull << sp.hbits;
         const u64 *bound = planned ? cursor + x : R->d_counters + x;
         void *mid = A.alloc(raw * rb);
@@ -767,7 +770,7 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         if (planned) check(R->d_counters + f, raw);
         R->tables[f] = {out, raw, 0, true};
         R->tables[f].sort_n = sp.b;
-        R->tables[f].sort_min = sp.nsl ? sp.nsl : sp.b + 1;
+        R->tables[f].sort_min = sp.hslots ? sp.hslots : sp.b + 1;
         R->tables[f].sort_hbits = sp.hbits;
         R->tables[f].sort_hslots = sp.hslots;
         for (int j = 0; j < sp.b; ++j) R->tables[f].sort_slots[j] = sp.order[j];
@@ -796,9 +799,11 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
           A.release(srt);
           return CC_ENOMEM;
         }
+        const bool narrow = cc::sort_narrows(R->kw, sp, R->opts.sort_sweep);
         rc = timed(f, CC_K_REDUCE, 3, [&] {
           return cc::launch_reduce(c->stream, c->dev, R->kw, srt, R->d_counters + x, raw, blk, out,
-                                   R->d_counters + f, R->opts.sort_sweep ? &sp : nullptr);
+                                   R->d_counters + f, R->opts.sort_sweep ? &sp : nullptr,
+                                   narrow);
         });
         A.release(srt);
         if (rc) return rc;

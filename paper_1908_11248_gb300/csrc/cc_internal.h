@@ -199,7 +199,12 @@ int launch_part_merge(cudaStream_t s, const DevInfo &d, int kw, const SortSpec &
 // that order (a one-sweep sort leaves them so) and are written back as packed keys.
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
                   const unsigned long long *n, unsigned long long n_cap, unsigned long long *blk,
-                  void *dst, unsigned long long *count, const SortSpec *from_s);
+                  void *dst, unsigned long long *count, const SortSpec *from_s,
+                  bool narrow = false);
+// True when a one-sweep sort (sort_sweep 1) of 128-bit-key records by a full order of at most
+// 64 bits moves 16-byte (sort key, count) records from its first pass on: the reduce that
+// follows must then be given narrow = true.
+bool sort_narrows(int kw, const SortSpec &sp, int sort_sweep);
 // Introduce of a vertex with at most one bag neighbour, warp by warp, for planned runs: mode 1
 // appends in per-warp chunks from a.cursor (holes left where chunks are not filled), mode 2
 // adds into the parent forget's hash table.

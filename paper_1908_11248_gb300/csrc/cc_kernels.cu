@@ -495,11 +495,19 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
   u64 cbase = 0, cfill = chunk;  // warp-uniform chunk state
   u64 produced = 0, fresh = 0, examined = 0;
   bool full = false;
+  // the next window's records are loaded while the current one is expanded
+  K nkey = 0;
+  u64 nc_ = 0;
+  if (wid * 32 + lane < bound) load_slot(in, wid * 32 + lane, nkey, nc_);
   for (u64 base = wid * 32; base < bound; base += warps * 32) {
-    const u64 i = base + lane;
-    K key = 0;
-    u64 c = 0;
-    if (i < bound) load_slot(in, i, key, c);
+    const K key = nkey;
+    const u64 c = nc_;
+    {
+      const u64 i2 = base + warps * 32 + lane;
+      nkey = 0;
+      nc_ = 0;
+      if (i2 < bound) load_slot(in, i2, nkey, nc_);
+    }
     I nc = 0;
     int rs = 0;
     K ob = 0;          // output key without the new vertex
@@ -608,11 +616,19 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   // bufs[cb * kGroupCap + cs .. + cl) (cl < 0: none)
   u64 ctup = ~0ull;
   int cb = 0, cs = 0, cl = -1;
+  // the next window's records are loaded while the current one is processed
+  K nkey = 0;
+  u64 nc_ = 0;
+  if (w0 < w1 && w0 * 32 + lane < bound) load_slot(in, w0 * 32 + lane, nkey, nc_);
   for (u64 win = w0; win < w1; ++win) {
-    const u64 i = win * 32 + lane;
-    K key = 0;
-    u64 c = 0;
-    if (i < bound) load_slot(in, i, key, c);
+    const K key = nkey;
+    const u64 c = nc_;
+    {
+      const u64 i2 = (win + 1) * 32 + lane;
+      nkey = 0;
+      nc_ = 0;
+      if (win + 1 < w1 && i2 < bound) load_slot(in, i2, nkey, nc_);
+    }
     const u64 tup = key != 0 ? nb_tuple(key, a) : ~0ull;
     const u64 up = __shfl_up_sync(0xffffffffu, tup, 1);
     const bool lead = key != 0 && (lane == 0 ? (cl < 0 || tup != ctup) : up != tup);
@@ -678,7 +694,6 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       if (key == 0) n0 = 0;
       int nmax = n0;
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-      const K ob = key != 0 ? intro_base(key, a.L, a.p, q) : (K)0;
       const uint32_t cm = key_mask(key, a.L);
       const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
       for (int r = 0; r < nmax; ++r) {
@@ -688,7 +703,9 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
           const int v = lst[s0 + r];
           const int cv = a.G.colors[crow + (u64)v];
           valid = !((cm >> cv) & 1u);
-          if (valid) okey = intro_out(ob, vsh, v, cv);
+          // most candidates of a closing step clash in colour: the output key is built only
+          // for the valid ones
+          if (valid) okey = intro_out(intro_base(key, a.L, a.p, q), vsh, v, cv);
         }
         warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
       }
@@ -716,7 +733,6 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       const int nc = key != 0 ? best : 0;
       int nmax = nc;
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-      const K ob = key != 0 ? intro_base(key, a.L, a.p, q) : (K)0;
       const uint32_t cm = key_mask(key, a.L);
       const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
       for (int j = 0; j < nmax; ++j) {
@@ -730,7 +746,7 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
           if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
           for (int qq = 0; qq < a.nnb && valid; ++qq)
             if (qq != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[qq]), v);
-          if (valid) okey = intro_out(ob, vsh, v, cv);
+          if (valid) okey = intro_out(intro_base(key, a.L, a.p, q), vsh, v, cv);
         }
         warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
       }

@@ -372,7 +372,9 @@ __global__ void __launch_bounds__(BLOCK, 4) sweep_pass_kernel(SortSpec sp, const
 // The same steps as sweep_pass_kernel with twice the tile per block, so that each tile's
 // fixed costs (claim, barriers, look-back over 256 digit words, publication) are spread over
 // twice the records; the staging buffer lives in dynamic shared memory.
-template <typename K, typename SK, int ITEMS, bool FROM_KEY, bool STORE_S>
+// KI: record type read; K: record type written (narrower when the records leave carrying a
+// sort key of at most 64 bits in place of a 128-bit packed key).
+template <typename K, typename SK, int ITEMS, bool FROM_KEY, bool STORE_S, typename KI = K>
 __global__ void __launch_bounds__(512, 2) sweep_pass_wide_kernel(SortSpec sp, const void *src,
                                                                 const u64 *n_ptr, u64 n_cap,
                                                                 int shift, u64 epoch,
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(512, 2) sweep_pass_wide_kernel(SortSpec sp, co
   __shared__ unsigned s_tstart[256], s_wsum[8];
   __shared__ u64 s_excl[256];
   __shared__ unsigned s_tile, s_tcount, s_hist[256];
-  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  const Slot<KI> *in = reinterpret_cast<const Slot<KI> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const bool owner = tid < 256;  // warps 0..7: thread tid owns digit tid
@@ -412,13 +414,14 @@ __global__ void __launch_bounds__(512, 2) sweep_pass_wide_kernel(SortSpec sp, co
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const u64 i = wb + (u64)j * 32 + lane;
-      key[j] = 0;
+      KI kin = 0;
       cnt[j] = 0;
-      if (i < n) load_slot(in, i, key[j], cnt[j]);
+      if (i < n) load_slot(in, i, kin, cnt[j]);
+      // a full sort key never is 0 for a valid record: it holds the nonempty colour set
+      key[j] = (FROM_KEY && STORE_S) ? (kin != 0 ? (K)sort_key<SK>(kin, sp) : (K)0) : (K)kin;
     }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      if (key[j] != 0 && FROM_KEY && STORE_S) key[j] = (K)sort_key<SK>(key[j], sp);
       SK sk = (FROM_KEY && !STORE_S) ? sort_key<SK>(key[j], sp) : (SK)key[j];
       dig[j] = key[j] != 0 ? (int)((unsigned)(sk >> shift) & 255u) : -1;
       if (dig[j] >= 0) atomicAdd(&s_hist[dig[j]], 1u);
@@ -738,13 +741,14 @@ __global__ void __launch_bounds__(1024) blk_scan_kernel(u64 *blk, int G) {
   block_scan_array(blk, blk + G, (u64)G, blk + 2 * G);
 }
 
-template <typename K, int BLOCK, bool FROM_S>
+// KI: record type read (64-bit sort keys when a 128-bit table's records were narrowed)
+template <typename K, int BLOCK, bool FROM_S, typename KI = K>
 __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, const u64 *n_ptr,
                                                              u64 n_cap, const u64 *blk, void *dst,
                                                              u64 *count, SortSpec sp) {
   const u64 n = min(*n_ptr, n_cap);
   __shared__ int s_wc[BLOCK / 32];
-  const Slot<K> *in = reinterpret_cast<const Slot<K> *>(src);
+  const Slot<KI> *in = reinterpret_cast<const Slot<KI> *>(src);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(dst);
   const u64 G = gridDim.x, chunk = (n + G - 1) / G;
   const u64 lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
@@ -752,17 +756,17 @@ __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, co
   for (u64 base = lo; base < hi; base += BLOCK) {
     const u64 i = base + threadIdx.x;
     bool head = false;
-    K key = 0;
+    KI key = 0;
     u64 sum = 0;
     if (i < hi) {
-      K prev = 0;
+      KI prev = 0;
       u64 c;
       load_slot(in, i, key, sum);
       if (i > 0) load_slot(in, i - 1, prev, c);
       head = key != prev;
       if (head)  // the run may continue past this block's range
         for (u64 j = i + 1; j < n; ++j) {
-          K kj;
+          KI kj;
           load_slot(in, j, kj, c);
           if (kj != key) break;
           sum += c;
@@ -770,7 +774,7 @@ __global__ void __launch_bounds__(BLOCK) reduce_write_kernel(const void *src, co
     }
     int tot;
     const int rank = block_flag_rank<BLOCK>(head, s_wc, tot);
-    if (head) store_slot(out, cursor + rank, FROM_S ? unsort_key(key, sp) : key, sum);
+    if (head) store_slot(out, cursor + rank, FROM_S ? unsort_key((K)key, sp) : (K)key, sum);
     cursor += (u64)tot;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = blk[2 * G];
@@ -802,6 +806,27 @@ int sort_impl(cudaStream_t s, const DevInfo &d, const SortSpec &sp, const void *
     constexpr bool WIDE = sizeof(K) == 8;
     constexpr size_t WSMEM = (size_t)512 * ITEMS * (sizeof(Slot<K>) + 1);
     const int GW = d.sms * 2;
+    if constexpr (sizeof(K) == 16 && sizeof(SK) == 8) {
+      if (sp.full && !sw->tma) {  // 16-byte (sort key, count) records from the first pass on
+        constexpr size_t NSMEM = (size_t)512 * 8 * (sizeof(Slot<u64>) + 1);
+        for (int p = 0; p < passes; ++p) {
+          if (p == 0)
+            sweep_pass_wide_kernel<u64, u64, 8, true, true, K><<<GW, 512, NSMEM, s>>>(
+                sp, in, n_in, in_cap, 0, 1ull, sw->ghist, sw->status, sw->tile_ctr, bufs[cur],
+                buf_cap, sw->err);
+          else
+            sweep_pass_wide_kernel<u64, u64, 8, false, true><<<GW, 512, NSMEM, s>>>(
+                sp, in, n_in, in_cap, 8 * p, (u64)(p + 1), sw->ghist + 256 * p, sw->status,
+                sw->tile_ctr + p, bufs[cur], buf_cap, sw->err);
+          in = bufs[cur];
+          n_in = n;
+          in_cap = buf_cap;
+          cur ^= 1;
+        }
+        *which = cur ^ 1;
+        return (int)cudaGetLastError();
+      }
+    }
     for (int p = 0; p < passes; ++p) {
 #define CC_PASS(FK, SS)                                                                   \
   if (sw->tma)                                                                            \
@@ -880,6 +905,8 @@ int allow_wide_smem() {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   r |= (int)cudaFuncSetAttribute(sweep_pass_wide_kernel<u64, SK, 8, false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  r |= (int)cudaFuncSetAttribute(sweep_pass_wide_kernel<u64, u64, 8, true, true, u128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return r;
 }
 
@@ -911,15 +938,22 @@ int launch_sort_records(cudaStream_t s, const DevInfo &d, int kw, const SortSpec
                                         hist, which, sw);
 }
 
+bool sort_narrows(int kw, const SortSpec &sp, int sort_sweep) {
+  return kw == 2 && sp.full && sp.bits <= 64 && sort_sweep == 1;
+}
+
 int launch_reduce(cudaStream_t s, const DevInfo &d, int kw, const void *src,
                   const unsigned long long *n, unsigned long long n_cap, unsigned long long *blk,
-                  void *dst, unsigned long long *count, const SortSpec *from_s) {
+                  void *dst, unsigned long long *count, const SortSpec *from_s, bool narrow) {
   const int G = grid256(d);
   const SortSpec sp = from_s ? *from_s : SortSpec{};
-  if (kw == 1) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
+  if (kw == 1 || narrow) reduce_count_kernel<u64, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
   else reduce_count_kernel<u128, 256><<<G, 256, 0, s>>>(src, n, n_cap, blk);
   blk_scan_kernel<<<1, 1024, 0, s>>>(blk, G);
-  if (kw == 1) {
+  if (narrow && from_s) {  // 64-bit sort keys in, 128-bit packed keys out
+    reduce_write_kernel<u128, 256, true, u64><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count,
+                                                                sp);
+  } else if (kw == 1) {
     if (from_s)
       reduce_write_kernel<u64, 256, true><<<G, 256, 0, s>>>(src, n, n_cap, blk, dst, count, sp);
     else
