@@ -30,6 +30,7 @@ import glob
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -68,12 +69,12 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_ratios(workload):
+def traffic_ratios(workload, out_dir=None):
     """Measured DRAM bytes per algorithmic byte of each node rule's kernels for `workload`, from
     the committed capture summary of this build (profiles/dram_<workload>.txt: lines
     `ratio <group> <dram bytes> <algorithmic bytes>` and `sources <hash>`); {} if there is none
     or the sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"dram_{workload}.txt")
+    path = os.path.join(out_dir or os.path.join(ROOT, "profiles"), f"dram_{workload}.txt")
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -143,6 +144,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+T_START = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - T_START:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def slot_bytes(b, k):
     """Algorithmic bytes of one table entry: b vertex ids, the colour set and the count."""
     return 4 * b + (2 if k <= 16 else 4) + 8
@@ -190,6 +199,142 @@ GROUPS = {"color": "colour", "leaf": "leaf", "intro_count": "introduce",
           "intro_write": "introduce", "intro_fused": "introduce+forget", "forget": "forget",
           "sort": "forget", "reduce": "forget", "merge": "forget", "join_build": "join",
           "join_count": "join", "join_write": "join", "root": "root"}
+
+
+# device kernels (by function name) grouped by the node rule they implement, for the DRAM-traffic
+# summary of an ncu capture; kernels of no node rule (graph set-up, enumeration) are "other"
+KERNEL_GROUPS = {
+    "color_kernel": "colour", "leaf_kernel": "leaf",
+    "intro_kernel": "introduce", "intro_warp_kernel": "introduce",
+    "intro_group_warp_kernel": "introduce",
+    "sort_hist_kernel": "forget", "row_scan_kernel": "forget", "digit_base_kernel": "forget",
+    "sort_scatter_kernel": "forget", "sweep_hist_kernel": "forget",
+    "sweep_bases_kernel": "forget", "sweep_pass_kernel": "forget",
+    "sweep_pass_wide_kernel": "forget", "sweep_pass_tma_kernel": "forget",
+    "reduce_count_kernel": "forget", "blk_scan_kernel": "forget",
+    "reduce_write_kernel": "forget", "forget_kernel": "forget", "part_hist_kernel": "forget",
+    "part_cursor_kernel": "forget", "part_split_kernel": "forget",
+    "part_local_kernel": "forget",
+    "join_build_kernel": "join", "join_probe_kernel": "join", "root_kernel": "root",
+}
+
+
+def kernel_base(name):
+    """Function name of a kernel as ncu lists it (demangled, with namespaces, template and
+    argument lists): the first word ending in _kernel, else the whole name."""
+    m = re.search(r"(\w+_kernel)\b", name)
+    return m.group(1) if m else name.strip()
+
+
+def kernel_group(name, fused):
+    """Node-rule group of a device kernel named `name` in an ncu listing (demangled names carry
+    templates and arguments); introduce kernels count as "introduce+forget" in a fused run."""
+    g = KERNEL_GROUPS.get(kernel_base(name), "other")
+    if fused and g == "introduce":
+        return "introduce+forget"
+    return g
+
+
+def ncu_kernels(csv_path):
+    """Per launch of an ncu CSV listing (--csv --log-file): kernel name, DRAM bytes read and
+    written and device time in ms (the metrics the listing has; the others 0)."""
+    import csv
+
+    rows = list(csv.reader(open(csv_path)))
+    head = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    cols = rows[head]
+    ci = {c: cols.index(c) for c in ("ID", "Kernel Name", "Metric Name", "Metric Unit",
+                                     "Metric Value")}
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6,
+             "GB": 1e9, "nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "ns": 1e-6,
+             "us": 1e-3, "ms": 1.0}
+    per = {}
+    for r in rows[head + 1:]:
+        if len(r) < len(cols):
+            continue
+        kid, kname, metric = r[ci["ID"]], r[ci["Kernel Name"]], r[ci["Metric Name"]]
+        v = float(r[ci["Metric Value"]].replace(",", "")) * scale.get(r[ci["Metric Unit"]], 1)
+        d = per.setdefault(kid, {"name": kname, "read": 0.0, "write": 0.0, "ms": 0.0})
+        if metric == "dram__bytes_read.sum":
+            d["read"] = v
+        elif metric == "dram__bytes_write.sum":
+            d["write"] = v
+        elif metric == "gpu__time_duration.sum":
+            d["ms"] = v
+    return list(per.values())
+
+
+def kernel_table(launches, fused=False):
+    """Launches summed per kernel function and per node-rule group."""
+    by_kernel, by_group = {}, {}
+    for d in launches:
+        k = by_kernel.setdefault(kernel_base(d["name"]),
+                                 {"launches": 0, "read": 0.0, "write": 0.0, "ms": 0.0})
+        k["launches"] += 1
+        for f in ("read", "write", "ms"):
+            k[f] += d[f]
+        g = by_group.setdefault(kernel_group(d["name"], fused),
+                                {"launches": 0, "dram": 0.0, "ms": 0.0})
+        g["launches"] += 1
+        g["dram"] += d["read"] + d["write"]
+        g["ms"] += d["ms"]
+    return by_kernel, by_group
+
+
+def traffic_summary(csv_path, alg_path, cmd, out_dir=None):
+    """profiles/dram_<workload>.txt from an ncu capture of one `--capture` step: DRAM bytes
+    (dram__bytes_read.sum + dram__bytes_write.sum) and device time of every kernel of the step,
+    summed per node rule, beside the algorithmic bytes the same step's node rules moved (written
+    by --capture); the bench scales each group's ratio to its own launches."""
+    alg = json.load(open(alg_path))
+    fused = "introduce+forget" in alg["groups"]
+    by_kernel, by_group = kernel_table(ncu_kernels(csv_path), fused)
+    total_ms = sum(g["ms"] for g in by_group.values()) or 1.0
+    out = [f"# DRAM traffic per node rule: {alg['workload']}, {alg['trials']} trials, one planned "
+           "step (profiled launches)",
+           f"# capture: {cmd}",
+           f"sources {alg['sources']}",
+           f"opts {json.dumps(alg['opts'], sort_keys=True)}",
+           "# ratio <group> <DRAM bytes of the step> <algorithmic bytes of the step>"]
+    for g, v in sorted(by_group.items(), key=lambda x: -x[1]["ms"]):
+        if g in alg["groups"] and alg["groups"][g]["bytes"] > 0:
+            out.append(f"ratio {g} {v['dram']:.0f} {alg['groups'][g]['bytes']:.0f}")
+    out.append("# group  share-of-kernel-time  DRAM-GB  algorithmic-GB  ms (cold-cache, "
+               "serialised under ncu)")
+    for g, v in sorted(by_group.items(), key=lambda x: -x[1]["ms"]):
+        ab = alg["groups"].get(g, {}).get("bytes", 0) / 1e9
+        out.append(f"#   {g:18s} {v['ms'] / total_ms:6.3f} {v['dram'] / 1e9:9.3f} {ab:9.3f} "
+                   f"{v['ms']:9.3f}")
+    out.append("# kernel  launches  DRAM read GB  DRAM write GB  ms")
+    for k, v in sorted(by_kernel.items(), key=lambda x: -x[1]["ms"]):
+        out.append(f"#   {k:26s} {v['launches']:5d} {v['read'] / 1e9:9.3f} "
+                   f"{v['write'] / 1e9:9.3f} {v['ms']:9.3f}")
+    path = os.path.join(out_dir or os.path.join(ROOT, "profiles"), f"dram_{alg['workload']}.txt")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+    return path
+
+
+def launch_summary(csv_path, workload, cmd, out_dir=None):
+    """profiles/launches_<workload>.txt from an ncu launch list (gpu__time_duration.sum of every
+    launch of a bench command): per kernel and per node rule the launches, total device time and
+    share.  Under ncu launches are serialised and run cold: the shares compare with the bench's
+    event-timed shares, the absolute times do not."""
+    by_kernel, by_group = kernel_table(ncu_kernels(csv_path))
+    total = sum(v["ms"] for v in by_kernel.values()) or 1.0
+    out = [f"# ncu launch list: {workload}", f"# command: {cmd}",
+           f"# {sum(v['launches'] for v in by_kernel.values())} launches, {total:.3f} ms of "
+           "device time (serialised, cold caches)",
+           "# group  launches  ms  share"]
+    for g, v in sorted(by_group.items(), key=lambda x: -x[1]["ms"]):
+        out.append(f"{g:18s} {v['launches']:6d} {v['ms']:10.3f} {v['ms'] / total:6.3f}")
+    out.append("# kernel  launches  ms  share")
+    for k, v in sorted(by_kernel.items(), key=lambda x: -x[1]["ms"]):
+        out.append(f"{k:26s} {v['launches']:6d} {v['ms']:10.3f} {v['ms'] / total:6.3f}")
+    path = os.path.join(out_dir or os.path.join(ROOT, "profiles"), f"launches_{workload}.txt")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+    return path
 
 
 def describe(name):
@@ -382,7 +527,8 @@ def roofline(kern, steps, workload):
                         for kn, v in sorted(kern.items(), key=lambda x: -x[1]["ms"])}}
 
 
-def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=None):
+def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=None,
+           capture=None):
     """The DP of workload `name` on one context: (optionally) autotune, W untimed warm-up steps,
     K timed steps (colour, DP with profiled launches, counts back, enumerate), then the same
     steps end to end through the C ABI with the graph copied from pinned host memory."""
@@ -398,13 +544,17 @@ def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=N
     pid = cc.cc_load_pattern(h, nF, edges, td)
     out = {"config": describe(name)}
     out["config"]["trials"] = T
-    tuned = cc.cc_default_opts()
-    if tune:
+    tuned = cc.cc_default_opts(**(json.loads(args.opts) if args.opts else {}))
+    if tune and not args.opts:
         cid = cc.cc_color(h, seed, T, k)
         t0 = time.perf_counter()
+        pid0 = pid
+        log(f"{name}: autotuning")
         tuned, pid, best_ms, tried = cc.cc_autotune(h, pid, cid, None, 6, 2)
+        log(f"{name}: autotuned ({tried} configurations, best {best_ms:.1f} ms)")
         out["autotune"] = {"configs_tried": tried, "best_ms": best_ms,
-                           "seconds": time.perf_counter() - t0}
+                           "seconds": time.perf_counter() - t0,
+                           "schedule": "re-rooted" if pid != pid0 else "as given"}
         cc.cc_release_colors(h, cid)
     out["config"]["opts"] = {f: getattr(tuned, f) for f, _ in tuned._fields_}
     nodes = cc.cc_pattern_nodes(h, pid, nF)
@@ -421,15 +571,35 @@ def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=N
         rows = cc.cc_enumerate(h, run, enum_limit, nF)[0] if enum_limit else None
         return cid, run, counts, rows
 
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 1 if capture else 0)):  # a capture's step is planned
         cid, run, counts, rows = step(opts)
         cc.cc_release(h, run)
         cc.cc_release_colors(h, cid)
     torch.cuda.synchronize()
+    if capture:  # one planned step inside the profiler range, for an ncu capture
+        torch.cuda.profiler.start()
+        cid, run, counts, rows = step(opts)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        sizes, total = cc.cc_table_stats(h, run, len(nodes))
+        node, kind, ms, cand = cc.cc_run_timings(h, run)
+        groups = {}
+        for i in range(len(node)):
+            kn = cc.KERNEL_KINDS[int(kind[i])]
+            g2 = groups.setdefault(GROUPS.get(kn, kn), {"launches": 0, "bytes": 0})
+            g2["launches"] += 1
+            g2["bytes"] += algorithmic_bytes(kn, int(node[i]), nodes, sizes, cand[i], n, T, k)
+        with open(capture, "w") as f:
+            json.dump({"workload": name, "trials": T, "sources": source_hash(),
+                       "opts": out["config"]["opts"], "entries": int(total),
+                       "groups": groups}, f)
+        ctx.close()
+        return None
     if dist:
         dist.barrier()
     if sampler:
         sampler.start()
+    log(f"{name}: warm-up done, timing {args.steps} steps")
     launches0 = cc.cc_context_stats(h)[0]
     step_ms, entries, kern, modes = [], 0, {}, set()
     for _ in range(args.steps):
@@ -467,6 +637,7 @@ def dp_leg(cc, torch, name, args, rank, dist, tune=True, enum_limit=0, sampler=N
     if enum_limit:
         out["enumerated_rows"] = int(len(rows))
 
+    log(f"{name}: timed steps done ({sum(step_ms) / args.steps:.1f} ms per step)")
     # end to end through the C ABI: graph from pinned host memory, counts (and rows) back
     if rank == 0:
         rp_h = torch.from_numpy(np.asarray(g[0], np.int32)).pin_memory().numpy()
@@ -719,6 +890,8 @@ def er_phase_leg(cc, torch, step=None, arena_gb=8):
                 ms[ip, iq] = (time.perf_counter() - t0) * 1e3
                 status[ip, iq], width[ip, iq], found[ip, iq] = st, w, 1 if f else 0
                 entries += ent
+            log(f"er_phase: row p={probs[ip]:.2f} done ({ms[ip].sum() / 1e3:.1f} s, "
+                f"max point {ms[ip].max() / 1e3:.2f} s)")
     ok = status == 0
     return {
         "workload": "er_phase", "target": f"G({spec['n_target']}, p)",
@@ -775,6 +948,7 @@ def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
     drain([cc.cc_serve_submit(h, pids[q["pattern"]], q["seed"] ^ 0x5A5A, q["trials"], q["k"])
            for q in warm], [q["trials"] for q in warm])
     cc.cc_serve_stop(h)
+    log(f"serving: {len(warm)} keys planned; submitting {len(stream)} queries")
     cc.cc_serve_start(h, budget_gb << 30, slots)
     t0 = time.perf_counter()
     tickets = []
@@ -792,6 +966,7 @@ def serve_leg(cc, torch, count, arena_gb, budget_gb, slots):
     lat_ms = [res[i][2] / 1e6 for i in ok]
     makespan = max(stream[i]["t"] + res[i][2] / 1e9 for i in range(len(stream)))
     # plain path under the same arrivals, measured: query i starts at max(arrival, previous end)
+    log(f"serving: served leg done (makespan {makespan:.1f} s); plain leg")
     plain_lat, plain_ms, same = [], [], True
     t0 = time.perf_counter()
     for i in ok:
@@ -853,7 +1028,29 @@ def main():
                     help="device arena of the DP context (small values for profiling captures)")
     ap.add_argument("--serve-queries", type=int, default=2000,
                     help="queries of the serving stream to run (the full stream has 2000)")
+    ap.add_argument("--opts", default="",
+                    help="run options as a JSON object of cc_run_opts fields (default options "
+                         "otherwise); given options are used as they are, without autotuning")
+    ap.add_argument("--capture", default="", metavar="JSON",
+                    help="for an ncu capture: warm-up steps, then one step inside the profiler "
+                         "range (ncu --profile-from-start off); writes the step's algorithmic "
+                         "bytes per node rule to JSON and prints nothing else")
+    ap.add_argument("--traffic-summary", nargs=2, metavar=("CSV", "JSON"),
+                    help="write profiles/dram_<workload>.txt from the ncu CSV of a --capture "
+                         "run (dram__bytes_read.sum, dram__bytes_write.sum, "
+                         "gpu__time_duration.sum) and its JSON; runs nothing on the GPU")
+    ap.add_argument("--capture-cmd", default="", help="the capture's command line, recorded in "
+                    "the summary")
+    ap.add_argument("--launch-summary", default="", metavar="CSV",
+                    help="write profiles/launches_<workload>.txt from the ncu launch list "
+                         "(gpu__time_duration.sum) of a bench command; runs nothing on the GPU")
     args = ap.parse_args()
+    if args.launch_summary:
+        print(launch_summary(args.launch_summary, args.workload, args.capture_cmd))
+        return
+    if args.traffic_summary:
+        print(traffic_summary(*args.traffic_summary, args.capture_cmd))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -876,11 +1073,16 @@ def main():
         dist.init_process_group("nccl")
     legs = set() if args.legs == "none" else set(args.legs.split(","))
     enum_limit = ENUM_LIMIT if args.workload == MAIN else 0
+    if args.capture:
+        dp_leg(cc, torch, args.workload, args, rank, None, tune=False,
+               enum_limit=ENUM_LIMIT if args.workload == MAIN else 0, capture=args.capture)
+        return
     sampler = ClockSampler(torch.cuda.current_device())
     main_leg = dp_leg(cc, torch, args.workload, args, rank, dist, tune=not args.no_tune,
                       enum_limit=enum_limit, sampler=sampler)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("cpu baseline (oracle)")
         cpu = cpu_baseline(cc, args.workload, main_leg, main_leg["counts"])
     main_leg.pop("_ctx")[0].close()
     torch.cuda.empty_cache()
@@ -907,6 +1109,7 @@ def main():
         if "ba20k" in legs and args.workload != "ba20k_grid2x4":
             a2 = argparse.Namespace(**vars(args))
             a2.arena_gb = min(args.arena_gb, 96)
+            log("leg: ba20k_grid2x4")
             leg = dp_leg(cc, torch, "ba20k_grid2x4", a2, rank, None, tune=False,
                          sampler=ClockSampler(torch.cuda.current_device()))
             leg.pop("_ctx")[0].close()
@@ -914,15 +1117,20 @@ def main():
             torch.cuda.empty_cache()
             line["ba20k_grid2x4"] = leg
         if "latency" in legs:
+            log("leg: latency")
             line["er200_c5_latency"] = latency_leg(cc, torch)
         if "batching" in legs:
+            log("leg: batching")
             line["batched_vs_plain"] = batching_leg(cc, torch)
             torch.cuda.empty_cache()
         if "er_phase" in legs:
+            log("leg: er_phase")
             line["er_phase"] = er_phase_leg(cc, torch, args.er_phase_step or None)
             torch.cuda.empty_cache()
         if "serve" in legs and args.serve_queries > 0:
+            log("leg: serving")
             line["serving"] = serve_leg(cc, torch, args.serve_queries, 200, 160, 8)
+    log("done")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -35,3 +35,56 @@ def test_percentile_and_entry_bytes():
     xs = list(range(1, 101))
     assert bench.pct(xs, 50) == 50 and bench.pct(xs, 99) == 99 and bench.pct([7], 99) == 7
     assert bench.slot_bytes(2, 8) == 4 * 2 + 2 + 8 and bench.slot_bytes(3, 20) == 12 + 4 + 8
+
+
+def test_traffic_summary_from_an_ncu_listing(tmp_path):
+    """The DRAM-traffic summary of a capture: DRAM bytes of each kernel summed by node rule
+    (templated, demangled names included), each rule's ratio to the step's algorithmic bytes,
+    read back by the bench only while the library's sources are unchanged."""
+    import json
+
+    head = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+            '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+            '"Metric Value"')
+    rows = [head]
+
+    def add(i, name, rd, wr, ns):
+        for m, u, v in (("dram__bytes_read.sum", "Mbyte", rd), ("dram__bytes_write.sum",
+                                                                 "Kbyte", wr),
+                        ("gpu__time_duration.sum", "nsecond", ns)):
+            rows.append(f'"{i}","1","python","h","{name}","1","7","(256, 1, 1)","(10, 1, 1)",'
+                        f'"0","10.3","Command line profiler metrics","{m}","{u}","{v}"')
+
+    add(0, "void cc::(anonymous namespace)::color_kernel(int, int)", "1.5", "3,000", "1000")
+    add(1, "void cc::(anonymous namespace)::intro_warp_kernel<unsigned long, 1>(cc::X)", "100",
+        "50,000", "500000")
+    add(2, "void cc::(anonymous namespace)::sweep_pass_kernel<unsigned long, unsigned long, "
+        "256, 6, true, false>(cc::SortSpec)", "200", "200,000", "250000")
+    add(3, "reduce_write_kernel<unsigned long, 256, false>", "40", "10,000", "50000")
+    add(4, "enum_step_kernel", "1", "1", "100")
+    csv = tmp_path / "dram.csv"
+    csv.write_text("==PROF== Connected\n" + "\n".join(rows) + "\n")
+    alg = {"workload": "toy", "trials": 2, "sources": bench.source_hash(), "opts": {"fuse": 0},
+           "entries": 1, "groups": {"colour": {"launches": 1, "bytes": 4.5e6},
+                                    "introduce": {"launches": 1, "bytes": 75e6},
+                                    "forget": {"launches": 2, "bytes": 100e6}}}
+    aj = tmp_path / "alg.json"
+    aj.write_text(json.dumps(alg))
+    path = bench.traffic_summary(str(csv), str(aj), "ncu ... bench.py --capture", str(tmp_path))
+    r = bench.traffic_ratios("toy", str(tmp_path))
+    assert abs(r["colour"] - 1.0) < 1e-9
+    assert abs(r["introduce"] - 2.0) < 1e-9  # 150 MB against 75 MB
+    assert abs(r["forget"] - 4.5) < 1e-9  # (400 + 50) MB against 100 MB
+    assert "other" not in r
+    text = open(path).read()
+    assert "sweep_pass_kernel" in text and "bench.py --capture" in text
+    # another build's capture is not used
+    alg["sources"] = "0" * 16
+    aj.write_text(json.dumps(alg))
+    bench.traffic_summary(str(csv), str(aj), "x", str(tmp_path))
+    assert bench.traffic_ratios("toy", str(tmp_path)) == {}
+    # the launch list summary of the same listing: shares per kernel and per node rule
+    lp = bench.launch_summary(str(csv), "toy", "ncu ... bench.py", str(tmp_path))
+    lines = {ln.split()[0]: ln.split() for ln in open(lp) if not ln.startswith("#")}
+    assert lines["forget"][1] == "2" and abs(float(lines["forget"][3]) - 0.3 / 0.8001) < 1e-3
+    assert lines["intro_warp_kernel"][1] == "1"
