@@ -42,6 +42,7 @@ extern "C" {
 #define CC_ENOTFOUND (-6)  /* unknown pattern, colouring, run or ticket id                      */
 #define CC_EKEYWIDTH (-7)  /* trial, bag-mapping and colour-set bits do not fit in 128 bits     */
 #define CC_EBUSY (-8)      /* the context is serving: only cc_serve_* and the pattern calls run */
+#define CC_ECANCELED (-9)  /* a served query was dropped before it started (cc_serve_cancel)     */
 
 /* Static text for an error code. */
 const char *cc_strerror(int code);
@@ -171,6 +172,12 @@ typedef struct {
                          /*    (CC_MODE_SLICED); 0 = 4096                                        */
   int32_t part_bits;     /* sort_sweep 3: log2 of the bucket count (1..20); 0 = from the size  */
                          /*    of the table, about 1024 records a bucket                         */
+  int32_t chain;         /* 1 (default): in planned runs, an introduce whose parent introduces */
+                         /*    a vertex not adjacent to its own, with >= 2 bag neighbours whose */
+                         /*    images the child's runs share, runs in one pass with that parent: */
+                         /*    its entries are generated, counted and extended at once, and its */
+                         /*    table is never stored (its size is still counted; enumeration   */
+                         /*    resolves introduce nodes by their rule, Section 4)              */
 } cc_run_opts;
 
 /* Fills *opts with the defaults (degree_filter 1, retain 0, fuse 2, use_graph 0, load factor
@@ -314,6 +321,7 @@ int cc_release(cc_ctx *ctx, int32_t run_id);
 #define CC_K_SORT 10   /* all passes of one radix sort of a table's records */
 #define CC_K_REDUCE 11 /* reduce-by-key of sorted records (a forget's merge) */
 #define CC_K_MERGE 12  /* a forget's whole bucketed merge (sort_sweep 3): split, sort, merge */
+#define CC_K_INTRO_CHAIN 13 /* two introduces in one pass (option chain); node = the upper one */
 
 /* Per-launch device times of a run made with profile = 1, in launch order: node id, kernel
  * kind (CC_K_*), milliseconds between CUDA events recorded on the context's stream just before
@@ -409,6 +417,13 @@ int cc_serve_poll(cc_ctx *ctx, int64_t ticket, int32_t *done, int32_t *status,
 int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed, int32_t *inflight_max,
                    uint64_t *reserved_max, uint64_t *exact_runs, uint64_t *reruns,
                    uint64_t *sliced);
+
+/* Drops every query submitted so far that has not started: each ends with status CC_ECANCELED
+ * (its ticket is polled as usual); queries already running finish.  Lets a caller bound a
+ * session by time when some queries are far costlier than others (a query that runs split
+ * holds the GPU alone until it ends).  *n_cancelled (may be NULL) = queries dropped.  Errors:
+ * CC_EINVAL (not serving). */
+int cc_serve_cancel(cc_ctx *ctx, uint64_t *n_cancelled);
 
 /* Stops the server after the queued and running queries finish; results not yet polled stay
  * available.  Returns CC_OK if no server runs. */

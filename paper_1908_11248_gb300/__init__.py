@@ -24,20 +24,23 @@ LEAF, INTRODUCE, FORGET, JOIN = 0, 1, 2, 3
 CC_OK, CC_EINVAL, CC_ENOMEM, CC_ECAPACITY, CC_ETIMEOUT, CC_ECUDA, CC_ENOTFOUND, CC_EKEYWIDTH = \
     0, -1, -2, -3, -4, -5, -6, -7
 CC_EBUSY = -8
+CC_ECANCELED = -9
 
 EXPORTS = [
     "cc_strerror", "cc_create", "cc_destroy", "cc_load_graph", "cc_load_pattern",
     "cc_pattern_info", "cc_pattern_nodes", "cc_color", "cc_set_colors", "cc_get_colors",
     "cc_release_colors", "cc_default_opts", "cc_run_dp", "cc_run_batch", "cc_decide", "cc_count",
     "cc_table_stats", "cc_table_dump", "cc_enumerate", "cc_release", "cc_serve_start",
-    "cc_serve_submit", "cc_serve_poll", "cc_serve_stop", "cc_run_timings", "cc_context_stats",
+    "cc_serve_submit", "cc_serve_poll", "cc_serve_cancel", "cc_serve_stop", "cc_run_timings",
+    "cc_context_stats",
     "cc_nice_decomposition", "cc_check_graph", "cc_count_noalloc", "cc_run_mode",
     "cc_serve_stats", "cc_autotune", "cc_solve_trials", "cc_solve",
     "cc_load_pattern_masked", "cc_enumerate_sets", "cc_probe_bounded_wait",
 ]
 RUN_MODES = ["exact", "planned", "graph", "streamed", "sliced"]
 KERNEL_KINDS = ["color", "leaf", "intro_count", "intro_write", "intro_fused", "forget",
-                "join_build", "join_count", "join_write", "root", "sort", "reduce", "merge"]
+                "join_build", "join_count", "join_write", "root", "sort", "reduce", "merge",
+                "intro_chain"]
 
 
 class CCError(RuntimeError):
@@ -57,7 +60,8 @@ class cc_run_opts(ctypes.Structure):
                 ("load_factor", ctypes.c_float), ("block", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("group", ctypes.c_int32),
                 ("sort_sweep", ctypes.c_int32), ("distance_prune", ctypes.c_int32),
-                ("max_slices", ctypes.c_int32), ("part_bits", ctypes.c_int32)]
+                ("max_slices", ctypes.c_int32), ("part_bits", ctypes.c_int32),
+                ("chain", ctypes.c_int32)]
 
 
 _lib = None
@@ -100,6 +104,7 @@ def lib():
         "cc_serve_submit": ([P, i32, u64, i32, i32, u64, P], ctypes.c_int),
         "cc_serve_poll": ([P, i64, P, P, P, P, P, P, P], ctypes.c_int),
         "cc_serve_stop": ([P], ctypes.c_int),
+        "cc_serve_cancel": ([P, P], ctypes.c_int),
         "cc_run_timings": ([P, i32, i32, P, P, P, P, P], ctypes.c_int),
         "cc_context_stats": ([P, P, P, P], ctypes.c_int),
         "cc_nice_decomposition": ([i32, i32, P, P, i32, P, P, P, P, P, P, P, P], ctypes.c_int),
@@ -438,6 +443,13 @@ def cc_serve_stats(ctx) -> dict:
     names = ["submitted", "completed", "inflight_max", "reserved_max", "exact_runs", "reruns",
              "sliced"]
     return {k: int(x.value) for k, x in zip(names, v)}
+
+
+def cc_serve_cancel(ctx) -> int:
+    """Drops the queued queries that have not started (status CC_ECANCELED); their number."""
+    n = ctypes.c_uint64(0)
+    _check(lib().cc_serve_cancel(ctx, ctypes.byref(n)), "cc_serve_cancel")
+    return n.value
 
 
 def cc_serve_stop(ctx):

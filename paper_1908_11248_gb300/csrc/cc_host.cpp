@@ -504,8 +504,34 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     }
     return true;
   };
+  // chained introduces (option chain): introduce x1 with a bag neighbour, under an introduce
+  // x2 of a vertex not adjacent to x1's that has >= 2 bag neighbours (all of them in x1's child
+  // y) and whose table is not added into a forget's hash; returns x2 and fills x2's
+  // bag-neighbour slots counted in y's bag, else -1 (structure only: y's order is checked when
+  // x1 is reached)
+  auto chain_parent = [&](int x1, int *nb2, int *nnb2) -> int {
+    if (!R->opts.chain || !R->opts.group) return -1;
+    const NiceNode &n1 = P.nodes[x1];
+    if (n1.type != 1 || n1.parent < 0) return -1;
+    const int x2 = n1.parent;
+    const NiceNode &n2 = P.nodes[x2];
+    if (n2.type != 1 || (P.adj[n2.vertex] >> n1.vertex & 1u)) return -1;
+    const NiceNode &ny = P.nodes[n1.child0];
+    int k1 = 0, k2 = 0;
+    for (size_t s = 0; s < ny.bag.size(); ++s) {
+      if (P.adj[n1.vertex] >> ny.bag[s] & 1u) ++k1;
+      if (P.adj[n2.vertex] >> ny.bag[s] & 1u) nb2[k2++] = (int)s;
+    }
+    if (k1 < 1 || k2 < 2 || k2 * R->L.nb > 64) return -1;
+    const int f = n2.parent;
+    if (f >= 0 && P.nodes[f].type == 2 && R->opts.fuse == 1) return -1;
+    *nnb2 = k2;
+    return x2;
+  };
+  std::vector<int> chain_from(N, -1);  // x2 -> the x1 it runs together with
   // full sort order for the table of forget node f: when the next node introduces a vertex
-  // with bag neighbours, their slots come first so that its runs are contiguous
+  // with bag neighbours, their slots come first so that its runs are contiguous (when that
+  // introduce runs chained with its parent, the parent's bag neighbours come first)
   auto forget_order = [&](int f) {
     const NiceNode &fn = P.nodes[f];
     cc::SortSpec sp{};
@@ -515,9 +541,15 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
     sp.nsl = 0;
     bool used[cc::kMaxBag] = {};
     const int g = fn.parent;
+    int nb2[cc::kMaxBag], nnb2 = 0;
+    if (g >= 0 && chain_parent(g, nb2, &nnb2) >= 0)
+      for (int j = 0; j < nnb2; ++j) {
+        sp.order[sp.nsl++] = nb2[j];
+        used[nb2[j]] = true;
+      }
     if (g >= 0 && P.nodes[g].type == 1)
       for (int s = 0; s < sp.b; ++s)
-        if (P.adj[P.nodes[g].vertex] >> fn.bag[s] & 1u) {
+        if (!used[s] && (P.adj[P.nodes[g].vertex] >> fn.bag[s] & 1u)) {
           sp.order[sp.nsl++] = s;
           used[s] = true;
         }
@@ -584,17 +616,42 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
       rc = timed(x, CC_K_LEAF, 1, [&] { return cc::launch_leaf(c->stream, c->dev, R->kw, a); });
       if (rc) return rc;
     } else if (nd.type == 1) {  // introduce
-      const int y = nd.child0;
-      const NiceNode &ch = P.nodes[y];
+      if (planned) {
+        // the lower introduce of a chain: nothing runs now, its parent runs both
+        int nb2[cc::kMaxBag], nnb2 = 0;
+        const int x2 = chain_parent(x, nb2, &nnb2);
+        if (x2 >= 0 && grouped_by(R->tables[nd.child0], nnb2, nb2)) {
+          chain_from[x2] = x;
+          made[x] = true;
+          continue;
+        }
+      }
+      // chained: the input is the lower introduce's child, whose bag lacks that introduce's
+      // vertex (slot c_p of the lower bag); this introduce's bag neighbours are all in it
+      const int x1 = chain_from[x];
+      const int y = x1 >= 0 ? P.nodes[x1].child0 : nd.child0;
+      const NiceNode &ch = P.nodes[nd.child0];
       cc::IntroArgs a{};
       a.G = G;
       a.L = R->L;
       a.in = desc(y);
-      a.b_in = (int)ch.bag.size();
+      a.b_in = (int)P.nodes[y].bag.size();
       a.p = pos_in(nd.bag, nd.vertex);
       a.nnb = 0;
       for (size_t s = 0; s < ch.bag.size(); ++s)
         if (P.adj[nd.vertex] >> ch.bag[s] & 1u) a.nb_slot[a.nnb++] = (int)s;
+      if (x1 >= 0) {
+        const NiceNode &n1 = P.nodes[x1];
+        const NiceNode &ny = P.nodes[y];
+        a.c_p = pos_in(n1.bag, n1.vertex);
+        for (int j = 0; j < a.nnb; ++j) a.nb_slot[j] -= a.nb_slot[j] > a.c_p ? 1 : 0;
+        a.c_nnb = 0;
+        for (size_t s = 0; s < ny.bag.size(); ++s)
+          if (P.adj[n1.vertex] >> ny.bag[s] & 1u) a.c_nb_slot[a.c_nnb++] = (int)s;
+        a.c_degF = df ? P.deg[n1.vertex] : 0;
+        a.c_ubit = 1u << n1.vertex;
+        a.c_valid = R->d_counters + x1;
+      }
       if (a.nnb == 0 && R->opts.distance_prune) {
         // distance bound: candidates are the ball of radius dist_F(w, u) around the image of
         // the nearest bag vertex w, walked like an adjacency list (no other bag neighbour is
@@ -672,14 +729,29 @@ int run_nodes(Ctx *c, Run *R, const Pattern &P, const cc::Coloring &col, const c
         a.cursor = planned ? cursor + x : nullptr;
         a.cand = planned ? R->d_counters + 3 * N + x : nullptr;
         if (planned) check(cursor + x, cap);
-        // planned runs: lean warp kernels (expanding, or grouped by bag-neighbour images)
+        // planned runs: lean warp kernels (expanding, or grouped by bag-neighbour images, or
+        // two introduces chained)
         const bool warp = planned && a.nnb <= 1, gwarp = planned && grouped;
-        int r = timed(x, CC_K_INTRO_WRITE, 1, [&] {
-          return warp    ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 1, a)
+        // chained, the lower introduce with one bag neighbour: colour counts of every host
+        // vertex's neighbours let entries whose runs have no upper candidate count their lower
+        // extensions without walking the adjacency
+        u64 *hist = nullptr;
+        if (x1 >= 0 && a.c_nnb == 1 && R->L.k <= 16 && c->max_deg < 65536)
+          hist = arena_alloc<u64>(c, (size_t)R->trials * (size_t)n * 4);
+        a.c_hist = hist;
+        int r = timed(x, x1 >= 0 ? CC_K_INTRO_CHAIN : CC_K_INTRO_WRITE, hist ? 2 : 1, [&] {
+          if (hist) {
+            const int h = cc::launch_nb_colour_hist(c->stream, c->dev, a.G, R->trials, a.c_degF,
+                                                    a.c_ubit, hist, a.cand);
+            if (h) return h;
+          }
+          return x1 >= 0 ? cc::launch_intro_chain(c->stream, c->dev, R->kw, a)
+                 : warp  ? cc::launch_intro_warp(c->stream, c->dev, R->kw, 1, a)
                  : gwarp ? cc::launch_intro_group_warp(c->stream, c->dev, R->kw, 1, a)
                          : cc::launch_intro_blk(c->stream, c->dev, R->kw, 1, grouped, block, a,
                                                 blk);
         });
+        A.release(hist);
         if (R->opts.profile && !r) R->timings.back().candidates = cand;
         return r;
       };
@@ -922,7 +994,8 @@ int finish_run(Ctx *c, Run *R) {
     if (words[2 * N + x]) R->pairs[x] = words[2 * N + x];
   }
   for (auto &t : R->timings)
-    if (t.kind == CC_K_INTRO_COUNT || t.kind == CC_K_INTRO_WRITE || t.kind == CC_K_INTRO_FUSED)
+    if (t.kind == CC_K_INTRO_COUNT || t.kind == CC_K_INTRO_WRITE || t.kind == CC_K_INTRO_FUSED ||
+        t.kind == CC_K_INTRO_CHAIN)
       t.candidates = words[3 * (size_t)N + t.node];
   for (const auto &chk : R->checks) {
     const u64 v = words[chk.first - R->d_counters];
@@ -1290,7 +1363,8 @@ int init_run(Ctx *c, int32_t pid, const cc::Coloring &col, int32_t cid, const cc
 std::vector<long long> plan_key(const Ctx *c, int32_t pid, int32_t trials, int32_t k,
                                 const cc_run_opts &o) {
   return {pid, c->graph_fp, trials, k, o.degree_filter, o.fuse, o.group, o.block,
-          (long long)(o.load_factor * 1000), o.sort_sweep, o.distance_prune, o.part_bits};
+          (long long)(o.load_factor * 1000), o.sort_sweep, o.distance_prune, o.part_bits,
+          o.chain};
 }
 
 // init_run for colouring id cid of the context, which the run then holds a reference to.
@@ -1841,6 +1915,7 @@ const char *cc_strerror(int code) {
     case CC_ENOTFOUND: return "unknown id";
     case CC_EKEYWIDTH: return "trial, bag-mapping and colour bits exceed 128";
     case CC_EBUSY: return "the context is serving";
+    case CC_ECANCELED: return "served query cancelled before it started";
     default: return "unknown error";
   }
 }
@@ -1858,6 +1933,7 @@ void cc_default_opts(cc_run_opts *o) {
   o->distance_prune = 0;
   o->max_slices = 0;
   o->part_bits = 0;
+  o->chain = 1;
 }
 
 int cc_create(cc_ctx **out, int device, void *stream, void *d_arena, size_t arena_bytes) {
@@ -1974,6 +2050,9 @@ int cc_load_graph(cc_ctx *ctx, int32_t n, const int32_t *h_row_ptr, const int32_
   c->graph_fp = fp;
   c->h_row_ptr.assign(h_row_ptr, h_row_ptr + n + 1);
   c->h_col.assign(h_col, h_col + m2);
+  c->max_deg = 0;
+  for (int32_t v = 0; v < n; ++v)
+    c->max_deg = std::max<int64_t>(c->max_deg, (int64_t)h_row_ptr[v + 1] - h_row_ptr[v]);
   c->n = n;
   CUDA_OK(cudaStreamSynchronize(c->stream));
   return CC_OK;
@@ -2278,7 +2357,8 @@ int cc_table_dump(cc_ctx *ctx, int32_t run_id, int32_t node, uint64_t capacity, 
   uint32_t *d_mask = (uint32_t *)(d_phi + m * b);
   u64 *d_cnt = (u64 *)(((uintptr_t)(d_mask + m) + 7) & ~uintptr_t(7));
   int rc = CC_OK;
-  TableDesc td{t.slots, t.cap, R->d_counters + node, t.hashed};
+  // a planned table appended in chunks has holes: scan it up to its cursor
+  TableDesc td{t.slots, t.cap, t.bound ? t.bound : R->d_counters + node, t.hashed};
   if (cudaMemsetAsync(d_n, 0, sizeof(u64), c->stream) != cudaSuccess ||
       cc::launch_unpack(c->stream, c->dev, R->kw, R->L, td, b, m, d_trial, d_phi, d_mask, d_cnt,
                         d_n) != 0) {

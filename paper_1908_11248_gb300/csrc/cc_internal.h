@@ -75,6 +75,20 @@ struct IntroArgs {
   int *err;
   uint32_t ubit;             // 1 << u, tested against G.allow
   unsigned chunk;            // warp kernels, mode 1: slots a warp reserves at a time (32..256)
+  // chained introduce (launch_intro_chain): the input is the child y of a lower introduce x1
+  // whose table is not stored; the fields above describe the upper introduce x2 (its bag
+  // neighbours' slots counted in y's bag), these the lower one
+  int c_p;                   // slot of x1's vertex in x1's bag
+  int c_nnb;                 // bag neighbours of x1's vertex (at least one)
+  int c_nb_slot[kMaxBag];    // their slots in y's bag
+  int c_degF;                // degree filter of x1's vertex (0 = off)
+  uint32_t c_ubit;           // 1 << x1's vertex, tested against G.allow
+  unsigned long long *c_valid;  // number of x1 entries (|D_x1|), counted, not written
+  // non-null (x1 with one bag neighbour, k <= 16): per trial t and host vertex w, sixteen
+  // 16-bit counts of w's neighbours of each colour that pass x1's degree filter and allowed
+  // mappings (launch_nb_colour_hist); an entry whose run has no x2 candidate then counts its x1
+  // extensions from them instead of walking w's adjacency
+  const unsigned long long *c_hist;
 };
 
 struct ForgetArgs {
@@ -219,6 +233,18 @@ int launch_deg8(cudaStream_t s, const DevInfo &d, const int32_t *row_ptr, int32_
                 uint8_t *deg8);
 // Grouped introduce (child sorted by bag-neighbour images), warp by warp, for planned runs;
 // modes as launch_intro_warp.
+// Two introduces in one pass (planned capacities, mode 1): x1 = introduce u1 over y, then x2 =
+// introduce u2 over x1, u2 not adjacent to u1 and y in runs of equal images of u2's bag
+// neighbours.  x1's entries are generated and counted (into c_valid) but not stored; each is
+// extended by the run's shared list of u2's candidates and x2's entries are appended as in
+// launch_intro_group_warp.
+int launch_intro_chain(cudaStream_t s, const DevInfo &d, int kw, const IntroArgs &a);
+// hist[(t * n + w) * 4 .. + 4): colour c's count in 16-bit field c of the four words, over w's
+// neighbours v with deg(v) >= degF and bit `ubit` of allow[v] (when G.allow); adds the
+// adjacency entries read (trials times 2m) to *cand.  Degrees must be below 65536.
+int launch_nb_colour_hist(cudaStream_t s, const DevInfo &d, const GraphDev &G, int trials,
+                          int degF, uint32_t ubit, unsigned long long *hist,
+                          unsigned long long *cand);
 int launch_intro_group_warp(cudaStream_t s, const DevInfo &d, int kw, int mode,
                             const IntroArgs &a);
 int launch_forget(cudaStream_t s, const DevInfo &d, int kw, int block, const ForgetArgs &a);

@@ -16,6 +16,7 @@
 //                         set of phi's image; equal results summed
 //   root                : a colourful copy exists iff the root table is nonempty; the count is
 //                         the sum of the root counts
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -592,8 +593,87 @@ __global__ void __launch_bounds__(256, 4) intro_warp_kernel(IntroArgs a) {
 // lists do not fit a buffer is processed entry by entry.
 constexpr int kGroupCap = 256;  // candidate-list buffer per warp (two of them)
 
-template <typename K, int MODE>
-__global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
+// Per host vertex w (one thread) and every trial: counts of w's neighbours by colour, four
+// colours to a 64-bit word (16-bit fields), for the chained introduce's counted entries.
+__global__ void __launch_bounds__(256) nb_colour_hist_kernel(GraphDev G, int trials, int degF,
+                                                             uint32_t ubit, u64 *hist,
+                                                             u64 *cand) {
+  u64 seen = 0;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < G.n; w += gridDim.x * blockDim.x) {
+    const int r0 = G.row_ptr[w], r1 = G.row_ptr[w + 1];
+    for (int t = 0; t < trials; ++t) {
+      const uint8_t *col = G.colors + (u64)t * (u64)G.n;
+      u64 h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+      for (int r = r0; r < r1; ++r) {
+        const int v = __ldg(G.col + r);
+        if (degF && G.deg8[v] < degF) continue;
+        if (G.allow && !(G.allow[v] & ubit)) continue;
+        const int c = col[v];
+        const u64 one = 1ull << (16 * (c & 3));
+        h0 += (c >> 2) == 0 ? one : 0;
+        h1 += (c >> 2) == 1 ? one : 0;
+        h2 += (c >> 2) == 2 ? one : 0;
+        h3 += (c >> 2) == 3 ? one : 0;
+      }
+      u64 *o = hist + ((u64)t * (u64)G.n + (u64)w) * 4;
+      reinterpret_cast<ulonglong2 *>(o)[0] = make_ulonglong2(h0, h1);
+      reinterpret_cast<ulonglong2 *>(o)[1] = make_ulonglong2(h2, h3);
+    }
+    seen += (u64)(r1 - r0) * (u64)trials;
+  }
+  for (int o = 16; o > 0; o >>= 1) seen += __shfl_down_sync(0xffffffffu, seen, o);
+  if ((threadIdx.x & 31) == 0 && seen) atomicAdd(cand, seen);
+}
+
+// x1's extensions of an entry with colour set cm from the colour counts of its anchor image
+__device__ __forceinline__ u64 hist_count(const u64 *h, uint32_t cm, int k) {
+  const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(h));
+  const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(h) + 1);
+  const u64 w[4] = {a.x, a.y, b.x, b.y};
+  u64 sum = 0;
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    if (c < k && !((cm >> c) & 1u)) sum += (w[c >> 2] >> (16 * (c & 3))) & 0xFFFFull;
+  return sum;
+}
+
+// x1's candidates of one y entry (chained introduce): the adjacency list of the bag neighbour
+// image with the fewest neighbours
+template <typename K>
+__device__ __forceinline__ void chain_anchor(const IntroArgs &a, K key, int &rs, int &d,
+                                             int &anc) {
+  rs = 0;
+  d = 0;
+  anc = 0;
+  if (key == 0) return;
+  int best = INT_MAX;
+  for (int j = 0; j < a.c_nnb; ++j) {
+    const int w = key_slot(key, a.L, a.c_nb_slot[j]);
+    const int r0 = a.G.row_ptr[w], dd = a.G.row_ptr[w + 1] - r0;
+    if (dd < best) {
+      best = dd;
+      rs = r0;
+      anc = j;
+    }
+  }
+  d = best;
+}
+
+// x1's rule for candidate v of y entry `key` (colour set cm): colour not in the set, degree
+// filter, allowed mapping, adjacent to every bag neighbour image but the anchor's
+template <typename K>
+__device__ __forceinline__ bool chain_ok(const IntroArgs &a, K key, uint32_t cm, int v, int cv,
+                                         int anc) {
+  if ((cm >> cv) & 1u) return false;
+  if (a.c_degF && a.G.deg8[v] < a.c_degF) return false;
+  if (a.G.allow && !(a.G.allow[v] & a.c_ubit)) return false;
+  for (int j = 0; j < a.c_nnb; ++j)
+    if (j != anc && !adjacent(a.G, key_slot(key, a.L, a.c_nb_slot[j]), v)) return false;
+  return true;
+}
+
+template <typename K, int MODE, bool CHAIN = false>
+__global__ void __launch_bounds__(256, CHAIN ? 3 : 4) intro_group_warp_kernel(IntroArgs a) {
   __shared__ int s_buf[8][2 * kGroupCap];
   const Slot<K> *in = reinterpret_cast<const Slot<K> *>(a.in.slots);
   Slot<K> *out = reinterpret_cast<Slot<K> *>(a.out.slots);
@@ -610,7 +690,7 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   const u64 n = (u64)a.G.n;
   const u64 chunk = a.chunk;
   u64 cbase = 0, cfill = chunk;
-  u64 produced = 0, fresh = 0, examined = 0;
+  u64 produced = 0, fresh = 0, examined = 0, produced1 = 0;
   bool full = false;
   // the run the previous window ended in (warp-uniform): its tuple and its list
   // bufs[cb * kGroupCap + cs .. + cl) (cl < 0: none)
@@ -696,6 +776,62 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
       const uint32_t cm = key_mask(key, a.L);
       const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
+      if constexpr (CHAIN) {
+        // every x1 extension (entry, v1) of this entry is counted; those with a nonempty u2 list
+        // are extended by it at once
+        int r1, d1, anc1;
+        chain_anchor(a, key, r1, d1, anc1);
+        // u2 candidates of the run whose colour is not in this entry's set: only those can
+        // extend one of its x1 entries (the set only grows with v1's colour)
+        int nv = 0;
+        for (int r = 0; r < nmax; ++r)
+          if (r < n0 && !((cm >> a.G.colors[crow + (u64)lst[s0 + r]]) & 1u)) ++nv;
+        if (a.c_hist && key != 0 && nv == 0) {
+          // none: the entry's x1 extensions are only counted, from the colour counts of its
+          // anchor image
+          const u64 w1 = (u64)key_slot(key, a.L, a.c_nb_slot[anc1]);
+          produced1 += hist_count(a.c_hist + ((u64)key_trial(key, a.L) * n + w1) * 4, cm,
+                                  a.L.k);
+          d1 = 0;
+        }
+        if (nv == 0) n0 = 0;  // no pair can be valid
+        int dmax = d1, dsum = d1;
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        }
+        if (lane == 0) examined += (u64)dsum;
+        const K b1 = key != 0 ? intro_base(key, a.L, a.c_p, -1) : (K)0;
+        const int vsh1 = intro_vshift(a.L, a.c_p, -1);
+        for (int j = 0; j < dmax; ++j) {
+          bool ok1 = false;
+          int v1 = 0, cv1 = 0;
+          if (j < d1) {
+            v1 = __ldg(a.G.col + r1 + j);
+            cv1 = a.G.colors[crow + (u64)v1];
+            ok1 = chain_ok(a, key, cm, v1, cv1, anc1);
+          }
+          produced1 += ok1 ? 1u : 0u;
+          const bool pair = ok1 && n0 > 0;
+          if (!__any_sync(0xffffffffu, pair)) continue;
+          int m = pair ? n0 : 0;
+          for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+          const uint32_t cm1 = cm | (1u << cv1);
+          const K k1 = pair ? intro_out(b1, vsh1, v1, cv1) : (K)0;
+          for (int r = 0; r < m; ++r) {
+            bool valid = false;
+            K okey = 0;
+            if (pair && r < n0) {
+              const int v = lst[s0 + r];
+              const int cv = a.G.colors[crow + (u64)v];
+              valid = !((cm1 >> cv) & 1u);
+              if (valid) okey = intro_out(intro_base(k1, a.L, a.p, q), vsh, v, cv);
+            }
+            warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
+          }
+        }
+        nmax = 0;  // the plain loop below has nothing left to do
+      }
       for (int r = 0; r < nmax; ++r) {
         bool valid = false;
         K okey = 0;
@@ -735,6 +871,52 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
       for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
       const uint32_t cm = key_mask(key, a.L);
       const u64 crow = key != 0 ? (u64)key_trial(key, a.L) * n : 0;
+      if constexpr (CHAIN) {
+        // every x1 extension, then every u2 candidate of the entry's own anchor list with all
+        // of x2's checks
+        int r1, d1, anc1;
+        chain_anchor(a, key, r1, d1, anc1);
+        int dmax = d1, dsum = d1, nsum = 0;
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        }
+        const K b1 = key != 0 ? intro_base(key, a.L, a.c_p, -1) : (K)0;
+        const int vsh1 = intro_vshift(a.L, a.c_p, -1);
+        for (int j = 0; j < dmax; ++j) {
+          bool ok1 = false;
+          int v1 = 0, cv1 = 0;
+          if (j < d1) {
+            v1 = __ldg(a.G.col + r1 + j);
+            cv1 = a.G.colors[crow + (u64)v1];
+            ok1 = chain_ok(a, key, cm, v1, cv1, anc1);
+          }
+          produced1 += ok1 ? 1u : 0u;
+          const bool pair = ok1 && nc > 0;
+          if (!__any_sync(0xffffffffu, pair)) continue;
+          nsum += pair ? nc : 0;
+          const uint32_t cm1 = cm | (1u << cv1);
+          const K k1 = pair ? intro_out(b1, vsh1, v1, cv1) : (K)0;
+          for (int r = 0; r < nmax; ++r) {
+            bool valid = false;
+            K okey = 0;
+            if (pair && r < nc) {
+              const int v = __ldg(a.G.col + rs + r);
+              const int cv = a.G.colors[crow + (u64)v];
+              valid = !((cm1 >> cv) & 1u);
+              if (valid && a.degF) valid = a.G.deg8[v] >= a.degF;
+              if (valid && a.G.allow) valid = (a.G.allow[v] & a.ubit) != 0;
+              for (int qq = 0; qq < a.nnb && valid; ++qq)
+                if (qq != anc) valid = adjacent(a.G, key_slot(key, a.L, a.nb_slot[qq]), v);
+              if (valid) okey = intro_out(intro_base(k1, a.L, a.p, q), vsh, v, cv);
+            }
+            warp_emit<K, MODE>(a, valid, okey, c, lane, lt, cbase, cfill, produced, fresh, full);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+        if (lane == 0) examined += (u64)(dsum + nsum);
+        nmax = 0;
+      }
       for (int j = 0; j < nmax; ++j) {
         bool valid = false;
         K okey = 0;
@@ -761,8 +943,10 @@ __global__ void __launch_bounds__(256, 4) intro_group_warp_kernel(IntroArgs a) {
   for (int o = 16; o > 0; o >>= 1) {
     produced += __shfl_down_sync(0xffffffffu, produced, o);
     fresh += __shfl_down_sync(0xffffffffu, fresh, o);
+    if (CHAIN) produced1 += __shfl_down_sync(0xffffffffu, produced1, o);
   }
   if (lane == 0) {
+    if (CHAIN && a.c_valid && produced1) atomicAdd(a.c_valid, produced1);
     if (a.valid && produced) atomicAdd(a.valid, produced);
     if (MODE == 2 && fresh) atomicAdd(a.out.count, fresh);
     if (a.cand && examined) atomicAdd(a.cand, examined);
@@ -1034,6 +1218,21 @@ int launch_intro_group_warp(cudaStream_t s, const DevInfo &d, int kw, int mode,
     if (mode == 1) intro_group_warp_kernel<u128, 1><<<grid, 256, 0, s>>>(a);
     else intro_group_warp_kernel<u128, 2><<<grid, 256, 0, s>>>(a);
   }
+  return (int)cudaGetLastError();
+}
+
+int launch_nb_colour_hist(cudaStream_t s, const DevInfo &d, const GraphDev &G, int trials,
+                          int degF, uint32_t ubit, unsigned long long *hist,
+                          unsigned long long *cand) {
+  const int grid = std::max(1, std::min(d.sms * 8, (G.n + 255) / 256));
+  nb_colour_hist_kernel<<<grid, 256, 0, s>>>(G, trials, degF, ubit, hist, cand);
+  return (int)cudaGetLastError();
+}
+
+int launch_intro_chain(cudaStream_t s, const DevInfo &d, int kw, const IntroArgs &a) {
+  const int grid = d.sms * d.blocks_per_sm;
+  if (kw == 1) intro_group_warp_kernel<u64, 1, true><<<grid, 256, 0, s>>>(a);
+  else intro_group_warp_kernel<u128, 1, true><<<grid, 256, 0, s>>>(a);
   return (int)cudaGetLastError();
 }
 

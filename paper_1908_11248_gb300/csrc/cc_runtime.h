@@ -228,6 +228,7 @@ struct Ctx {
   int32_t n = -1;
   int32_t *d_row_ptr = nullptr, *d_col = nullptr;
   uint8_t *d_deg8 = nullptr;  // min(degree, 255) per vertex
+  int64_t max_deg = 0;        // largest vertex degree of the loaded graph
   std::vector<int32_t> h_row_ptr, h_col;
   // per radius r, per vertex the vertices within distance r (CSR row pointers and columns,
   // built on first use by the distance bound)

@@ -73,6 +73,7 @@ struct Server {
   std::deque<ServeQuery> queue;
   std::map<int64_t, ServeResult> results;
   int64_t next_ticket = 1;
+  int64_t cancel_upto = 0;  // queued queries with tickets up to this one end cancelled
   bool running = false, stopping = false;
   std::thread worker;
   size_t budget = 0;    // arena bytes the queries may hold at once
@@ -351,6 +352,16 @@ void serve_loop(Server *S, Ctx *c) {
         if (S->queue.empty()) break;
         q = S->queue.front();
       }
+      bool cancelled;
+      {
+        std::lock_guard<std::mutex> g(S->mu);
+        cancelled = q.ticket <= S->cancel_upto;
+        if (cancelled) S->queue.pop_front();
+      }
+      if (cancelled) {  // put back by a retry after cc_serve_cancel dropped the queue
+        publish(S, q, CC_ECANCELED, {}, {});
+        continue;
+      }
       const size_t need = estimate(S, c, q);
       {
         std::lock_guard<std::mutex> g(S->mu);
@@ -497,6 +508,24 @@ int cc_serve_stats(cc_ctx *ctx, uint64_t *submitted, uint64_t *completed,
   if (exact_runs) *exact_runs = S->exact_runs;
   if (reruns) *reruns = S->reruns;
   if (sliced) *sliced = S->sliced;
+  return CC_OK;
+}
+
+int cc_serve_cancel(cc_ctx *ctx, uint64_t *n_cancelled) {
+  Ctx *c = (Ctx *)ctx;
+  if (!c) return CC_EINVAL;
+  Server *S = c->server;
+  if (!S) return CC_EINVAL;
+  std::deque<cc::ServeQuery> dropped;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    if (!S->running) return CC_EINVAL;
+    S->cancel_upto = S->next_ticket - 1;
+    dropped.swap(S->queue);
+  }
+  for (const auto &q : dropped) cc::publish(S, q, CC_ECANCELED, {}, {});
+  if (n_cancelled) *n_cancelled = dropped.size();
+  cc::wake(S);
   return CC_OK;
 }
 

@@ -6,7 +6,7 @@
 // node rule is carried out.  The tuner times the planned run of one (pattern, colouring) under candidate node schedules
 // (the pattern's decomposition rooted at different bags, which changes the order in which the
 // nice decomposition introduces, forgets and joins) and candidate execution options (forget
-// scheme, threads per block, hash load factor, sort schedule, grouped introduce), by coordinate
+// scheme, threads per block, hash load factor, sort schedule, grouped and chained introduces), by coordinate
 // descent from the starting options, and returns the fastest.  Every candidate's per-trial
 // counts must equal the first's: the root results do not depend on any of these choices.
 #include <algorithm>
@@ -183,6 +183,7 @@ int cc_autotune(cc_ctx *ctx, int32_t pattern_id, int32_t coloring_id, const cc_r
   if (!rc) rc = sweep([](cc_run_opts &o, float v) { o.load_factor = v; }, {0.5f, 0.35f, 0.7f});
   if (!rc) rc = sweep([](cc_run_opts &o, float v) { o.sort_sweep = (int)v; }, {1, 0});
   if (!rc) rc = sweep([](cc_run_opts &o, float v) { o.group = (int)v; }, {1, 0});
+  if (!rc) rc = sweep([](cc_run_opts &o, float v) { o.chain = (int)v; }, {1, 0});
   if (rc) return rc;
   *best_opts = cur;
   *best_pattern_id = cur_pid;

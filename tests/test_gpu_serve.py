@@ -210,3 +210,30 @@ def test_big_query_runs_split_alone_and_in_the_mix(ctx, graph):
         assert np.array_equal(counts, want[0]) and np.array_equal(exists, want[1])
     for (status, counts, exists, _), w in zip(mix[:3] + mix[4:], want_s):
         assert status == 0 and np.array_equal(counts, w[0])
+
+
+def test_cancel_drops_unstarted_queries(ctx, graph):
+    """cc_serve_cancel right after a burst: every query ends, either with its result (equal to
+    the same query run alone) or with CC_ECANCELED; queries submitted after the cancel run."""
+    cc.cc_load_graph(ctx.h, *graph)
+    pids = [cc.cc_load_pattern(ctx.h, *p) for p in PATTERNS]
+    qs = _queries(64, 5)
+    cc.cc_serve_start(ctx.h, 0, 2)
+    tickets = [cc.cc_serve_submit(ctx.h, pids[p], s, T, k) for p, s, T, k in qs]
+    dropped = cc.cc_serve_cancel(ctx.h)
+    after = [cc.cc_serve_submit(ctx.h, pids[p], s + 1, T, k) for p, s, T, k in qs[:4]]
+    res = _wait(ctx, tickets + after, [q[2] for q in qs] + [q[2] for q in qs[:4]])
+    cc.cc_serve_stop(ctx.h)
+    statuses = [r[0] for r in res[:64]]
+    assert set(statuses) <= {0, cc.CC_ECANCELED}
+    assert statuses.count(cc.CC_ECANCELED) >= dropped >= 1
+    for (p, s, T, k), (status, counts, exists, _) in zip(qs, res[:64]):
+        if status == 0:
+            want_c, want_e = _plain(ctx, pids[p], s, T, k)
+            assert np.array_equal(counts, want_c) and np.array_equal(exists, want_e)
+    for (p, s, T, k), (status, counts, exists, _) in zip(qs[:4], res[64:]):
+        assert status == 0
+        want_c, want_e = _plain(ctx, pids[p], s + 1, T, k)
+        assert np.array_equal(counts, want_c) and np.array_equal(exists, want_e)
+    with pytest.raises(cc.CCError):
+        cc.cc_serve_cancel(ctx.h)  # not serving
