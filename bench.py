@@ -319,15 +319,22 @@ def traffic_summary(csv_path, alg_path, cmd, out_dir=None):
     return path
 
 
-def launch_summary(csv_path, workload, cmd, out_dir=None):
+def launch_summary(csv_path, workload, cmd, out_dir=None, skip_steps=0):
     """profiles/launches_<workload>.txt from an ncu launch list (gpu__time_duration.sum of every
     launch of a bench command): per kernel and per node rule the launches, total device time and
-    share.  Under ncu launches are serialised and run cold: the shares compare with the bench's
-    event-timed shares, the absolute times do not."""
-    by_kernel, by_group = kernel_table(ncu_kernels(csv_path))
+    share, from the (skip_steps + 1)-th colouring launch on (a step starts by colouring: the
+    warm-up steps, whose first run of a key is exact, are left out).  Under ncu launches are
+    serialised and run cold: the shares compare with the bench's event-timed shares, the
+    absolute times do not."""
+    launches = ncu_kernels(csv_path)
+    colour_at = [i for i, d in enumerate(launches) if kernel_base(d["name"]) == "color_kernel"]
+    if skip_steps and len(colour_at) > skip_steps:
+        launches = launches[colour_at[skip_steps]:]
+    by_kernel, by_group = kernel_table(launches)
     total = sum(v["ms"] for v in by_kernel.values()) or 1.0
     out = [f"# ncu launch list: {workload}", f"# command: {cmd}",
-           f"# {sum(v['launches'] for v in by_kernel.values())} launches, {total:.3f} ms of "
+           f"# launches from colouring launch {skip_steps + 1} on (warm-up steps left out): "
+           f"{sum(v['launches'] for v in by_kernel.values())} launches, {total:.3f} ms of "
            "device time (serialised, cold caches)",
            "# group  launches  ms  share"]
     for g, v in sorted(by_group.items(), key=lambda x: -x[1]["ms"]):
@@ -1081,7 +1088,8 @@ def main():
                          "(gpu__time_duration.sum) of a bench command; runs nothing on the GPU")
     args = ap.parse_args()
     if args.launch_summary:
-        print(launch_summary(args.launch_summary, args.workload, args.capture_cmd))
+        print(launch_summary(args.launch_summary, args.workload, args.capture_cmd,
+                             skip_steps=args.warmup))
         return
     if args.traffic_summary:
         print(traffic_summary(*args.traffic_summary, args.capture_cmd))
