@@ -733,6 +733,17 @@ __global__ void __launch_bounds__(256, CHAIN ? 3 : 4) intro_group_warp_kernel(In
         }
       }
       if (lane == 0) examined += (u64)best;
+      // two bag neighbours, the other one of degree <= 32: its adjacency list is held one entry
+      // a lane and every candidate is compared against it by shuffles instead of a binary
+      // search in global memory
+      int ob = 0, od = 33;
+      if (a.nnb == 2) {
+        const int w2 = key_slot(lkey, a.L, a.nb_slot[1 - anc]);
+        ob = a.G.row_ptr[w2];
+        od = a.G.row_ptr[w2 + 1] - ob;
+      }
+      const bool inreg = od <= 32;
+      const int bv = (inreg && lane < od) ? __ldg(a.G.col + ob + lane) : -1;
       const int start = used;
       for (int j0 = 0; j0 < best; j0 += 32) {
         const int j = j0 + lane;
@@ -742,8 +753,14 @@ __global__ void __launch_bounds__(256, CHAIN ? 3 : 4) intro_group_warp_kernel(In
           v = __ldg(a.G.col + rs + j);
           ok = (a.degF == 0 || a.G.deg8[v] >= a.degF) &&
                (!a.G.allow || (a.G.allow[v] & a.ubit));
-          for (int qq = 0; qq < a.nnb && ok; ++qq)
-            if (qq != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[qq]), v);
+          if (!inreg)
+            for (int qq = 0; qq < a.nnb && ok; ++qq)
+              if (qq != anc) ok = adjacent(a.G, key_slot(lkey, a.L, a.nb_slot[qq]), v);
+        }
+        if (inreg) {  // every lane takes part in the shuffles
+          bool hit = false;
+          for (int qq = 0; qq < od; ++qq) hit |= __shfl_sync(0xffffffffu, bv, qq) == v;
+          ok = ok && hit;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         const int pos = used + __popc(bal & lt);
