@@ -210,7 +210,7 @@ GROUPS = {"color": "colour", "leaf": "leaf", "intro_count": "introduce",
 KERNEL_GROUPS = {
     "color_kernel": "colour", "leaf_kernel": "leaf",
     "intro_kernel": "introduce", "intro_warp_kernel": "introduce",
-    "intro_group_warp_kernel": "introduce",
+    "intro_group_warp_kernel": "introduce", "nb_colour_hist_kernel": "introduce",
     "sort_hist_kernel": "forget", "row_scan_kernel": "forget", "digit_base_kernel": "forget",
     "sort_scatter_kernel": "forget", "sweep_hist_kernel": "forget",
     "sweep_bases_kernel": "forget", "sweep_pass_kernel": "forget",

@@ -88,3 +88,20 @@ def test_traffic_summary_from_an_ncu_listing(tmp_path):
     lines = {ln.split()[0]: ln.split() for ln in open(lp) if not ln.startswith("#")}
     assert lines["forget"][1] == "2" and abs(float(lines["forget"][3]) - 0.3 / 0.8001) < 1e-3
     assert lines["intro_warp_kernel"][1] == "1"
+
+
+def test_chained_introduce_byte_accounting():
+    """A chained launch (two introduces in one pass, timed at the upper node) reads the lower
+    introduce's child and writes the upper introduce's entries: the lower table is neither
+    written nor read back, so its entries add no bytes."""
+    # nodes: (type, child0, child1, vertex, bag): leaf 0, introduce 1 (lower), introduce 2
+    nodes = [(0, -1, -1, 0, [0]), (1, 0, -1, 1, [0, 1]), (1, 1, -1, 2, [0, 1, 2])]
+    sizes = [10, 1000, 7]
+    k = 3
+    got = bench.algorithmic_bytes("intro_chain", 2, nodes, sizes, 40, 100, 1, k)
+    assert got == 10 * bench.slot_bytes(1, k) + 40 * 5 + 7 * bench.slot_bytes(3, k)
+    assert bench.GROUPS["intro_chain"] == "introduce"
+    assert bench.kernel_group("void cc::(anonymous namespace)::nb_colour_hist_kernel(x)",
+                              False) == "introduce"  # timed with the chained launch
+    assert bench.kernel_group("intro_group_warp_kernel<unsigned long, 1, true>", True) == \
+        "introduce+forget"
