@@ -848,6 +848,93 @@ def batching_leg(cc, torch, name="ba20k_grid2x4"):
     return res
 
 
+def tree_hom_counts(row_ptr, col, t):
+    """Injective homomorphism counts into G[V_t], the subgraph of G induced by the vertices of
+    degree >= t (every map into it passes a degree filter of at most t), of the forests on at
+    most four vertices, keyed by (vertices, edges, sorted vertex degrees); exact except the
+    4-vertex path, a lower bound (its maps with a = d are at most min(d_b, d_c) - 1 per middle
+    edge)."""
+    rp = np.asarray(row_ptr, np.int64)
+    col = np.asarray(col, np.int64)
+    n = len(rp) - 1
+    deg = np.diff(rp)
+    src = np.repeat(np.arange(n), deg)
+    keep = deg >= t
+    m = keep[src] & keep[col]
+    s2, c2 = src[m], col[m]
+    d = np.bincount(s2, minlength=n).astype(np.float64)
+    nv = float(keep.sum())
+    m2 = float(len(s2))  # ordered edges = 2m'
+    p3 = float((d * (d - 1)).sum())
+    return {
+        (1, 0, (0,)): nv,
+        (2, 0, (0, 0)): nv * (nv - 1),
+        (2, 1, (1, 1)): m2,
+        (3, 1, (0, 1, 1)): m2 * (nv - 2),
+        (3, 2, (1, 1, 2)): p3,
+        (4, 2, (0, 1, 1, 2)): p3 * (nv - 3),
+        (4, 2, (1, 1, 1, 1)): m2 * m2 - 4.0 * float((d * d).sum()) + 2.0 * m2,
+        (4, 3, (1, 1, 1, 3)): float((d * (d - 1) * (d - 2)).sum()),
+        (4, 3, (1, 1, 2, 2)): float(((d[s2] - 1) * (d[c2] - 1)).sum()
+                                    - np.maximum(np.minimum(d[s2], d[c2]) - 1, 0).sum()),
+    }
+
+
+def pl_bound_leg(cc, hbm_bytes):
+    """The batched power-law configuration (n = 10^6, 64 random partial 3-trees of 10-12
+    vertices, k = n_F, 16 trials each) against one GPU's memory, on the host: for every pattern,
+    the library's nice decomposition; a node whose subtree holds only a leaf and introduces has
+    V*_x = V_x, so its table holds one entry per trial and colourful injective map of F[V_x]
+    (Section 2.1, table semantics): in expectation T * inj(F[V_x], G) * k!/((k-b)! k^b).  For
+    the forest-shaped F[V_x] the count is taken in G[V_t] (t the largest F-degree in the bag, so
+    the degree filter of Section 3.2 keeps every such map), a lower bound on the table; times the
+    entry size 4b + 2 + 8 bytes it is compared with the GPU's memory.  Patterns whose pure nodes
+    all contain a cycle get no bound here."""
+    w = synth.WORKLOADS["pl1m_ktree3"]
+    g = synth.make_graph(w["graph"])
+    T = w["trials"]
+    counts = {}
+    out, proven = [], 0
+    for i, (nF, edges, td) in enumerate(synth.ktree_batch(w)):
+        nodes, width = cc.cc_nice_decomposition(nF, edges, td)
+        adj = [set() for _ in range(nF)]
+        for a, b in np.asarray(edges).reshape(-1, 2).tolist():
+            adj[a].add(b)
+            adj[b].add(a)
+        pure, best = [False] * len(nodes), None
+        for x, (ty, c0, _, _, bag) in enumerate(nodes):
+            pure[x] = ty == 0 or (ty == 1 and pure[c0])
+            if not pure[x]:
+                continue
+            b = len(bag)
+            e = sum(1 for a in bag for c in bag if a < c and c in adj[a])
+            shape = (b, e, tuple(sorted(sum(1 for c in bag if c in adj[a]) for a in bag)))
+            t = max(len(adj[u]) for u in bag)
+            if t not in counts:
+                counts[t] = tree_hom_counts(g[0], g[1], t)
+            if shape not in counts[t]:
+                continue
+            falling = float(np.prod([nF - j for j in range(b)])) / float(nF) ** b
+            ent = T * counts[t][shape] * falling
+            byt = ent * slot_bytes(b, nF)
+            if best is None or byt > best["bytes"]:
+                best = {"pattern": i, "n_F": nF, "width": width, "node": x, "bag": b,
+                        "edges": e, "degree_threshold": t, "entries": ent, "bytes": byt}
+        if best is None:
+            out.append({"pattern": i, "n_F": nF, "bound": None})
+            continue
+        best["exceeds_gpu_memory"] = bool(best["bytes"] > hbm_bytes)
+        proven += best["exceeds_gpu_memory"]
+        out.append(best)
+    return {"workload": "pl1m_ktree3", "trials": T, "gpu_memory_bytes": hbm_bytes,
+            "patterns": len(out), "with_forest_bound": sum(1 for o in out if "bytes" in o),
+            "proven_too_large": int(proven), "per_pattern": out,
+            "note": "expected entries of one table (a node whose subtree is a leaf and "
+                    "introduces) counted in the subgraph of vertices of degree >= the bag's "
+                    "largest F-degree: a lower bound on the DP's memory for the library's "
+                    "decomposition of each pattern"}
+
+
 def er_phase_point(cc, h, pat, k, seed, trials):
     """One point of the Erdos-Renyi study on the loaded target: load the pattern (minimum-width
     decomposition), colour `trials` times, run the DP over all colourings at once and decide.
@@ -1054,9 +1141,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=MAIN, choices=sorted(ORACLE_SAMPLE),
                     help="workload of the bench line")
-    ap.add_argument("--legs", default="ba20k,latency,batching,serve,er_phase",
+    ap.add_argument("--legs", default="ba20k,latency,batching,serve,er_phase,pl_bound",
                     help="extra keys to measure (comma list of ba20k, latency, batching, serve, "
-                         "er_phase; 'none' for none)")
+                         "er_phase, pl_bound; 'none' for none)")
     ap.add_argument("--er-phase-step", type=float, default=0.0,
                     help="grid step of the Erdos-Renyi study (default: the paper's 0.03)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1166,6 +1253,10 @@ def main():
             log("leg: batching")
             line["batched_vs_plain"] = batching_leg(cc, torch)
             torch.cuda.empty_cache()
+        if "pl_bound" in legs:
+            log("leg: pl_bound")
+            line["pl1m_ktree3_bound"] = pl_bound_leg(
+                cc, torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory)
         if "er_phase" in legs:
             log("leg: er_phase")
             line["er_phase"] = er_phase_leg(cc, torch, args.er_phase_step or None)

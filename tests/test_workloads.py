@@ -105,3 +105,33 @@ def test_chained_introduce_byte_accounting():
                               False) == "introduce"  # timed with the chained launch
     assert bench.kernel_group("intro_group_warp_kernel<unsigned long, 1, true>", True) == \
         "introduce+forget"
+
+
+def test_forest_hom_counts_against_brute_force():
+    """The host-side counts behind the power-law memory bound: injective homomorphisms of the
+    forests on at most four vertices into the subgraph induced by the vertices of degree >= t,
+    by brute force over all injective maps; the 4-vertex path's count is a lower bound."""
+    import itertools
+
+    g = synth.barabasi_albert(22, 3, 4)
+    rp, col = np.asarray(g[0]), np.asarray(g[1])
+    n = len(rp) - 1
+    deg = np.diff(rp)
+    E = {(int(a), int(b)) for a in range(n) for b in col[rp[a]:rp[a + 1]]}
+    shapes = {  # (vertices, edges, sorted degrees) -> an edge list on 0..b-1
+        (1, 0, (0,)): [], (2, 0, (0, 0)): [], (2, 1, (1, 1)): [(0, 1)],
+        (3, 1, (0, 1, 1)): [(0, 1)], (3, 2, (1, 1, 2)): [(0, 1), (1, 2)],
+        (4, 2, (0, 1, 1, 2)): [(0, 1), (1, 2)], (4, 2, (1, 1, 1, 1)): [(0, 1), (2, 3)],
+        (4, 3, (1, 1, 1, 3)): [(0, 1), (0, 2), (0, 3)],
+        (4, 3, (1, 1, 2, 2)): [(0, 1), (1, 2), (2, 3)],
+    }
+    for t in (1, 4, 6):
+        got = bench.tree_hom_counts(rp, col, t)
+        vs = [v for v in range(n) if deg[v] >= t]
+        for shape, es in shapes.items():
+            brute = sum(1 for phi in itertools.permutations(vs, shape[0])
+                        if all((phi[a], phi[b]) in E for a, b in es))
+            if shape == (4, 3, (1, 1, 2, 2)):
+                assert got[shape] <= brute and got[shape] >= 0.5 * brute, (t, shape)
+            else:
+                assert got[shape] == brute, (t, shape, got[shape], brute)
