@@ -1255,8 +1255,11 @@ def main():
             torch.cuda.empty_cache()
         if "pl_bound" in legs:
             log("leg: pl_bound")
-            line["pl1m_ktree3_bound"] = pl_bound_leg(
-                cc, torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory)
+            try:  # host-only arithmetic; a failure here must not cost the bench line
+                line["pl1m_ktree3_bound"] = pl_bound_leg(
+                    cc, torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory)
+            except Exception as ex:  # noqa: BLE001
+                line["pl1m_ktree3_bound"] = {"error": repr(ex)}
         if "er_phase" in legs:
             log("leg: er_phase")
             line["er_phase"] = er_phase_leg(cc, torch, args.er_phase_step or None)
