@@ -935,6 +935,56 @@ def pl_bound_leg(cc, hbm_bytes):
                     "decomposition of each pattern"}
 
 
+def hash_leg(cc, torch):
+    """The hashed node rules, event-timed: `ba20k_grid2x4` (64 trials) with every introduce
+    adding its projected entries into its forget's open-addressing hash table (fuse 1: one
+    compare-and-swap to claim a key, one atomic add of the count, per entry), and pattern A of
+    Fig. 1 (three joins: hash join on the shared bag map) on the same graph with 16 trials, k =
+    n_F.  Reports each group's time and entries per second: for the hashed forget, entries
+    inserted (= atomic updates) per second."""
+    w = synth.WORKLOADS["ba20k_grid2x4"]
+    g = synth.make_graph(w["graph"])
+    out = {"graph": "BA n=20000 m=4 seed 1"}
+    with cc.Context(arena_bytes=64 << 30) as ctx:
+        h = ctx.h
+        cc.cc_load_graph(h, *g)
+        for label, pat, T, k, opts in (
+                ("forget_hashed", synth.make_pattern(w["pattern"]), w["trials"], w["k"],
+                 dict(fuse=1)),
+                ("join", synth.make_pattern(("A",)), 16, 9, {})):
+            pid = cc.cc_load_pattern(h, *pat)
+            N, _ = cc.cc_pattern_info(h, pid)
+            cid = cc.cc_color(h, w["seed"], T, k)
+            kinds = {}
+            for rep in range(3):  # exact, then planned runs
+                run = cc.cc_run_dp(h, pid, cid, cc.cc_default_opts(profile=1, **opts))
+                sizes = cc.cc_table_stats(h, run, N)[0]
+                if rep == 2:
+                    node, kind, ms, _ = cc.cc_run_timings(h, run)
+                    for i in range(len(node)):
+                        kn = cc.KERNEL_KINDS[int(kind[i])]
+                        x = int(node[i])
+                        d = kinds.setdefault(kn, {"launches": 0, "ms": 0.0, "entries": 0})
+                        d["launches"] += 1
+                        d["ms"] += float(ms[i])
+                        # entries a launch handles: an introduce's own entries (each inserted
+                        # into the forget's hash table when fused); a join's output entries
+                        d["entries"] += int(sizes[x])
+                    mode = cc.cc_run_mode(h, run)
+                cc.cc_release(h, run)
+            cc.cc_release_colors(h, cid)
+            for d in kinds.values():
+                d["entries_per_s"] = d["entries"] / (d["ms"] / 1e3) if d["ms"] else None
+            out[label] = {"pattern": "grid 2 4" if label == "forget_hashed" else "A (Fig. 1)",
+                          "trials": T, "k": k, "run_mode": mode, "kinds": kinds,
+                          "entries_per_step": int(sizes.sum())}
+    out["note"] = ("event-timed planned runs; intro_fused = introduce whose entries are inserted "
+                   "into the forget's hash table (entries_per_s = hash inserts per second, one "
+                   "claim and one atomic count update each); join_* = hash join build and "
+                   "probe/write (entries_per_s = join output entries per second)")
+    return out
+
+
 def er_phase_point(cc, h, pat, k, seed, trials):
     """One point of the Erdos-Renyi study on the loaded target: load the pattern (minimum-width
     decomposition), colour `trials` times, run the DP over all colourings at once and decide.
@@ -1141,9 +1191,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=MAIN, choices=sorted(ORACLE_SAMPLE),
                     help="workload of the bench line")
-    ap.add_argument("--legs", default="ba20k,latency,batching,serve,er_phase,pl_bound",
-                    help="extra keys to measure (comma list of ba20k, latency, batching, serve, "
-                         "er_phase, pl_bound; 'none' for none)")
+    ap.add_argument("--legs", default="ba20k,latency,batching,hash,serve,er_phase,pl_bound",
+                    help="extra keys to measure (comma list of ba20k, latency, batching, hash, "
+                         "serve, er_phase, pl_bound; 'none' for none)")
     ap.add_argument("--er-phase-step", type=float, default=0.0,
                     help="grid step of the Erdos-Renyi study (default: the paper's 0.03)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1252,6 +1302,13 @@ def main():
         if "batching" in legs:
             log("leg: batching")
             line["batched_vs_plain"] = batching_leg(cc, torch)
+            torch.cuda.empty_cache()
+        if "hash" in legs:
+            log("leg: hash")
+            try:
+                line["hashed_rules"] = hash_leg(cc, torch)
+            except Exception as ex:  # noqa: BLE001
+                line["hashed_rules"] = {"error": repr(ex)}
             torch.cuda.empty_cache()
         if "pl_bound" in legs:
             log("leg: pl_bound")
